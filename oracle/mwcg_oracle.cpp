@@ -1,0 +1,759 @@
+// CPU oracle for multi-word-arithmetic Conjugate Gradient.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the slow, single-threaded reference
+// that the CUDA solver is checked against.  Only the tests, the smoke check
+// and the CPU-baseline leg of the benchmark load it; the product path never
+// links, imports or calls it.  It shares no code with the CUDA sources.
+//
+// Everything is written from the paper "Sparse Iterative Solvers Using
+// High-Precision Arithmetic with Quasi Multi-Word Algorithms" (Mukunoki and
+// Ozaki): word algorithms of Sec. III (Algorithms 2-10), the solver of
+// Algorithm 1 with the implementation choices of Sec. IV-C (FP64 relative
+// residual) and Sec. IV-D (normalise r once per iteration, after its AXPY).
+// Where the paper is silent the reading taken is stated at the function.
+//
+// Build: plain C++17, -O2 -ffp-contract=off, no fast-math.  Every FP64
+// operation is an explicit call below (fadd/fsub/fmul/ffma/fdiv/fsqrt), so
+// nothing can be contracted or reordered, and each one bumps an operation
+// counter (FMA counts as one operation, Sec. III) that the tests read.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// FP64 primitives (round-to-nearest-even), counted.
+// ---------------------------------------------------------------------------
+uint64_t g_ops = 0;
+inline double fadd(double a, double b) { ++g_ops; return a + b; }
+inline double fsub(double a, double b) { ++g_ops; return a - b; }
+inline double fmul(double a, double b) { ++g_ops; return a * b; }
+inline double ffma(double a, double b, double c) { ++g_ops; return std::fma(a, b, c); }
+inline double fdiv(double a, double b) { return a / b; }
+inline double fsqrt(double a) { return std::sqrt(a); }
+
+// ---------------------------------------------------------------------------
+// Error-free transformations (Sec. III).
+// ---------------------------------------------------------------------------
+// Algorithm 2, TwoSum: x = fl(a+b), y = (a - (x - z)) + (b - z), z = x - a.
+inline void two_sum(double a, double b, double& x, double& y) {
+  double s = fadd(a, b);
+  double z = fsub(s, a);
+  double t1 = fsub(a, fsub(s, z));
+  double t2 = fsub(b, z);
+  y = fadd(t1, t2);
+  x = s;
+}
+// Algorithm 3, QuickTwoSum: x = fl(a+b), y = (a - x) + b.
+inline void quick_two_sum(double a, double b, double& x, double& y) {
+  double s = fadd(a, b);
+  y = fadd(fsub(a, s), b);
+  x = s;
+}
+// Algorithm 4, TwoProdFMA: x = fl(a*b), y = fma(a, b, -x).
+inline void two_prod(double a, double b, double& x, double& y) {
+  double p = fmul(a, b);
+  y = ffma(a, b, -p);
+  x = p;
+}
+
+// ---------------------------------------------------------------------------
+// Multi-word numbers.  W words, w[0] the leading one.
+// ---------------------------------------------------------------------------
+template <int W> struct MW { double w[W]; };
+
+// ---- FP64 (one word).  The paper's baseline CG-FP64; FMA is used wherever
+// a product is added to an accumulator (g++ -O3 -march=native contracts
+// a*b+c in the paper's build, Sec. V-A).
+struct FP64 {
+  static constexpr int W = 1;
+  using T = MW<1>;
+  static T zero() { return T{{0.0}}; }
+  static T from(double a) { return T{{a}}; }
+  static T add(const T& a, const T& b) { return T{{fadd(a.w[0], b.w[0])}}; }
+  static T mul(const T& a, const T& b) { return T{{fmul(a.w[0], b.w[0])}}; }
+  static T dxmul(double a, const T& b) { return T{{fmul(a, b.w[0])}}; }
+  static T muladd(const T& acc, const T& a, const T& b) { return T{{ffma(a.w[0], b.w[0], acc.w[0])}}; }
+  static T dxmuladd(const T& acc, double a, const T& b) { return T{{ffma(a, b.w[0], acc.w[0])}}; }
+  static T div(const T& a, const T& b) { return T{{fdiv(a.w[0], b.w[0])}}; }
+  static void normalize(T&) {}
+  static double collapse(const T& a) { return a.w[0]; }
+};
+
+// ---- DW, Dekker double-word (Algorithms 5 and 6).
+struct DW {
+  static constexpr int W = 2;
+  using T = MW<2>;
+  static T zero() { return T{{0.0, 0.0}}; }
+  static T from(double a) { return T{{a, 0.0}}; }
+  // Algorithm 5, DWadd: TwoSum(a1,b1); e = fl(e + a2 + b2) left to right; QuickTwoSum(s,e).
+  static T add(const T& a, const T& b) {
+    double s, e;
+    two_sum(a.w[0], b.w[0], s, e);
+    e = fadd(fadd(e, a.w[1]), b.w[1]);
+    T c;
+    quick_two_sum(s, e, c.w[0], c.w[1]);
+    return c;
+  }
+  // Algorithm 6, DWmul: TwoProdFMA(a1,b1); e = fma(a1,b2,e); e = fma(a2,b1,e); QuickTwoSum.
+  static T mul(const T& a, const T& b) {
+    double p, e;
+    two_prod(a.w[0], b.w[0], p, e);
+    e = ffma(a.w[0], b.w[1], e);
+    e = ffma(a.w[1], b.w[0], e);
+    T c;
+    quick_two_sum(p, e, c.w[0], c.w[1]);
+    return c;
+  }
+  // FP64 x DW (Sec. III, last paragraph): DWmul with a2 = 0 and the steps on
+  // the zero word dropped; fma(0, b1, e) = e, so only that FMA disappears.
+  static T dxmul(double a, const T& b) {
+    double p, e;
+    two_prod(a, b.w[0], p, e);
+    e = ffma(a, b.w[1], e);
+    T c;
+    quick_two_sum(p, e, c.w[0], c.w[1]);
+    return c;
+  }
+  static T muladd(const T& acc, const T& a, const T& b) { return add(acc, mul(a, b)); }
+  static T dxmuladd(const T& acc, double a, const T& b) { return add(acc, dxmul(a, b)); }
+  static T div(const T& a, const T& b);
+  static void normalize(T&) {}
+  static double collapse(const T& a) { return fadd(a.w[0], a.w[1]); }
+};
+
+// ---- QDW, quasi double-word (pair arithmetic): DW without the closing
+// QuickTwoSum (Sec. III, QDW paragraph).
+struct QDWbase {
+  static constexpr int W = 2;
+  using T = MW<2>;
+  static T zero() { return T{{0.0, 0.0}}; }
+  static T from(double a) { return T{{a, 0.0}}; }
+  static T add(const T& a, const T& b) {
+    T c;
+    two_sum(a.w[0], b.w[0], c.w[0], c.w[1]);
+    c.w[1] = fadd(fadd(c.w[1], a.w[1]), b.w[1]);
+    return c;
+  }
+  static T mul(const T& a, const T& b) {
+    T c;
+    two_prod(a.w[0], b.w[0], c.w[0], c.w[1]);
+    c.w[1] = ffma(a.w[0], b.w[1], c.w[1]);
+    c.w[1] = ffma(a.w[1], b.w[0], c.w[1]);
+    return c;
+  }
+  static T dxmul(double a, const T& b) {
+    T c;
+    two_prod(a, b.w[0], c.w[0], c.w[1]);
+    c.w[1] = ffma(a, b.w[1], c.w[1]);
+    return c;
+  }
+  static T muladd(const T& acc, const T& a, const T& b) { return add(acc, mul(a, b)); }
+  static T dxmuladd(const T& acc, double a, const T& b) { return add(acc, dxmul(a, b)); }
+  // QDW normalisation is QuickTwoSum(c1, c2) (Sec. III, normalisation paragraph).
+  static void renorm(T& a) { quick_two_sum(a.w[0], a.w[1], a.w[0], a.w[1]); }
+  static double collapse(const T& a) { return fadd(a.w[0], a.w[1]); }
+};
+struct QDW : QDWbase {
+  static T div(const T& a, const T& b);
+  static void normalize(T& a) { renorm(a); }   // Sec. IV-D: r is normalised after its AXPY
+};
+struct QDW_NN : QDWbase {                        // Sec. V-B3: no normalisation at all
+  static T div(const T& a, const T& b) { return QDW::div(a, b); }
+  static void normalize(T&) {}
+};
+
+// ---- QTW, quasi triple-word (Algorithms 7, 8, 9, 10).
+struct QTWbase {
+  static constexpr int W = 3;
+  using T = MW<3>;
+  static T zero() { return T{{0.0, 0.0, 0.0}}; }
+  static T from(double a) { return T{{a, 0.0, 0.0}}; }
+  // Algorithm 7, QTWadd.  c3 = fl(((a3 + b3) + e2) + e3), left to right.
+  static T add(const T& a, const T& b) {
+    T c;
+    double e1, e2, e3;
+    two_sum(a.w[0], b.w[0], c.w[0], e1);
+    two_sum(a.w[1], b.w[1], c.w[1], e2);
+    two_sum(c.w[1], e1, c.w[1], e3);
+    c.w[2] = fadd(fadd(fadd(a.w[2], b.w[2]), e2), e3);
+    return c;
+  }
+  // Algorithm 8, QTWmul.  c3 = fl(((f1 + f2) + f3) + e5) with
+  // f1 = fma(a3,b1,e2), f2 = fma(a2,b2,e3), f3 = fma(a1,b3,e4).
+  static T mul(const T& a, const T& b) {
+    T c;
+    double e1, t2, e2, t3, e3, e4, e5;
+    two_prod(a.w[0], b.w[0], c.w[0], e1);
+    two_prod(a.w[0], b.w[1], t2, e2);
+    two_prod(a.w[1], b.w[0], t3, e3);
+    two_sum(t2, t3, c.w[1], e4);
+    two_sum(c.w[1], e1, c.w[1], e5);
+    double f1 = ffma(a.w[2], b.w[0], e2);
+    double f2 = ffma(a.w[1], b.w[1], e3);
+    double f3 = ffma(a.w[0], b.w[2], e4);
+    c.w[2] = fadd(fadd(fadd(f1, f2), f3), e5);
+    return c;
+  }
+  // Algorithm 10, DxQTWmul (FP64 times QTW), exactly as printed.
+  static T dxmul(double a, const T& b) {
+    T c;
+    double e1, e2, e5;
+    two_prod(a, b.w[0], c.w[0], e1);
+    two_prod(a, b.w[1], c.w[1], e2);
+    two_sum(c.w[1], e1, c.w[1], e5);
+    c.w[2] = fadd(ffma(a, b.w[2], e2), e5);
+    return c;
+  }
+  static T muladd(const T& acc, const T& a, const T& b) { return add(acc, mul(a, b)); }
+  static T dxmuladd(const T& acc, double a, const T& b) { return add(acc, dxmul(a, b)); }
+  // Algorithm 9, VecSum3, as printed: TwoSum(c1,c2) then TwoSum(c2,c3).
+  static void renorm(T& a) {
+    two_sum(a.w[0], a.w[1], a.w[0], a.w[1]);
+    two_sum(a.w[1], a.w[2], a.w[1], a.w[2]);
+  }
+  // Collapse to FP64 lowest word first: fl(c1 + fl(c2 + c3)).
+  static double collapse(const T& a) { return fadd(a.w[0], fadd(a.w[1], a.w[2])); }
+};
+struct QTW : QTWbase {
+  static T div(const T& a, const T& b);
+  static void normalize(T& a) { renorm(a); }
+};
+struct QTW_NN : QTWbase {
+  static T div(const T& a, const T& b) { return QTW::div(a, b); }
+  static void normalize(T&) {}
+};
+
+// ---- TW, triple-word arithmetic.  The paper uses the addition and "fast"
+// multiplication of Fabiano, Muller and Picot (2019) but does not print them
+// (Sec. III, TW paragraph).  What follows is this project's restatement of
+// that scheme: error-free VecSum, then a renormalisation with branches that
+// skips zero errors ("tests").  Bit-level agreement with the original
+// sequences is therefore not claimed (parity unpinned for TW against the
+// cited work); accuracy and non-overlap are pinned by the tests.
+struct TW {
+  static constexpr int W = 3;
+  using T = MW<3>;
+  static T zero() { return T{{0.0, 0.0, 0.0}}; }
+  static T from(double a) { return T{{a, 0.0, 0.0}}; }
+
+  // Error-free VecSum, bottom-up: s = x[n-1]; (s, e[i+1]) = TwoSum(x[i], s).
+  static void vecsum(double* x, int n) {
+    double s = x[n - 1];
+    for (int i = n - 2; i >= 0; --i) {
+      double hi, lo;
+      two_sum(x[i], s, hi, lo);
+      x[i + 1] = lo;
+      s = hi;
+    }
+    x[0] = s;
+  }
+  // Renormalisation to three words.  A running value eps is combined with
+  // the next term by QuickTwoSum; a nonzero error closes the current output
+  // word, a zero error keeps accumulating into it.  Stops once three words
+  // are closed.
+  static T renorm3(const double* e, int n) {
+    double r[3] = {0.0, 0.0, 0.0};
+    int j = 0;
+    double eps = e[0];
+    for (int i = 0; i + 1 < n; ++i) {
+      double hi, lo;
+      quick_two_sum(eps, e[i + 1], hi, lo);
+      r[j] = hi;
+      if (lo != 0.0) {
+        if (j >= 2) return T{{r[0], r[1], r[2]}};
+        ++j;
+        eps = lo;
+      } else {
+        eps = hi;
+      }
+    }
+    r[j] = eps;
+    return T{{r[0], r[1], r[2]}};
+  }
+  static bool mag_ge(double a, double b) { return std::fabs(a) >= std::fabs(b); }
+  // TWadd: merge the six words by decreasing magnitude (ties: a first),
+  // VecSum, renormalise.
+  static T add(const T& a, const T& b) {
+    double z[6];
+    int i = 0, k = 0, m = 0;
+    while (m < 6) {
+      if (k >= 3 || (i < 3 && mag_ge(a.w[i], b.w[k]))) z[m++] = a.w[i++];
+      else z[m++] = b.w[k++];
+    }
+    vecsum(z, 6);
+    return renorm3(z, 6);
+  }
+  // Fast TWmul: the three order-1 and order-u products exactly, the order-u^2
+  // products folded into one FP64 sum, order-u^3 products dropped.
+  static T mul(const T& a, const T& b) {
+    double p00, e00, p01, e01, p10, e10;
+    two_prod(a.w[0], b.w[0], p00, e00);
+    two_prod(a.w[0], b.w[1], p01, e01);
+    two_prod(a.w[1], b.w[0], p10, e10);
+    double t, s3, s1, s2;
+    two_sum(p01, p10, t, s3);
+    two_sum(e00, t, s1, s2);
+    double c = fadd(s2, s3);
+    c = fadd(c, e01);
+    c = fadd(c, e10);
+    c = ffma(a.w[2], b.w[0], c);
+    c = ffma(a.w[1], b.w[1], c);
+    c = ffma(a.w[0], b.w[2], c);
+    double z[3] = {p00, s1, c};
+    vecsum(z, 3);
+    return renorm3(z, 3);
+  }
+  // FP64 x TW: mul((a,0,0), b) with the operations on zero words removed
+  // (each removal is an identity: TwoProd(0,x) = (0,0), TwoSum(x,0) = (x,0),
+  // x + 0 = x, fma(0,x,c) = c), so it equals the full product up to the sign
+  // of zero.
+  static T dxmul(double a, const T& b) {
+    double p00, e00, p01, e01;
+    two_prod(a, b.w[0], p00, e00);
+    two_prod(a, b.w[1], p01, e01);
+    double s1, s2;
+    two_sum(e00, p01, s1, s2);
+    double c = fadd(s2, e01);
+    c = ffma(a, b.w[2], c);
+    double z[3] = {p00, s1, c};
+    vecsum(z, 3);
+    return renorm3(z, 3);
+  }
+  static T muladd(const T& acc, const T& a, const T& b) { return add(acc, mul(a, b)); }
+  static T dxmuladd(const T& acc, double a, const T& b) { return add(acc, dxmul(a, b)); }
+  static T div(const T& a, const T& b);
+  static void normalize(T&) {}
+  static double collapse(const T& a) { return fadd(a.w[0], fadd(a.w[1], a.w[2])); }
+};
+
+template <class A> typename A::T neg(const typename A::T& a) {
+  typename A::T c;
+  for (int k = 0; k < A::W; ++k) c.w[k] = -a.w[k];
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Division.  CG needs it (Sec. III, first paragraph) but the paper gives no
+// algorithm.  Reading: long division in the arithmetic's own operations.
+//   q1 = fl(a1/b1); r = a - q1*b; q2 = fl(r1/b1); [w=3: r = r - q2*b; q3 = fl(r1/b1)]
+// then the quotient words are combined with the arithmetic's normalisation.
+// For the quasi arithmetics the remainder is normalised before its leading
+// word is read, because an unnormalised leading word can be far from the
+// value after cancellation.
+// ---------------------------------------------------------------------------
+MW<2> DW::div(const MW<2>& a, const MW<2>& b) {
+  double q1 = fdiv(a.w[0], b.w[0]);
+  MW<2> r = add(a, neg<DW>(dxmul(q1, b)));
+  double q2 = fdiv(r.w[0], b.w[0]);
+  MW<2> c;
+  quick_two_sum(q1, q2, c.w[0], c.w[1]);
+  return c;
+}
+MW<2> QDW::div(const MW<2>& a, const MW<2>& b) {
+  double q1 = fdiv(a.w[0], b.w[0]);
+  MW<2> r = add(a, neg<QDW>(dxmul(q1, b)));
+  renorm(r);
+  double q2 = fdiv(r.w[0], b.w[0]);
+  MW<2> c;
+  quick_two_sum(q1, q2, c.w[0], c.w[1]);
+  return c;
+}
+MW<3> QTW::div(const MW<3>& a, const MW<3>& b) {
+  double q1 = fdiv(a.w[0], b.w[0]);
+  MW<3> r = add(a, neg<QTW>(dxmul(q1, b)));
+  renorm(r);
+  double q2 = fdiv(r.w[0], b.w[0]);
+  r = add(r, neg<QTW>(dxmul(q2, b)));
+  renorm(r);
+  double q3 = fdiv(r.w[0], b.w[0]);
+  MW<3> c{{q1, q2, q3}};
+  renorm(c);
+  return c;
+}
+MW<3> TW::div(const MW<3>& a, const MW<3>& b) {
+  double q1 = fdiv(a.w[0], b.w[0]);
+  MW<3> r = add(a, neg<TW>(dxmul(q1, b)));
+  double q2 = fdiv(r.w[0], b.w[0]);
+  r = add(r, neg<TW>(dxmul(q2, b)));
+  double q3 = fdiv(r.w[0], b.w[0]);
+  double z[3] = {q1, q2, q3};
+  vecsum(z, 3);
+  return renorm3(z, 3);
+}
+
+// ---------------------------------------------------------------------------
+// SoA vectors: word k of element i at v[k*n + i].
+// ---------------------------------------------------------------------------
+template <class A> inline typename A::T load(const double* v, int64_t n, int64_t i) {
+  typename A::T t;
+  for (int k = 0; k < A::W; ++k) t.w[k] = v[k * n + i];
+  return t;
+}
+template <class A> inline void store(double* v, int64_t n, int64_t i, const typename A::T& t) {
+  for (int k = 0; k < A::W; ++k) v[k * n + i] = t.w[k];
+}
+
+// ---------------------------------------------------------------------------
+// Summation orders.
+//   plain (V == 0): each row summed left to right over its entries; a dot is
+//     the left-to-right accumulation acc = acc (+) u_i*v_i from acc = u_0*v_0
+//     (FMA for FP64).  This is the literal reading of Algorithm 1.
+//   mirrored (V > 0): the order the CUDA kernels use, a function of the plan
+//     {V lanes per row, T threads per block, G blocks}:
+//     * row i: lane l (0 <= l < V) owns entries row_start + l + jV, j = 0,1,..
+//       and sums their products left to right starting from its first
+//       product; lanes without entries are absent; lanes are combined by the
+//       pairwise tree below.
+//     * dot: leaf i is u_i (x) v_i; rows are cut into tiles of R consecutive
+//       rows (R = T/V in the SpMV, R = T in the vector kernels); a tile's
+//       leaves are combined by the pairwise tree; tile t belongs to block
+//       t mod G, which adds its tiles left to right in increasing t; the G
+//       block values are combined by the pairwise tree (absent blocks skipped).
+//   Pairwise tree over slots 0..S-1: for h = 1, 2, 4, ... < S, every slot s
+//   that is a multiple of 2h takes v[s] = v[s] (+) v[s+h] when both are
+//   present (just v[s+h] if only that one is); result in slot 0.
+// ---------------------------------------------------------------------------
+template <class A>
+void pair_tree(std::vector<typename A::T>& v, std::vector<char>& present) {
+  size_t S = v.size();
+  for (size_t h = 1; h < S; h <<= 1) {
+    for (size_t s = 0; s + h < S; s += 2 * h) {
+      if (!present[s + h]) continue;
+      if (present[s]) v[s] = A::add(v[s], v[s + h]);
+      else { v[s] = v[s + h]; present[s] = 1; }
+    }
+  }
+}
+
+struct Plan { int V; int T; int G; };
+
+template <class A>
+typename A::T spmv_row(const int64_t* rp, const int32_t* col, const double* val,
+                       const double* p, int64_t n, int64_t i, int V) {
+  using T = typename A::T;
+  int64_t s = rp[i], e = rp[i + 1];
+  if (s == e) return A::zero();
+  if (V <= 1) {
+    T acc = A::dxmul(val[s], load<A>(p, n, col[s]));
+    for (int64_t k = s + 1; k < e; ++k) acc = A::dxmuladd(acc, val[k], load<A>(p, n, col[k]));
+    return acc;
+  }
+  std::vector<T> lane(V);
+  std::vector<char> present(V, 0);
+  for (int l = 0; l < V; ++l) {
+    int64_t k = s + l;
+    if (k >= e) continue;
+    T acc = A::dxmul(val[k], load<A>(p, n, col[k]));
+    for (k += V; k < e; k += V) acc = A::dxmuladd(acc, val[k], load<A>(p, n, col[k]));
+    lane[l] = acc;
+    present[l] = 1;
+  }
+  pair_tree<A>(lane, present);
+  return lane[0];
+}
+
+template <class A>
+void spmv(const int64_t* rp, const int32_t* col, const double* val, const double* p,
+          double* q, int64_t n, int V) {
+  for (int64_t i = 0; i < n; ++i) store<A>(q, n, i, spmv_row<A>(rp, col, val, p, n, i, V));
+}
+
+// Reduce per-row leaves (already computed) in the plain or mirrored order.
+template <class A>
+typename A::T reduce_leaves(const std::vector<typename A::T>& leaf, int64_t R, int G, bool plain,
+                            const double* u, const double* v, int64_t n) {
+  using T = typename A::T;
+  if (n == 0) return A::zero();
+  if (plain) {
+    T acc = A::mul(load<A>(u, n, 0), load<A>(v, n, 0));
+    for (int64_t i = 1; i < n; ++i) acc = A::muladd(acc, load<A>(u, n, i), load<A>(v, n, i));
+    return acc;
+  }
+  int64_t ntiles = (n + R - 1) / R;
+  std::vector<T> blk(G);
+  std::vector<char> bpres(G, 0);
+  for (int64_t t = 0; t < ntiles; ++t) {
+    int64_t r0 = t * R;
+    int64_t cnt = std::min<int64_t>(R, n - r0);
+    std::vector<T> sl(R);
+    std::vector<char> pr(R, 0);
+    for (int64_t s = 0; s < cnt; ++s) { sl[s] = leaf[r0 + s]; pr[s] = 1; }
+    pair_tree<A>(sl, pr);
+    int b = (int)(t % G);
+    if (bpres[b]) blk[b] = A::add(blk[b], sl[0]);
+    else { blk[b] = sl[0]; bpres[b] = 1; }
+  }
+  pair_tree<A>(blk, bpres);
+  return blk[0];
+}
+
+template <class A>
+typename A::T dot(const double* u, const double* v, int64_t n, int64_t R, int G, bool plain) {
+  std::vector<typename A::T> leaf;
+  if (!plain) {
+    leaf.resize(n);
+    for (int64_t i = 0; i < n; ++i) leaf[i] = A::mul(load<A>(u, n, i), load<A>(v, n, i));
+  }
+  return reduce_leaves<A>(leaf, R, G, plain, u, v, n);
+}
+
+// ||b||_2^2 in FP64 (Sec. IV-C: the relative residual is an FP64 quantity).
+double bnorm2(const double* b, int64_t n, int64_t R, int G, bool plain) {
+  return dot<FP64>(b, b, n, R, G, plain).w[0];
+}
+
+enum { ST_CONVERGED = 0, ST_MAXIT = 1, ST_BREAKDOWN = 2 };
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 in arithmetic A.
+// Readings (the paper leaves these open):
+//  * r0 = b - A x0 is formed as (b, 0, ..) (+) (-(A x0)); it is not
+//    normalised (Sec. IV-D normalises only after the r-AXPY of the loop).
+//  * ||b|| = 0: x = 0, zero iterations.  r0 = 0 exactly (all words zero):
+//    x0 is returned with zero iterations.
+//  * One pass of the loop counts as one iteration, including the pass that
+//    breaks.  The stop test is strict (<) and comes after rho_{i+1}, before
+//    beta (Algorithm 1, lines 9-12).
+//  * The FP64 relative residual is sqrt(collapse(rho_{i+1})) / ||b||_2, with
+//    collapse summing the words lowest first and ||b|| from an FP64 dot.
+//  * Breakdown: collapse(p^T q) not > 0 (covers NaN), or a non-finite
+//    residual, ends the solve with status 2.
+//  * maxit <= 0 returns x0 with status 1.
+//  * Order of operands: x (+) alpha*p, r (+) (-alpha)*q, r (+) beta*p, a dot
+//    leaf is u_i*v_i; negation flips every word (exact).
+// ---------------------------------------------------------------------------
+struct CGResult { int status; int iters; double relres; };
+
+template <class A>
+CGResult cg(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+            const double* b, double* x, double tol, int maxit, Plan plan, double* hist) {
+  using T = typename A::T;
+  const int W = A::W;
+  const bool plain = plan.V <= 0;
+  const int V = plain ? 1 : plan.V;
+  const int64_t Rs = plain ? 1 : std::max(1, plan.T / V);
+  const int64_t Rv = plain ? 1 : plan.T;
+  const int G = plain ? 1 : plan.G;
+  CGResult res{ST_CONVERGED, 0, 0.0};
+
+  double bn = fsqrt(bnorm2(b, n, Rv, G, plain));
+  if (bn == 0.0) {
+    for (int64_t i = 0; i < W * n; ++i) x[i] = 0.0;
+    return res;
+  }
+  std::vector<double> r(W * n), p(W * n), q(W * n);
+  spmv<A>(rp, col, val, x, q.data(), n, V);
+  for (int64_t i = 0; i < n; ++i) {
+    T bi = A::from(b[i]);
+    T ri = A::add(bi, neg<A>(load<A>(q.data(), n, i)));
+    store<A>(r.data(), n, i, ri);
+  }
+  p = r;
+  T rho = dot<A>(r.data(), r.data(), n, Rv, G, plain);
+  bool rzero = true;
+  for (int k = 0; k < W; ++k) rzero = rzero && (rho.w[k] == 0.0);
+  double relres = fdiv(fsqrt(A::collapse(rho)), bn);
+  res.relres = relres;
+  if (rzero) { res.relres = 0.0; return res; }
+  if (maxit <= 0) { res.status = ST_MAXIT; return res; }
+
+  for (;;) {
+    spmv<A>(rp, col, val, p.data(), q.data(), n, V);
+    T pq = dot<A>(p.data(), q.data(), n, Rs, G, plain);
+    res.iters += 1;
+    double pqc = A::collapse(pq);
+    if (!(pqc > 0.0) || !std::isfinite(pqc)) { res.status = ST_BREAKDOWN; return res; }
+    T alpha = A::div(rho, pq);
+    T malpha = neg<A>(alpha);
+    for (int64_t i = 0; i < n; ++i) {
+      store<A>(x, n, i, A::muladd(load<A>(x, n, i), alpha, load<A>(p.data(), n, i)));
+      T ri = A::muladd(load<A>(r.data(), n, i), malpha, load<A>(q.data(), n, i));
+      A::normalize(ri);
+      store<A>(r.data(), n, i, ri);
+    }
+    T rho1 = dot<A>(r.data(), r.data(), n, Rv, G, plain);
+    relres = fdiv(fsqrt(A::collapse(rho1)), bn);
+    res.relres = relres;
+    if (hist) hist[res.iters - 1] = relres;
+    if (relres < tol) { res.status = ST_CONVERGED; return res; }
+    if (!std::isfinite(relres)) { res.status = ST_BREAKDOWN; return res; }
+    if (res.iters >= maxit) { res.status = ST_MAXIT; return res; }
+    T beta = A::div(rho1, rho);
+    for (int64_t i = 0; i < n; ++i)
+      store<A>(p.data(), n, i, A::muladd(load<A>(r.data(), n, i), beta, load<A>(p.data(), n, i)));
+    rho = rho1;
+  }
+}
+
+// Gradient of L = w^T x through A x = b (values only, sparsity kept):
+// dL/dval_k = -lambda_row(k) * x_col(k), lambda the adjoint solution, formed
+// as the arithmetic's product lambda_i * x_j and collapsed to FP64.
+template <class A>
+void grad_values(int64_t n, const int64_t* rp, const int32_t* col, const double* lam,
+                 const double* x, double* g) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      g[k] = -A::collapse(A::mul(load<A>(lam, n, i), load<A>(x, n, col[k])));
+}
+
+// Arithmetic dispatch: 0 FP64, 1 DW, 2 QDW, 3 TW, 4 QTW, 5 QDW-NN, 6 QTW-NN.
+template <template <class> class F, class... Args>
+int dispatch(int arith, Args... args) {
+  switch (arith) {
+    case 0: return F<FP64>::run(args...);
+    case 1: return F<DW>::run(args...);
+    case 2: return F<QDW>::run(args...);
+    case 3: return F<TW>::run(args...);
+    case 4: return F<QTW>::run(args...);
+    case 5: return F<QDW_NN>::run(args...);
+    case 6: return F<QTW_NN>::run(args...);
+  }
+  return -1;
+}
+
+template <class A> struct OpAdd {
+  static int run(int64_t n, const double* a, const double* b, double* c) {
+    for (int64_t i = 0; i < n; ++i) store<A>(c, n, i, A::add(load<A>(a, n, i), load<A>(b, n, i)));
+    return 0;
+  }
+};
+template <class A> struct OpMul {
+  static int run(int64_t n, const double* a, const double* b, double* c) {
+    for (int64_t i = 0; i < n; ++i) store<A>(c, n, i, A::mul(load<A>(a, n, i), load<A>(b, n, i)));
+    return 0;
+  }
+};
+template <class A> struct OpDiv {
+  static int run(int64_t n, const double* a, const double* b, double* c) {
+    for (int64_t i = 0; i < n; ++i) store<A>(c, n, i, A::div(load<A>(a, n, i), load<A>(b, n, i)));
+    return 0;
+  }
+};
+template <class A> struct OpDx {
+  static int run(int64_t n, const double* a, const double* b, double* c) {
+    for (int64_t i = 0; i < n; ++i) store<A>(c, n, i, A::dxmul(a[i], load<A>(b, n, i)));
+    return 0;
+  }
+};
+template <class A> struct OpNorm {
+  static int run(int64_t n, const double* a, const double* b, double* c) {
+    (void)b;
+    for (int64_t i = 0; i < n; ++i) {
+      auto t = load<A>(a, n, i);
+      A::normalize(t);
+      store<A>(c, n, i, t);
+    }
+    return 0;
+  }
+};
+template <class A> struct OpCollapse {
+  static int run(int64_t n, const double* a, const double* b, double* c) {
+    (void)b;
+    for (int64_t i = 0; i < n; ++i) c[i] = A::collapse(load<A>(a, n, i));
+    return 0;
+  }
+};
+template <class A> struct OpSpmv {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* p, double* q, int V) {
+    spmv<A>(rp, col, val, p, q, n, V);
+    return 0;
+  }
+};
+template <class A> struct OpDot {
+  static int run(int64_t n, const double* u, const double* v, double* out, int64_t R, int G) {
+    auto t = dot<A>(u, v, n, R, G, R <= 0);
+    for (int k = 0; k < A::W; ++k) out[k] = t.w[k];
+    return 0;
+  }
+};
+template <class A> struct OpCG {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                 int* iters, double* relres, double* hist) {
+    CGResult r = cg<A>(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist);
+    *iters = r.iters;
+    *relres = r.relres;
+    return r.status;
+  }
+};
+template <class A> struct OpGrad {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* lam,
+                 const double* x, double* g) {
+    grad_values<A>(n, rp, col, lam, x, g);
+    return 0;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C exports (loaded by the tests through ctypes).
+// Arrays of multi-word values are SoA: word k of element i at [k*n + i].
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void orc_ops_reset(void) { g_ops = 0; }
+uint64_t orc_ops_get(void) { return g_ops; }
+
+void orc_two_sum(int64_t n, const double* a, const double* b, double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) two_sum(a[i], b[i], x[i], y[i]);
+}
+void orc_quick_two_sum(int64_t n, const double* a, const double* b, double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) quick_two_sum(a[i], b[i], x[i], y[i]);
+}
+void orc_two_prod(int64_t n, const double* a, const double* b, double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) two_prod(a[i], b[i], x[i], y[i]);
+}
+void orc_vecsum3(int64_t n, const double* a, double* c) {   // Algorithm 9 alone
+  for (int64_t i = 0; i < n; ++i) {
+    MW<3> t = load<QTW>(a, n, i);
+    QTW::renorm(t);
+    store<QTW>(c, n, i, t);
+  }
+}
+int orc_add(int arith, int64_t n, const double* a, const double* b, double* c) {
+  return dispatch<OpAdd>(arith, n, a, b, c);
+}
+int orc_mul(int arith, int64_t n, const double* a, const double* b, double* c) {
+  return dispatch<OpMul>(arith, n, a, b, c);
+}
+int orc_div(int arith, int64_t n, const double* a, const double* b, double* c) {
+  return dispatch<OpDiv>(arith, n, a, b, c);
+}
+int orc_dxmul(int arith, int64_t n, const double* a, const double* b, double* c) {
+  return dispatch<OpDx>(arith, n, a, b, c);
+}
+int orc_normalize(int arith, int64_t n, const double* a, double* c) {
+  return dispatch<OpNorm>(arith, n, a, (const double*)nullptr, c);
+}
+int orc_collapse(int arith, int64_t n, const double* a, double* c) {
+  return dispatch<OpCollapse>(arith, n, a, (const double*)nullptr, c);
+}
+int orc_spmv(int arith, int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+             const double* p, double* q, int V) {
+  return dispatch<OpSpmv>(arith, n, rp, col, val, p, q, V);
+}
+int orc_dot(int arith, int64_t n, const double* u, const double* v, double* out, int64_t R, int G) {
+  return dispatch<OpDot>(arith, n, u, v, out, R, G);
+}
+// Mirrored order when V > 0 (plan {V, T, G}), plain order when V <= 0.
+int orc_cg(int arith, int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+           const double* b, double* x, double tol, int maxit, int V, int T, int G,
+           int* iters, double* relres, double* hist) {
+  return dispatch<OpCG>(arith, n, rp, col, val, b, x, tol, maxit, V, T, G, iters, relres, hist);
+}
+int orc_grad_values(int arith, int64_t n, const int64_t* rp, const int32_t* col,
+                    const double* lam, const double* x, double* g) {
+  return dispatch<OpGrad>(arith, n, rp, col, lam, x, g);
+}
+int orc_words(int arith) {
+  static const int w[7] = {1, 2, 2, 3, 3, 2, 3};
+  return (arith >= 0 && arith < 7) ? w[arith] : -1;
+}
+
+}  // extern "C"
