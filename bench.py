@@ -1,0 +1,337 @@
+"""Benchmark: QTW-CG time to relative residual 1e-14 on the 128^3 7-point Poisson system.
+
+One step = one complete solve (initialisation + CG iterations until the FP64
+relative residual drops below 1e-14) of the 3-D Poisson system (n = 2,097,152,
+nnz = 14,581,760, b = 2U-1 seeded, x0 = 0) in quasi triple-word arithmetic,
+through the C ABI (mwcg_solve).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mwcg|reference]
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload (a few CG iterations per step) and extrapolates to the
+oracle's own iteration count for the full solve (tests/golden/fullsize_c2.json,
+written from the oracle).  The solver has a single-GPU path; with N > 1
+(torchrun) every rank solves its own replica and rank 0 reports the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "QTW-CG time-to-1e-14 residual (3-D Poisson 128^3, 7-point)"
+WORKLOAD = "c2"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_c2.json")
+# FP64 peak of the GB300 for the ALU roofline: 2 FP64 operations per clock per
+# SM (FMA counted as one operation, as the paper counts), 152 SMs, 2070 MHz.
+FP64_OPS_PER_CLK_SM = 2
+SMS = 152
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_OPS = FP64_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6
+# FP64 operations (FMA = 1) per stored entry and per row of the fused SpMV + p^T q
+# kernel: FP64 x MW product + MW add per entry, minus the add saved on each
+# row's first product, plus the dot leaf (MW product) and its accumulation.
+SPMV_OPS = {  # arith: (per nnz, per row)
+    "fp64": (1, 1 + 1),
+    "dw": (6 + 11, 7 + 11 - 11),
+    "qdw": (3 + 8, 4 + 8 - 8),
+    "qtw": (12 + 21, 24 + 21 - 21),
+}
+WORDS = {"fp64": 1, "dw": 2, "qdw": 2, "qtw": 3, "tw": 3}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rk = int(os.environ.get("RANK", "0"))
+    return ws, rk
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None], default=None)}
+
+
+def _golden_iters(arith):
+    try:
+        g = json.load(open(GOLDEN))
+        return int(g[arith]["iters"]), "oracle full solve (tests/golden/fullsize_c2.json)"
+    except Exception:
+        return None, None
+
+
+def oracle_sample(A, b, arith, iters_sample, total_iters):
+    """Time the CPU oracle (single thread) on `iters_sample` iterations of the
+    workload and scale to `total_iters` iterations.  Returns (seconds, per_iter, detail)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.cg(arith, A, b, tol=0.0, maxit=1, plan=(1, 256, 304))
+    t_init1 = time.perf_counter() - t0                      # init + 1 iteration
+    t0 = time.perf_counter()
+    oracle.cg(arith, A, b, tol=0.0, maxit=1 + iters_sample, plan=(1, 256, 304))
+    t_run = time.perf_counter() - t0                        # init + 1 + k iterations
+    per_it = max(t_run - t_init1, 1e-9) / iters_sample
+    init = max(t_init1 - per_it, 0.0)
+    return init + per_it * total_iters, per_it, init
+
+
+def run_reference(args):
+    ws, rk = _dist()
+    if rk != 0:
+        return 0
+    from paper_2510_13536_gb300 import problems as P
+    A, b, tol, maxit = P.workload(WORKLOAD)
+    iters, src = _golden_iters("qtw")
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration count for the full solve missing "
+                                                               "(tests/golden/fullsize_c2.json)"}))
+        return 0
+    vals = []
+    for s in range(args.warmup + args.steps):
+        est, per_it, init = oracle_sample(A, b, "qtw", 2, iters)
+        if s >= args.warmup:
+            vals.append(est)
+    v = statistics.median(vals)
+    cb = {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+          "sample": f"2 QTW CG iterations of the full 128^3 system per step (plus init), single thread, "
+                    f"scaled to {iters} iterations ({src})"}
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD + ": " + P.WORKLOADS[WORKLOAD], "arith": "qtw", "tol": tol},
+           "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rk = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2510_13536_gb300 import build as _build
+    _build.build()
+    from paper_2510_13536_gb300 import problems as P
+    from paper_2510_13536_gb300 import solver as mw
+
+    A, b_np, tol, maxit = P.workload(WORKLOAD)
+    M = mw.CSRMatrix.from_csr(A)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    b = torch.as_tensor(b_np, device=dev)
+    arith = args.arith
+    w = WORDS[arith]
+    x = torch.zeros((w, A.n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one_solve(ar=arith, xx=None):
+        xx = x if xx is None else xx
+        xx.zero_()
+        return mw.solve(M, b, ar, tol, maxit, x0=xx)
+
+    for _ in range(args.warmup):
+        r = one_solve()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    iters = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for s in range(args.steps):
+            x.zero_()
+            starts[s].record(stream)
+            r = mw.solve(M, b, arith, tol, maxit, x0=x)
+            ends[s].record(stream)
+            iters.append(r.iters)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(args.steps)]
+    ms = statistics.mean(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    it = iters[-1]
+    status, relres = r.status, r.relres
+
+    # DW solve of the same system (QTW / DW time ratio).
+    xdw = torch.zeros((2, A.n), dtype=torch.float64, device=dev)
+    one_solve("dw", xdw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dw_ms = []
+    dw_it = 0
+    for _ in range(2):
+        xdw.zero_()
+        e0.record(stream)
+        rd = mw.solve(M, b, "dw", tol, maxit, x0=xdw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dw_ms.append(e0.elapsed_time(e1))
+        dw_it = rd.iters
+
+    # Per-kernel durations (CUDA events around each launch, no graph).
+    import ctypes
+    from paper_2510_13536_gb300 import _capi
+    kms = (ctypes.c_double * 3)()
+    x.zero_()
+    _capi.check(_capi.load().mwcg_profile_kernels(M.handle, ctypes.c_void_p(b.data_ptr()),
+                                                  ctypes.c_void_p(x.data_ptr()), mw.arith_id(arith), 30,
+                                                  ctypes.c_void_p(stream.cuda_stream), kms))
+    spmv_ms = kms[0]
+    per_nnz, per_row = SPMV_OPS[arith]
+    ops = per_nnz * A.nnz + per_row * A.n
+    achieved = ops / (spmv_ms * 1e-3)
+    spmv_bytes = 12 * A.nnz + 8 * (A.n + 1) + 2 * 8 * w * A.n
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "k_spmv_qtw_c2_traffic.json")))
+        traffic = prof.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+
+    # End to end through the C ABI with host buffers (pinned), copies included.
+    bh = torch.empty(A.n, dtype=torch.float64, pin_memory=True)
+    bh.copy_(torch.as_tensor(b_np))
+    xh = torch.zeros((w, A.n), dtype=torch.float64, pin_memory=True)
+    e2e_s = []
+    for _ in range(2):
+        xh.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _xh, ith, rrh, sth = mw.solve_host(M, bh.numpy(), arith, tol, maxit, x0=xh.numpy())
+        e2e_s.append(time.perf_counter() - t0)
+    e2e = {"value": min(e2e_s), "unit": "s", "h2d_bytes_per_step": 8 * A.n + 8 * w * A.n,
+           "d2h_bytes_per_step": 8 * w * A.n + 160}
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only).
+    cpu = None
+    if rk == 0 and ws == 1 and not args.no_cpu:
+        gi, src = _golden_iters(arith)
+        tot = gi if gi is not None else it
+        src = src or "iteration count of this run (oracle count missing)"
+        est, per_it, init = oracle_sample(A, b_np, arith, 2, tot)
+        cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"2 CG iterations + init of the full system, single thread, scaled to {tot} iterations "
+                         f"({src}); {per_it:.3f} s per iteration"}
+
+    alg_bytes_iter = 12 * A.nnz + 8 * (A.n + 1) + 88 * w * A.n
+    out = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + ": " + P.WORKLOADS[WORKLOAD], "arith": arith, "tol": tol,
+                   "maxit": maxit, "plan": list(M.plan), "parallelism": "replicas only" if ws > 1 else "1 GPU",
+                   "l2": "working set (CSR 192 MB + 4 vectors of 50 MB) larger than the 129 MB L2"},
+        "iters": it, "status": status, "relres": relres, "iters_per_s": it / (ms / 1e3),
+        "hbm_gbs_algorithmic": alg_bytes_iter * it / (ms / 1e3) / 1e9,
+        "dw": {"time_s": min(dw_ms) / 1e3, "iters": dw_it},
+        "qtw_over_dw_time": (ms / min(dw_ms)) if arith == "qtw" else None,
+        "kernel_ms": {"spmv_dot": kms[0], "update_dot": kms[1], "p_update": kms[2]},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": args.steps * (3 + 3 * it),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
+                     "unit": "TFLOP64-op/s (FMA = 1)", "frac": achieved / FP64_PEAK_OPS, "traffic": traffic,
+                     "kernel": "k_spmv<QTW> (SpMV + p^T q + alpha)", "ops_per_launch": ops,
+                     "alg_bytes_per_launch": spmv_bytes,
+                     "hbm_frac_of_measured": spmv_bytes / (spmv_ms * 1e-3) / 6691.8e9,
+                     "peak_source": "2 FP64 op/clk/SM x 152 SMs x 2070 MHz (microbenchmark: 2.06 DFMA/clk/SM)"},
+        "cpu_baseline": cpu,
+    }
+    if rk == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mwcg", choices=["mwcg", "reference"])
+    ap.add_argument("--arith", default="qtw", choices=["qtw", "dw", "qdw", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * mwcg.h -- C ABI of the GB300 (sm_103a) multi-word-arithmetic CG solver.
+ *
+ * The solver runs the Conjugate Gradient method (Algorithm 1 of Mukunoki and
+ * Ozaki, "Sparse Iterative Solvers Using High-Precision Arithmetic with Quasi
+ * Multi-Word Algorithms") on a sparse symmetric positive definite matrix
+ * stored as FP64 CSR, with every vector and scalar of the iteration held in
+ * one of five arithmetics built from FP64 words (Sec. III): FP64, DW
+ * (double-word), QDW (quasi double-word), TW (triple-word) and QTW (quasi
+ * triple-word), plus the unnormalised quasi variants of Sec. V-B3.  A and b
+ * are FP64 (Sec. IV-C); the stopping residual is computed in FP64 (Sec.
+ * IV-C); the quasi arithmetics normalise r once per iteration after its AXPY
+ * (Sec. IV-D).
+ *
+ * Conventions for every function:
+ *  - Multi-word vectors are structure of arrays: a vector of n elements in an
+ *    arithmetic with w words (mwcg_words) is a double[w*n] with word k of
+ *    element i at [k*n + i]; word 0 is the leading word.
+ *  - "device" pointers are CUDA global-memory pointers of the current device;
+ *    "host" pointers are ordinary (preferably pinned) host memory.
+ *  - Work is ordered on the caller's CUDA stream (`stream`, a cudaStream_t;
+ *    NULL is the legacy default stream).  Functions that return results on
+ *    the host synchronise that stream once before returning.
+ *  - Return codes: MWCG_OK (0) or a positive solver status, or a negative
+ *    error code; mwcg_last_error() then gives a message (thread-local).
+ *  - A matrix handle owns its device copy of the matrix and the solver
+ *    workspace.  One solve at a time per handle (the workspace is shared);
+ *    distinct handles may be used concurrently.
+ */
+#ifndef MWCG_H
+#define MWCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Arithmetics (Sec. III).  *_NN: quasi arithmetic without the per-iteration
+ * normalisation of r (Sec. V-B3, "CG-QDW-NN", "CG-QTW-NN"). */
+typedef enum {
+  MWCG_FP64 = 0,
+  MWCG_DW = 1,
+  MWCG_QDW = 2,
+  MWCG_TW = 3,
+  MWCG_QTW = 4,
+  MWCG_QDW_NN = 5,
+  MWCG_QTW_NN = 6
+} mwcg_arith;
+
+/* Solver status (>= 0) and error codes (< 0). */
+enum {
+  MWCG_OK = 0,              /* converged: relres < tol                                  */
+  MWCG_NOT_CONVERGED = 1,   /* maxit iterations done without reaching tol               */
+  MWCG_BREAKDOWN = 2,       /* collapse(p^T q) not > 0, or a non-finite residual        */
+  MWCG_ERR_ARG = -1,        /* invalid argument (sizes, pointers, CSR structure, plan)  */
+  MWCG_ERR_CUDA = -2,       /* a CUDA runtime call failed                               */
+  MWCG_ERR_GUARD = -3,      /* device loop guard tripped (internal consistency failure) */
+  MWCG_ERR_NOMEM = -4       /* device allocation failed                                 */
+};
+
+/* Summation plan of the kernels.  It fixes the order of every FP64 operation
+ * and hence the result bits:
+ *   V  lanes per CSR row in the SpMV (1, 2, 4, 8, 16 or 32); lane l of a row
+ *      owns entries row_start + l + jV and the V lane sums are combined by a
+ *      pairwise tree;
+ *   T  threads per block (fixed at 256);
+ *   G  blocks (1..1024); rows are cut into tiles of T/V (SpMV) or T (vector
+ *      kernels) rows, tile t belongs to block t mod G, each block slot sums
+ *      its rows across the block's tiles in increasing order, then slots and
+ *      blocks are combined by pairwise trees.
+ * mwcg_create_csr picks the plan from the row-length distribution; tests
+ * read it with mwcg_get_plan and may pin one with mwcg_set_plan. */
+typedef struct {
+  int32_t V;
+  int32_t T;
+  int32_t G;
+} mwcg_plan;
+
+typedef struct mwcg_csr mwcg_csr;
+
+/* Number of FP64 words of an arithmetic (1, 2 or 3), or -1 if unknown. */
+int mwcg_words(int arith);
+
+/* Message of the last error on this thread ("" if none).  Owned by the
+ * library, valid until the next call on this thread. */
+const char* mwcg_last_error(void);
+
+/* Copy a CSR matrix to the device and build its solver handle.
+ *   n        rows = columns (n >= 0);
+ *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz;
+ *   col      int32[nnz], 0 <= col < n (any order within a row);
+ *   val      double[nnz], finite;
+ *   ptrs_on_device  0: the three arrays are host memory, 1: device memory;
+ *   out      receives the handle (caller frees it with mwcg_destroy_csr).
+ * The structure is validated on the host (device arrays are copied back for
+ * that); violations return MWCG_ERR_ARG.  Symmetry is not checked: the paper
+ * stores symmetric matrices in general form (Sec. IV-B) and so does the
+ * caller.  The arrays are copied; the caller keeps ownership of them. */
+int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                    int ptrs_on_device, void* stream, mwcg_csr** out);
+
+/* Release a handle and its device memory (NULL is ignored). */
+void mwcg_destroy_csr(mwcg_csr* A);
+
+/* Replace the values of A (same sparsity pattern); val is double[nnz] on the
+ * host (on_device = 0) or device (1).  Non-finite values: MWCG_ERR_ARG. */
+int mwcg_update_values(mwcg_csr* A, const double* val, int on_device, void* stream);
+
+int64_t mwcg_n(const mwcg_csr* A);
+int64_t mwcg_nnz(const mwcg_csr* A);
+int mwcg_get_plan(const mwcg_csr* A, mwcg_plan* out);
+/* Pin a plan (V power of two in 1..32, T = 256, G in 1..1024); MWCG_ERR_ARG otherwise. */
+int mwcg_set_plan(mwcg_csr* A, const mwcg_plan* plan);
+
+/* Solve A x = b by CG in the given arithmetic (Algorithm 1).
+ *   b        device double[n];
+ *   x        device double[w*n] (w = mwcg_words(arith)): x0 on entry, the
+ *            multi-word solution on return;
+ *   tol      stop when sqrt(collapse(r^T r)) / ||b||_2 < tol (FP64, Sec. IV-C);
+ *   maxit    iteration limit, 0 <= maxit <= 2^30 (0 returns x0 with status 1);
+ *   iters_out, relres_out (host, may be NULL): iterations done (the pass that
+ *            stops counts) and the last relative residual.
+ * Returns MWCG_OK, MWCG_NOT_CONVERGED, MWCG_BREAKDOWN or an error.  b = 0
+ * gives x = 0 and zero iterations; an exact x0 (r0 = 0) zero iterations.
+ * The whole solve (initialisation and the loop) is one CUDA graph launch
+ * whose loop is a device-side while node; the stream is synchronised once
+ * at the end to read the iteration count and residual. */
+int mwcg_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, void* stream,
+               int32_t* iters_out, double* relres_out);
+
+/* mwcg_solve with host buffers: b_host double[n], x_host double[w*n] (x0 in,
+ * solution out).  The copies to and from the device are part of the call. */
+int mwcg_solve_host(mwcg_csr* A, const double* b_host, double* x_host, int arith, double tol, int32_t maxit,
+                    void* stream, int32_t* iters_out, double* relres_out);
+
+/* Like mwcg_solve, and also writes the FP64 relative residual after every
+ * iteration to hist (device double[maxit]); entries past the last iteration
+ * are left untouched. */
+int mwcg_solve_history(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit,
+                       double* hist, void* stream, int32_t* iters_out, double* relres_out);
+
+/* Solve many independent systems in one persistent kernel launch.
+ *   nsys             number of systems;
+ *   A[s]             handles (distinct or repeated);
+ *   b[s], x[s]       device pointers as in mwcg_solve (x[s] holds
+ *                    mwcg_words(arith[s]) * n_s doubles, x0 on entry);
+ *   arith[s], tol[s], maxit[s]  per system (host arrays);
+ *   iters_out[s], relres_out[s], status_out[s]  host arrays (may be NULL).
+ * Each system runs the same iteration, in the same summation order as
+ * mwcg_solve with plan {1, 256, 1} on that matrix (one block per system).
+ * Returns MWCG_OK when the launch succeeded (per-system outcomes are in
+ * status_out), or an error. */
+int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b, double* const* x,
+                       const int32_t* arith, const double* tol, const int32_t* maxit, void* stream,
+                       int32_t* iters_out, double* relres_out, int32_t* status_out);
+
+/* Adjoint of a solve, for L with dL/dx = gx (device double[n]):
+ *   lambda = CG(A, gx) in the same arithmetic from lambda0 = 0 (A symmetric,
+ *   so A^T lambda = gx is solved with the forward kernels);
+ *   g_b[i]   = collapse(lambda_i)                (device double[n], may be NULL);
+ *   g_val[k] = -collapse(lambda_row(k) * x_col(k)) (device double[nnz], may be NULL),
+ *              the product taken in the arithmetic;
+ *   x        device double[w*n], the forward solution (only it is needed).
+ * Returns the status of the adjoint solve (as mwcg_solve) or an error. */
+int mwcg_adjoint(mwcg_csr* A, const double* x, const double* gx, int arith, double tol, int32_t maxit, void* stream,
+                 double* g_b, double* g_val, int32_t* iters_out, double* relres_out);
+
+/* q = A p in the arithmetic, with the handle's plan (p, q device double[w*n]). */
+int mwcg_spmv(mwcg_csr* A, int arith, const double* p, double* q, void* stream);
+
+/* u^T v in the arithmetic over n elements (u, v device double[w*n]) with
+ * tiles of 256 rows over G blocks (1..1024); out: host double[w]. */
+int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream, double* out);
+
+/* Element-wise word operations on device arrays of n elements:
+ *   op 0 add c = a + b; 1 mul c = a * b; 2 dxmul c = a (FP64, double[n]) * b;
+ *   3 div c = a / b; 4 normalize c = the arithmetic's normalisation of a
+ *   (QuickTwoSum for QDW, VecSum3 for QTW, identity otherwise);
+ *   5 collapse c (double[n]) = a summed lowest word first. */
+int mwcg_word_op(int op, int arith, int64_t n, const double* a, const double* b, double* c, void* stream);
+
+/* Time the solver's kernels one by one: runs the initialisation and then
+ * `niters` CG iterations of A x = b in the arithmetic without the CUDA graph
+ * (each kernel launched on `stream` between CUDA events; the stop test is
+ * disabled so exactly niters iterations run), and writes the mean duration in
+ * milliseconds of the SpMV + p^T q kernel, the x/r update + r^T r kernel and
+ * the p update kernel to ms_out[0..2] (host double[3]).  x (device
+ * double[w*n]) is overwritten.  niters in 2..100000. */
+int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int32_t niters, void* stream,
+                         double* ms_out);
+
+/* x64[i] = collapse of element i of the w-word vector xw (device arrays). */
+int mwcg_collapse(const double* xw, int32_t w, int64_t n, double* x64, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MWCG_H */

@@ -1,0 +1,658 @@
+// Host runtime and C ABI (include/mwcg.h) of the multi-word CG solver.
+//
+// A matrix handle owns the device CSR, the solver workspace (r, p, q and the
+// block partials), a DevState block and, per arithmetic, an instantiated
+// CUDA graph of the whole solve: SpMV of x0, initialisation, and a
+// conditional WHILE node whose body is one CG iteration (Algorithm 1, lines
+// 5-14).  The loop condition is set on the device by the kernels, so a solve
+// is one graph launch plus one small copy of the results back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mwcg.h"
+#include "cg_kernels.cuh"
+
+namespace mwk {
+KernelTable table_fp64();
+KernelTable table_dw();
+KernelTable table_qdw();
+KernelTable table_qdw_nn();
+KernelTable table_tw();
+KernelTable table_qtw();
+KernelTable table_qtw_nn();
+}  // namespace mwk
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? MWCG_ERR_NOMEM : MWCG_ERR_CUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                                        \
+  } while (0)
+
+const mwk::KernelTable* table(int arith) {
+  static mwk::KernelTable t[7];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    t[0] = mwk::table_fp64();
+    t[1] = mwk::table_dw();
+    t[2] = mwk::table_qdw();
+    t[3] = mwk::table_tw();
+    t[4] = mwk::table_qtw();
+    t[5] = mwk::table_qdw_nn();
+    t[6] = mwk::table_qtw_nn();
+  });
+  if (arith < 0 || arith > 6) return nullptr;
+  return &t[arith];
+}
+
+constexpr int kMaxG = 1024;
+constexpr int32_t kMaxIt = 1 << 30;
+
+// Dynamic shared memory of the last-block reductions: G slots of up to
+// (3 words + 1 FP64 + 2 int flags = 40 bytes).
+size_t red_smem(int G) { return (size_t)G * 40; }
+
+struct GraphCache {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  mwcg_plan plan{0, 0, 0};
+};
+
+int sm_count_of(int dev) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v > 0 ? v : 1;
+}
+
+bool is_pow2_le32(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
+
+}  // namespace
+
+struct mwcg_csr {
+  int device = 0;
+  int64_t n = 0, nnz = 0;
+  int64_t* rp = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  mwcg_plan plan{1, 256, 1};
+  double* ws = nullptr;        // r, p, q: 3 vectors of up to 3 words
+  double* part = nullptr;      // kMaxG * 8
+  mwk::DevState* st = nullptr;
+  mwk::DevState* h_st = nullptr;   // pinned mirror
+  double* lam = nullptr;       // adjoint solution, lazily allocated
+  double* hb = nullptr;        // staging for host-buffer solves, lazily allocated
+  double* hx = nullptr;
+  GraphCache graphs[7];
+  std::vector<int64_t> rowlen;  // host copy of row lengths (plan selection)
+};
+
+namespace {
+
+void free_graphs(mwcg_csr* A) {
+  for (auto& g : A->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = GraphCache{};
+  }
+}
+
+// FP64 operations per SpMV multiply-add and per add, by arithmetic (Sec. III
+// counts; TW about 80 and 45 with its branches).  Used only to rank plans.
+void op_costs(int arith, double& mac, double& add) {
+  switch (arith) {
+    case MWCG_FP64: mac = 1; add = 1; break;
+    case MWCG_DW: mac = 17; add = 11; break;
+    case MWCG_QDW: case MWCG_QDW_NN: mac = 11; add = 8; break;
+    case MWCG_TW: mac = 80; add = 45; break;
+    default: mac = 33; add = 21; break;
+  }
+}
+
+// Plan selection from the row-length sequence.  The multi-word SpMV is bound
+// by the FP64 pipe, and a warp instruction costs the same whatever its
+// active-lane count, so the cost of V lanes per row is, per warp (32/V
+// consecutive rows), the longest row's ceil(len/V) multiply-adds plus
+// log2(V) tree adds.  FP64 arithmetic is memory bound: there the cost adds the
+// number of 32-lane load rounds, which favours wider rows.
+mwcg_plan choose_plan(const std::vector<int64_t>& len, int sms, int arith) {
+  double mac, add;
+  op_costs(arith, mac, add);
+  const int64_t n = (int64_t)len.size();
+  int bestV = 1;
+  double best = -1;
+  for (int V = 1; V <= 32; V <<= 1) {
+    const int rows_per_warp = 32 / V;
+    int lg = 0;
+    while ((1 << lg) < V) ++lg;
+    double cost = 0;
+    for (int64_t r0 = 0; r0 < n; r0 += rows_per_warp) {
+      int64_t mx = 0;
+      for (int64_t r = r0; r < std::min(n, r0 + rows_per_warp); ++r) mx = std::max(mx, len[r]);
+      const double passes = (double)((mx + V - 1) / V);
+      cost += passes * mac + lg * add;
+      if (arith == MWCG_FP64) cost += passes * 2.0;
+    }
+    if (best < 0 || cost < best * 0.98) { best = cost; bestV = V; }
+  }
+  mwcg_plan p;
+  p.V = bestV;
+  p.T = mwk::TPB;
+  const int64_t tiles = (n + mwk::TPB - 1) / mwk::TPB;
+  p.G = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)sms, std::min<int64_t>(tiles, kMaxG)));
+  return p;
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int validate_csr(int64_t n, const int64_t* rp, const int32_t* col, const double* val) {
+  if (rp[0] != 0) return fail(MWCG_ERR_ARG, "row_ptr[0] = %lld, expected 0", (long long)rp[0]);
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return fail(MWCG_ERR_ARG, "row_ptr decreases at row %lld", (long long)i);
+  const int64_t nnz = rp[n];
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (col[k] < 0 || (int64_t)col[k] >= n)
+      return fail(MWCG_ERR_ARG, "col[%lld] = %d out of range [0, %lld)", (long long)k, col[k], (long long)n);
+    if (!std::isfinite(val[k])) return fail(MWCG_ERR_ARG, "val[%lld] is not finite", (long long)k);
+  }
+  return MWCG_OK;
+}
+
+template <class... Args>
+int add_kernel(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* dep, size_t ndep, const void* fn,
+               int grid, size_t smem, Args... args) {
+  void* ptrs[] = {(void*)&args...};
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(mwk::TPB);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = ptrs;
+  kp.extra = nullptr;
+  CK(cudaGraphAddKernelNode(node, g, dep, ndep, &kp));
+  return MWCG_OK;
+}
+
+mwk::Csr csr_view(const mwcg_csr* A) { return mwk::Csr{A->rp, A->col, A->val, A->n}; }
+
+mwk::Work work_view(const mwcg_csr* A, unsigned long long cond, int has_cond) {
+  const int64_t n = A->n;
+  mwk::Work W;
+  W.r = A->ws;
+  W.p = A->ws + 3 * n;
+  W.q = A->ws + 6 * n;
+  W.part = A->part;
+  W.st = A->st;
+  W.cond = cond;
+  W.has_cond = has_cond;
+  W.V = A->plan.V;
+  W.G = A->plan.G;
+  return W;
+}
+
+// Build (or reuse) the graph of a whole solve in one arithmetic.
+int ensure_graph(mwcg_csr* A, int arith) {
+  GraphCache& gc = A->graphs[arith];
+  if (gc.exec && gc.plan.V == A->plan.V && gc.plan.G == A->plan.G) return MWCG_OK;
+  if (gc.exec) cudaGraphExecDestroy(gc.exec);
+  if (gc.graph) cudaGraphDestroy(gc.graph);
+  gc = GraphCache{};
+  const mwk::KernelTable* kt = table(arith);
+  const int G = A->plan.G;
+  const size_t smem = red_smem(G);
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(MWCG_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
+  }
+  const mwk::Csr M = csr_view(A);
+  const mwk::Work W = work_view(A, (unsigned long long)h, 1);
+  cudaGraphNode_t n0, n1, n2, nw, b0, b1, b2;
+  int rc;
+  const int mode0 = 0, mode1 = 1;
+  if ((rc = add_kernel(&n0, g, nullptr, 0, kt->spmv, G, smem, M, W, mode0)) ||
+      (rc = add_kernel(&n1, g, &n0, 1, kt->init, G, smem, M, W)) ||
+      (rc = add_kernel(&n2, g, &n1, 1, kt->zero_x, G, 0, M, W))) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  e = cudaGraphAddNode(&nw, g, &n2, nullptr, 1, &cp);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(MWCG_ERR_CUDA, "cudaGraphAddNode(while): %s", cudaGetErrorString(e));
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((rc = add_kernel(&b0, body, nullptr, 0, kt->spmv, G, smem, M, W, mode1)) ||
+      (rc = add_kernel(&b1, body, &b0, 1, kt->update, G, smem, M, W)) ||
+      (rc = add_kernel(&b2, body, &b1, 1, kt->pupdate, G, 0, M, W))) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  cudaGraphExec_t ex;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(MWCG_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  gc.graph = g;
+  gc.exec = ex;
+  gc.plan = A->plan;
+  return MWCG_OK;
+}
+
+int ensure_ws(mwcg_csr* A) {
+  if (A->ws || A->n == 0) return MWCG_OK;
+  CK(cudaMalloc(&A->ws, sizeof(double) * 9 * (size_t)A->n));
+  return MWCG_OK;
+}
+
+int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
+              cudaStream_t s, int32_t* iters_out, double* relres_out) {
+  int rc;
+  if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
+  if ((rc = ensure_graph(A, arith)) != MWCG_OK) return rc;
+  mwk::DevState* h = A->h_st;
+  std::memset(h, 0, sizeof *h);
+  h->b = b;
+  h->x = x;
+  h->hist = hist;
+  h->tol = tol;
+  h->maxit = maxit;
+  CK(cudaMemcpyAsync(A->st, h, sizeof *h, cudaMemcpyHostToDevice, s));
+  CK(cudaGraphLaunch(A->graphs[arith].exec, s));
+  CK(cudaMemcpyAsync(h, A->st, sizeof *h, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (iters_out) *iters_out = h->iters;
+  if (relres_out) *relres_out = h->relres;
+  if (h->status == mwk::ST_GUARD) return fail(MWCG_ERR_GUARD, "device loop guard tripped");
+  return h->status;
+}
+
+int check_solve_args(const mwcg_csr* A, const void* b, const void* x, int arith, double tol, int32_t maxit) {
+  if (!A) return fail(MWCG_ERR_ARG, "null matrix handle");
+  if (!table(arith)) return fail(MWCG_ERR_ARG, "unknown arithmetic %d", arith);
+  if (A->n > 0 && (!b || !x)) return fail(MWCG_ERR_ARG, "null b or x");
+  if (!(tol >= 0.0) || std::isnan(tol)) return fail(MWCG_ERR_ARG, "tol must be >= 0");
+  if (maxit < 0 || maxit > kMaxIt) return fail(MWCG_ERR_ARG, "maxit must be in [0, 2^30]");
+  return MWCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mwcg_words(int arith) {
+  static const int w[7] = {1, 2, 2, 3, 3, 2, 3};
+  return (arith >= 0 && arith < 7) ? w[arith] : -1;
+}
+
+const char* mwcg_last_error(void) { return g_err.c_str(); }
+
+int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val, int ptrs_on_device,
+                    void* stream, mwcg_csr** out) {
+  g_err.clear();
+  if (!out) return fail(MWCG_ERR_ARG, "null output handle pointer");
+  *out = nullptr;
+  if (n < 0 || n > (int64_t)INT32_MAX) return fail(MWCG_ERR_ARG, "n = %lld out of range", (long long)n);
+  if (!row_ptr) return fail(MWCG_ERR_ARG, "null row_ptr");
+  cudaStream_t s = S(stream);
+  // Host copies for validation and plan selection.
+  std::vector<int64_t> hrp(n + 1);
+  if (ptrs_on_device) CK(cudaMemcpy(hrp.data(), row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+  else std::memcpy(hrp.data(), row_ptr, sizeof(int64_t) * (n + 1));
+  const int64_t nnz = hrp[n];
+  if (nnz < 0 || nnz > ((int64_t)1 << 40)) return fail(MWCG_ERR_ARG, "nnz = %lld out of range", (long long)nnz);
+  if (nnz > 0 && (!col || !val)) return fail(MWCG_ERR_ARG, "null col or val");
+  std::vector<int32_t> hcol;
+  std::vector<double> hval;
+  const int32_t* vc = col;
+  const double* vv = val;
+  if (ptrs_on_device) {
+    hcol.resize(nnz);
+    hval.resize(nnz);
+    if (nnz) {
+      CK(cudaMemcpy(hcol.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(hval.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+    }
+    vc = hcol.data();
+    vv = hval.data();
+  }
+  int rc = validate_csr(n, hrp.data(), vc, vv);
+  if (rc != MWCG_OK) return rc;
+
+  mwcg_csr* A = new mwcg_csr();
+  CK(cudaGetDevice(&A->device));
+  A->n = n;
+  A->nnz = nnz;
+  auto cleanup = [&](int code) {
+    mwcg_destroy_csr(A);
+    return code;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&A->rp, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (nnz && (e = cudaMalloc(&A->col, sizeof(int32_t) * nnz)) != cudaSuccess) ||
+      (nnz && (e = cudaMalloc(&A->val, sizeof(double) * nnz)) != cudaSuccess) ||
+      (e = cudaMalloc(&A->part, sizeof(double) * 8 * kMaxG)) != cudaSuccess ||
+      (e = cudaMalloc(&A->st, sizeof(mwk::DevState))) != cudaSuccess ||
+      (e = cudaMallocHost(&A->h_st, sizeof(mwk::DevState))) != cudaSuccess)
+    return cleanup(fail(e == cudaErrorMemoryAllocation ? MWCG_ERR_NOMEM : MWCG_ERR_CUDA, "allocation: %s",
+                        cudaGetErrorString(e)));
+  const cudaMemcpyKind kind = ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if ((e = cudaMemcpyAsync(A->rp, ptrs_on_device ? row_ptr : hrp.data(), sizeof(int64_t) * (n + 1), kind, s)) !=
+          cudaSuccess ||
+      (nnz && (e = cudaMemcpyAsync(A->col, col, sizeof(int32_t) * nnz, kind, s)) != cudaSuccess) ||
+      (nnz && (e = cudaMemcpyAsync(A->val, val, sizeof(double) * nnz, kind, s)) != cudaSuccess) ||
+      (e = cudaMemsetAsync(A->st, 0, sizeof(mwk::DevState), s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cleanup(fail(MWCG_ERR_CUDA, "copy to device: %s", cudaGetErrorString(e)));
+  A->rowlen.resize(n);
+  for (int64_t i = 0; i < n; ++i) A->rowlen[i] = hrp[i + 1] - hrp[i];
+  A->plan = choose_plan(A->rowlen, sm_count_of(A->device), MWCG_QTW);
+  *out = A;
+  return MWCG_OK;
+}
+
+void mwcg_destroy_csr(mwcg_csr* A) {
+  if (!A) return;
+  free_graphs(A);
+  cudaFree(A->rp);
+  cudaFree(A->col);
+  cudaFree(A->val);
+  cudaFree(A->ws);
+  cudaFree(A->part);
+  cudaFree(A->st);
+  cudaFree(A->lam);
+  cudaFree(A->hb);
+  cudaFree(A->hx);
+  if (A->h_st) cudaFreeHost(A->h_st);
+  delete A;
+}
+
+int mwcg_update_values(mwcg_csr* A, const double* val, int on_device, void* stream) {
+  g_err.clear();
+  if (!A) return fail(MWCG_ERR_ARG, "null matrix handle");
+  if (A->nnz == 0) return MWCG_OK;
+  if (!val) return fail(MWCG_ERR_ARG, "null val");
+  std::vector<double> hv(A->nnz);
+  if (on_device) CK(cudaMemcpy(hv.data(), val, sizeof(double) * A->nnz, cudaMemcpyDeviceToHost));
+  else std::memcpy(hv.data(), val, sizeof(double) * A->nnz);
+  for (int64_t k = 0; k < A->nnz; ++k)
+    if (!std::isfinite(hv[k])) return fail(MWCG_ERR_ARG, "val[%lld] is not finite", (long long)k);
+  CK(cudaMemcpyAsync(A->val, hv.data(), sizeof(double) * A->nnz, cudaMemcpyHostToDevice, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  return MWCG_OK;
+}
+
+int64_t mwcg_n(const mwcg_csr* A) { return A ? A->n : -1; }
+int64_t mwcg_nnz(const mwcg_csr* A) { return A ? A->nnz : -1; }
+
+int mwcg_get_plan(const mwcg_csr* A, mwcg_plan* out) {
+  if (!A || !out) return fail(MWCG_ERR_ARG, "null argument");
+  *out = A->plan;
+  return MWCG_OK;
+}
+
+int mwcg_set_plan(mwcg_csr* A, const mwcg_plan* p) {
+  if (!A || !p) return fail(MWCG_ERR_ARG, "null argument");
+  if (!is_pow2_le32(p->V) || p->T != mwk::TPB || p->G < 1 || p->G > kMaxG)
+    return fail(MWCG_ERR_ARG, "invalid plan V=%d T=%d G=%d", p->V, p->T, p->G);
+  A->plan = *p;
+  return MWCG_OK;
+}
+
+int mwcg_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, void* stream,
+               int32_t* iters_out, double* relres_out) {
+  return mwcg_solve_history(A, b, x, arith, tol, maxit, nullptr, stream, iters_out, relres_out);
+}
+
+int mwcg_solve_history(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit,
+                       double* hist, void* stream, int32_t* iters_out, double* relres_out) {
+  g_err.clear();
+  int rc = check_solve_args(A, b, x, arith, tol, maxit);
+  if (rc != MWCG_OK) return rc;
+  if (A->n == 0) {
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return MWCG_OK;
+  }
+  return run_solve(A, b, x, arith, tol, maxit, hist, S(stream), iters_out, relres_out);
+}
+
+int mwcg_solve_host(mwcg_csr* A, const double* b_host, double* x_host, int arith, double tol, int32_t maxit,
+                    void* stream, int32_t* iters_out, double* relres_out) {
+  g_err.clear();
+  int rc = check_solve_args(A, b_host, x_host, arith, tol, maxit);
+  if (rc != MWCG_OK) return rc;
+  if (A->n == 0) {
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return MWCG_OK;
+  }
+  const size_t n = (size_t)A->n;
+  const int w = mwcg_words(arith);
+  if (!A->hb) CK(cudaMalloc(&A->hb, sizeof(double) * n));
+  if (!A->hx) CK(cudaMalloc(&A->hx, sizeof(double) * 3 * n));
+  cudaStream_t s = S(stream);
+  CK(cudaMemcpyAsync(A->hb, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(A->hx, x_host, sizeof(double) * w * n, cudaMemcpyHostToDevice, s));
+  rc = run_solve(A, A->hb, A->hx, arith, tol, maxit, nullptr, s, iters_out, relres_out);
+  if (rc < 0) return rc;
+  CK(cudaMemcpyAsync(x_host, A->hx, sizeof(double) * w * n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return rc;
+}
+
+int mwcg_adjoint(mwcg_csr* A, const double* x, const double* gx, int arith, double tol, int32_t maxit, void* stream,
+                 double* g_b, double* g_val, int32_t* iters_out, double* relres_out) {
+  g_err.clear();
+  int rc = check_solve_args(A, gx, x, arith, tol, maxit);
+  if (rc != MWCG_OK) return rc;
+  if (A->n == 0) {
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return MWCG_OK;
+  }
+  cudaStream_t s = S(stream);
+  const size_t n = (size_t)A->n;
+  if (!A->lam) CK(cudaMalloc(&A->lam, sizeof(double) * 3 * n));
+  CK(cudaMemsetAsync(A->lam, 0, sizeof(double) * 3 * n, s));
+  rc = run_solve(A, gx, A->lam, arith, tol, maxit, nullptr, s, iters_out, relres_out);
+  if (rc < 0) return rc;
+  const mwk::KernelTable* kt = table(arith);
+  const mwk::Csr M = csr_view(A);
+  const int G = A->plan.G;
+  if (g_b) {
+    void* args[] = {(void*)&A->lam, (void*)&A->n, (void*)&g_b};
+    CK(cudaLaunchKernel(kt->collapse, dim3(G), dim3(mwk::TPB), args, 0, s));
+  }
+  if (g_val && A->nnz) {
+    const double* lam = A->lam;
+    void* args[] = {(void*)&M, (void*)&lam, (void*)&x, (void*)&g_val};
+    CK(cudaLaunchKernel(kt->grad_values, dim3(std::max(G, 1)), dim3(mwk::TPB), args, 0, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return rc;
+}
+
+int mwcg_spmv(mwcg_csr* A, int arith, const double* p, double* q, void* stream) {
+  g_err.clear();
+  if (!A || !table(arith)) return fail(MWCG_ERR_ARG, "bad handle or arithmetic");
+  if (A->n == 0) return MWCG_OK;
+  if (!p || !q) return fail(MWCG_ERR_ARG, "null p or q");
+  cudaStream_t s = S(stream);
+  int rc;
+  if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
+  mwk::DevState* h = A->h_st;
+  std::memset(h, 0, sizeof *h);
+  h->x = const_cast<double*>(p);
+  CK(cudaMemcpyAsync(A->st, h, sizeof *h, cudaMemcpyHostToDevice, s));
+  mwk::Csr M = csr_view(A);
+  mwk::Work W = work_view(A, 0, 0);
+  W.q = q;
+  int mode = 0;
+  void* args[] = {(void*)&M, (void*)&W, (void*)&mode};
+  CK(cudaLaunchKernel(table(arith)->spmv, dim3(A->plan.G), dim3(mwk::TPB), args, red_smem(A->plan.G), s));
+  CK(cudaStreamSynchronize(s));
+  return MWCG_OK;
+}
+
+int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream, double* out) {
+  g_err.clear();
+  if (!table(arith) || n < 0 || G < 1 || G > kMaxG || !out) return fail(MWCG_ERR_ARG, "bad argument");
+  const int w = mwcg_words(arith);
+  if (n == 0) {
+    for (int k = 0; k < w; ++k) out[k] = 0.0;
+    return MWCG_OK;
+  }
+  if (!u || !v) return fail(MWCG_ERR_ARG, "null u or v");
+  cudaStream_t s = S(stream);
+  double* part = nullptr;
+  mwk::DevState* st = nullptr;
+  double* dout = nullptr;
+  cudaError_t e = cudaMalloc(&part, sizeof(double) * 8 * G);
+  if (e == cudaSuccess) e = cudaMalloc(&st, sizeof(mwk::DevState));
+  if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(mwk::DevState), s);
+  if (e == cudaSuccess) {
+    mwk::Work W{};
+    W.part = part;
+    W.st = st;
+    W.V = 1;
+    W.G = G;
+    void* args[] = {(void*)&u, (void*)&v, (void*)&n, (void*)&W, (void*)&dout};
+    e = cudaLaunchKernel(table(arith)->dot, dim3(G), dim3(mwk::TPB), args, red_smem(G), s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(double) * w, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(part);
+  cudaFree(st);
+  cudaFree(dout);
+  if (e != cudaSuccess) return fail(MWCG_ERR_CUDA, "mwcg_dot: %s", cudaGetErrorString(e));
+  return MWCG_OK;
+}
+
+int mwcg_word_op(int op, int arith, int64_t n, const double* a, const double* b, double* c, void* stream) {
+  g_err.clear();
+  if (!table(arith) || op < 0 || op > 5 || n < 0) return fail(MWCG_ERR_ARG, "bad argument");
+  if (n == 0) return MWCG_OK;
+  if (!a || !c || ((op <= 3) && !b)) return fail(MWCG_ERR_ARG, "null operand");
+  cudaStream_t s = S(stream);
+  const int grid = (int)std::min<int64_t>((n + mwk::TPB - 1) / mwk::TPB, 4096);
+  void* args[] = {(void*)&op, (void*)&n, (void*)&a, (void*)&b, (void*)&c};
+  CK(cudaLaunchKernel(table(arith)->word_op, dim3(grid), dim3(mwk::TPB), args, 0, s));
+  CK(cudaStreamSynchronize(s));
+  return MWCG_OK;
+}
+
+int mwcg_collapse(const double* xw, int32_t w, int64_t n, double* x64, void* stream) {
+  g_err.clear();
+  if (w < 1 || w > 3 || n < 0) return fail(MWCG_ERR_ARG, "bad argument");
+  if (n == 0) return MWCG_OK;
+  if (!xw || !x64) return fail(MWCG_ERR_ARG, "null pointer");
+  const int arith = (w == 1) ? MWCG_FP64 : (w == 2) ? MWCG_DW : MWCG_QTW;
+  const int grid = (int)std::min<int64_t>((n + mwk::TPB - 1) / mwk::TPB, 4096);
+  void* args[] = {(void*)&xw, (void*)&n, (void*)&x64};
+  CK(cudaLaunchKernel(table(arith)->collapse, dim3(grid), dim3(mwk::TPB), args, 0, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  return MWCG_OK;
+}
+
+int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int32_t niters, void* stream,
+                         double* ms_out) {
+  g_err.clear();
+  int rc = check_solve_args(A, b, x, arith, 0.0, niters);
+  if (rc != MWCG_OK) return rc;
+  if (niters < 2 || niters > 100000 || !ms_out || A->n == 0) return fail(MWCG_ERR_ARG, "bad profile arguments");
+  if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
+  cudaStream_t s = S(stream);
+  const mwk::KernelTable* kt = table(arith);
+  mwk::DevState* h = A->h_st;
+  std::memset(h, 0, sizeof *h);
+  h->b = b;
+  h->x = x;
+  h->tol = 0.0;
+  h->maxit = niters;
+  CK(cudaMemcpyAsync(A->st, h, sizeof *h, cudaMemcpyHostToDevice, s));
+  mwk::Csr M = csr_view(A);
+  mwk::Work W = work_view(A, 0, 0);
+  const int G = A->plan.G;
+  const size_t smem = red_smem(G);
+  int mode0 = 0, mode1 = 1;
+  void* a_spmv0[] = {(void*)&M, (void*)&W, (void*)&mode0};
+  void* a_spmv1[] = {(void*)&M, (void*)&W, (void*)&mode1};
+  void* a_mw[] = {(void*)&M, (void*)&W};
+  CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
+  CK(cudaLaunchKernel(kt->init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
+  CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
+  std::vector<cudaEvent_t> ev(3 * (size_t)niters + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  int err = MWCG_OK;
+  cudaError_t ce = cudaEventRecord(ev[0], s);
+  for (int i = 0; i < niters && ce == cudaSuccess; ++i) {
+    ce = cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv1, smem, s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * i + 1], s);
+    if (ce == cudaSuccess) ce = cudaLaunchKernel(kt->update, dim3(G), dim3(mwk::TPB), a_mw, smem, s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * i + 2], s);
+    if (ce == cudaSuccess) ce = cudaLaunchKernel(kt->pupdate, dim3(G), dim3(mwk::TPB), a_mw, 0, s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * i + 3], s);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) err = fail(MWCG_ERR_CUDA, "profile: %s", cudaGetErrorString(ce));
+  double acc[3] = {0, 0, 0};
+  if (err == MWCG_OK) {
+    // The last p update is skipped by design (the loop has stopped), so it is
+    // averaged over the first niters-1 iterations.
+    for (int i = 0; i < niters; ++i)
+      for (int k = 0; k < 3; ++k) {
+        if (k == 2 && i == niters - 1) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[3 * i + k], ev[3 * i + k + 1]);
+        acc[k] += ms;
+      }
+    ms_out[0] = acc[0] / niters;
+    ms_out[1] = acc[1] / niters;
+    ms_out[2] = acc[2] / (niters - 1);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return err;
+}
+
+int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b, double* const* x,
+                       const int32_t* arith, const double* tol, const int32_t* maxit, void* stream,
+                       int32_t* iters_out, double* relres_out, int32_t* status_out) {
+  (void)nsys; (void)A; (void)b; (void)x; (void)arith; (void)tol; (void)maxit; (void)stream;
+  (void)iters_out; (void)relres_out; (void)status_out;
+  return fail(MWCG_ERR_ARG, "mwcg_solve_batched: not built in this library version");
+}
+
+}  // extern "C"

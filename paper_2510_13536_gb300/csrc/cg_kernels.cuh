@@ -1,0 +1,578 @@
+// CG kernels for one arithmetic (template parameter A from mw_device.cuh).
+//
+// One CG iteration (Algorithm 1) is three kernels:
+//   k_spmv   q = A p (line 5) fused with p^T q (line 6); the last block to
+//            finish reduces the block partials, divides alpha = rho / p^T q
+//            and tests for breakdown.
+//   k_update x += alpha p, r -= alpha q (lines 7-8), normalisation of r for
+//            the quasi arithmetics (Sec. IV-D), r^T r (line 9); the last block
+//            forms the FP64 relative residual (Sec. IV-C), applies the stop
+//            test (line 10), beta = rho' / rho (line 13) and sets the CUDA
+//            graph's loop condition.
+//   k_pupdate p = r + beta p (line 14).
+// plus k_init (line 1-2 and ||b||) and k_zero_x.  All of them read the
+// per-solve scalars from a DevState in device memory, so one instantiated
+// CUDA graph serves every call on the same matrix.
+//
+// Summation order (must match the CPU oracle's mirrored mode bit for bit),
+// a function of the plan {V lanes per row, T threads per block, G blocks}:
+//   row i of the SpMV: lane l of the row's V-lane group owns entries
+//     row_start + l + jV and sums their products left to right from its first
+//     product; lanes are combined by the pairwise tree.
+//   dots: rows are cut into tiles of R = T/V (SpMV) or R = T (vector kernels)
+//     rows; tile t belongs to block t mod G; slot s of a block adds the leaves
+//     of row t*R+s of its tiles in increasing t; the R slots, then the G
+//     blocks, are combined by the pairwise tree (level h pairs slot s with
+//     s+h for s a multiple of 2h; absent entries skipped).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "mw_device.cuh"
+
+namespace mwk {
+
+constexpr int TPB = 256;                  // threads per block of every kernel
+constexpr int NWARP = TPB / 32;
+
+enum { ST_CONVERGED = 0, ST_MAXIT = 1, ST_BREAKDOWN = 2, ST_GUARD = 3 };
+
+// Per-solve state in device memory.  Written by the host before a launch
+// (b, x, tol, maxit, hist) and by the kernels (everything else).
+struct DevState {
+  const double* b;          // f64[n]
+  double* x;                // f64[w][n], x0 in, solution out
+  double* hist;             // optional f64[maxit] relative-residual history, or null
+  double tol;
+  int32_t maxit;
+  int32_t pad0;
+  double rho[3];
+  double alpha[3];
+  double beta[3];
+  double bnorm;
+  double relres;
+  int32_t iters;
+  int32_t status;
+  int32_t done;
+  int32_t zero_x;
+  uint32_t counter;         // last-block election
+  uint32_t guard;           // loop passes seen by block 0 of k_spmv (hang guard)
+};
+
+struct Csr {
+  const int64_t* __restrict__ rp;
+  const int32_t* __restrict__ col;
+  const double* __restrict__ val;
+  int64_t n;
+};
+
+struct Work {
+  double* r;                // f64[w][n]
+  double* p;
+  double* q;
+  double* part;             // f64[G][4] block partials
+  DevState* st;
+  unsigned long long cond;  // cudaGraphConditionalHandle, valid if has_cond
+  int has_cond;
+  int V;                    // lanes per row in the SpMV
+  int G;                    // blocks
+};
+
+template <class A>
+__device__ __forceinline__ typename A::T ld(const double* __restrict__ v, int64_t n, int64_t i) {
+  typename A::T t;
+#pragma unroll
+  for (int k = 0; k < A::W; ++k) t.w[k] = v[k * n + i];
+  return t;
+}
+template <class A>
+__device__ __forceinline__ void st(double* __restrict__ v, int64_t n, int64_t i, const typename A::T& t) {
+#pragma unroll
+  for (int k = 0; k < A::W; ++k) v[k * n + i] = t.w[k];
+}
+template <class A>
+__device__ __forceinline__ typename A::T shfl_down(const typename A::T& v, int off) {
+  typename A::T o;
+#pragma unroll
+  for (int k = 0; k < A::W; ++k) o.w[k] = __shfl_down_sync(0xffffffffu, v.w[k], off);
+  return o;
+}
+// Combine step of the pairwise tree with presence flags.
+template <class A>
+__device__ __forceinline__ void combine(typename A::T& v, bool& pv, const typename A::T& o, bool po) {
+  if (po) {
+    if (pv) v = A::add(v, o);
+    else { v = o; pv = true; }
+  }
+}
+
+__device__ __forceinline__ void set_cond(const Work& W, unsigned v) {
+  if (W.has_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)W.cond, v);
+}
+
+// Pairwise tree over the R = TPB/V slots of a block; slot s lives in thread
+// s*V.  Returns the block value in thread 0 (and its presence).
+template <class A>
+__device__ __forceinline__ void block_tree(typename A::T& v, bool& pv, int V) {
+  __shared__ typename A::T sv[NWARP];
+  __shared__ int sp[NWARP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int spw = 32 / V;                  // slots per warp
+  const int s_in_warp = lane / V;
+  for (int h = 1; h < spw; h <<= 1) {
+    typename A::T o = shfl_down<A>(v, h * V);
+    bool po = __shfl_down_sync(0xffffffffu, (int)pv, h * V) != 0;
+    if ((lane % V) == 0 && (s_in_warp % (2 * h)) == 0 && s_in_warp + h < spw) combine<A>(v, pv, o, po);
+  }
+  if (lane == 0) { sv[warp] = v; sp[warp] = pv ? 1 : 0; }
+  __syncthreads();
+  if (warp == 0) {
+    typename A::T x = (lane < NWARP) ? sv[lane] : A::zero();
+    bool px = (lane < NWARP) ? (sp[lane] != 0) : false;
+    for (int h = 1; h < NWARP; h <<= 1) {
+      typename A::T o = shfl_down<A>(x, h);
+      bool po = __shfl_down_sync(0xffffffffu, (int)px, h) != 0;
+      if ((lane % (2 * h)) == 0 && lane + h < NWARP) combine<A>(x, px, o, po);
+    }
+    if (lane == 0) { v = x; pv = px; }
+  }
+  __syncthreads();
+}
+
+// Each block stores its value; the block that finishes last (atomic ticket)
+// reduces the G values by the pairwise tree and returns true in every thread
+// of that block, with the result in thread 0's `out`.
+template <class A, int OFF>
+__device__ __forceinline__ bool grid_reduce(const Work& W, const typename A::T& v, bool pv, typename A::T& out,
+                                            bool& pout) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    double* dst = W.part + (size_t)blockIdx.x * 8 + OFF;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) dst[k] = v.w[k];
+    dst[3] = pv ? 1.0 : 0.0;
+    __threadfence();
+    unsigned t = atomicAdd(&W.st->counter, 1u);
+    am_last = (t == (unsigned)(gridDim.x - 1));
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  // Pairwise tree over the G block values, in shared memory.
+  extern __shared__ double dyn[];
+  typename A::T* sv = reinterpret_cast<typename A::T*>(dyn);
+  int* spf = reinterpret_cast<int*>(sv + gridDim.x);
+  const int G = gridDim.x;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+    const double* src = W.part + (size_t)b * 8 + OFF;
+    typename A::T t;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) t.w[k] = __ldcg(src + k);
+    sv[b] = t;
+    spf[b] = __ldcg(src + 3) != 0.0 ? 1 : 0;
+  }
+  __syncthreads();
+  for (int h = 1; h < G; h <<= 1) {
+    for (int s = 2 * h * threadIdx.x; s + h < G; s += 2 * h * blockDim.x) {
+      typename A::T a = sv[s];
+      bool pa = spf[s] != 0;
+      combine<A>(a, pa, sv[s + h], spf[s + h] != 0);
+      sv[s] = a;
+      spf[s] = pa ? 1 : 0;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out = sv[0];
+    pout = spf[0] != 0;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// q = A p (mode 1, fused with p^T q and the alpha step) or q = A x0 (mode 0).
+// ---------------------------------------------------------------------------
+template <class A>
+__global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
+  using T = typename A::T;
+  DevState* S = W.st;
+  if (mode == 1 && S->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(W, 0);
+    return;
+  }
+  // Hang guard, independent of the last-block elections: the loop can run at
+  // most maxit passes, so a pass number above maxit + 1 means an election was
+  // lost; stop the loop with an error status.
+  if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned g = ++S->guard;
+    if (g > (unsigned)S->maxit + 1u) {
+      S->status = ST_GUARD;
+      S->done = 1;
+      set_cond(W, 0);
+    }
+  }
+  const double* __restrict__ p = (mode == 1) ? W.p : S->x;
+  double* __restrict__ q = W.q;
+  const int64_t n = M.n;
+  const int V = W.V;
+  const int R = TPB / V;
+  const int lane_in_row = threadIdx.x % V;
+  const int slot = threadIdx.x / V;
+  const int64_t ntiles = (n + R - 1) / R;
+  T acc = A::zero();
+  bool pacc = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t row = t * R + slot;
+    int64_t k0 = 0, k1 = 0;
+    if (row < n) { k0 = M.rp[row]; k1 = M.rp[row + 1]; }
+    const int64_t len = k1 - k0;
+    T sum = A::zero();
+    bool ps = false;
+    int64_t k = k0 + lane_in_row;
+    if (k < k1) {
+      sum = A::dxmul(M.val[k], ld<A>(p, n, M.col[k]));
+      ps = true;
+      for (k += V; k < k1; k += V) sum = A::dxmuladd(sum, M.val[k], ld<A>(p, n, M.col[k]));
+    }
+    // Pairwise tree over the V lanes of the row (groups are aligned in the warp).
+    for (int h = 1; h < V; h <<= 1) {
+      T o = shfl_down<A>(sum, h);
+      bool po = (lane_in_row % (2 * h)) == 0 && lane_in_row + h < len;
+      if (po) combine<A>(sum, ps, o, true);
+    }
+    if (lane_in_row == 0 && row < n) {
+      if (!ps) sum = A::zero();
+      st<A>(q, n, row, sum);
+      if (mode == 1) {
+        T leaf = A::mul(ld<A>(p, n, row), sum);
+        if (pacc) acc = A::add(acc, leaf);
+        else { acc = leaf; pacc = true; }
+      }
+    }
+  }
+  if (mode != 1) return;
+  block_tree<A>(acc, pacc, V);
+  T tot;
+  bool ptot = false;
+  if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  if (threadIdx.x == 0) {
+    S->counter = 0;
+    if (!ptot) tot = A::zero();
+    S->iters += 1;
+    double pq = A::collapse(tot);
+    // Breakdown: collapse(p^T q) not > 0 (NaN included) or not finite.
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      S->status = ST_BREAKDOWN;
+      S->done = 1;
+      set_cond(W, 0);
+    } else {
+      T rho;
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) rho.w[k] = S->rho[k];
+      T al = A::div(rho, tot);
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) S->alpha[k] = al.w[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// r0 = (b,0,..) + (-(A x0)), p0 = r0, rho0 = r0^T r0, ||b||^2 (FP64).
+// ---------------------------------------------------------------------------
+template <class A>
+__global__ void __launch_bounds__(TPB) k_init(Csr M, Work W) {
+  using T = typename A::T;
+  DevState* S = W.st;
+  const int64_t n = M.n;
+  const double* __restrict__ b = S->b;
+  const int64_t ntiles = (n + TPB - 1) / TPB;
+  T acc = A::zero();
+  bool pacc = false;
+  mw::MW<1> bb{{0.0}};
+  bool pbb = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i = t * TPB + threadIdx.x;
+    if (i < n) {
+      double bi = b[i];
+      T ri = A::add(A::from(bi), mw::neg<A>(ld<A>(W.q, n, i)));
+      st<A>(W.r, n, i, ri);
+      st<A>(W.p, n, i, ri);
+      T leaf = A::mul(ri, ri);
+      if (pacc) acc = A::add(acc, leaf);
+      else { acc = leaf; pacc = true; }
+      mw::MW<1> lb{{mw::dmul(bi, bi)}};
+      if (pbb) bb = mw::FP64::add(bb, lb);
+      else { bb = lb; pbb = true; }
+    }
+  }
+  block_tree<A>(acc, pacc, 1);
+  block_tree<mw::FP64>(bb, pbb, 1);
+  // Two grid reductions share one election: store both, then reduce both.
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    double* dst = W.part + (size_t)blockIdx.x * 8;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) dst[k] = acc.w[k];
+    dst[3] = pacc ? 1.0 : 0.0;
+    dst[4] = bb.w[0];
+    dst[7] = pbb ? 1.0 : 0.0;
+    __threadfence();
+    unsigned tk = atomicAdd(&S->counter, 1u);
+    am_last = (tk == (unsigned)(gridDim.x - 1));
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  extern __shared__ double dyn[];
+  const int G = gridDim.x;
+  T* sv = reinterpret_cast<T*>(dyn);
+  double* sb = reinterpret_cast<double*>(sv + G);
+  int* spf = reinterpret_cast<int*>(sb + G);
+  int* spb = spf + G;
+  for (int bk = threadIdx.x; bk < G; bk += blockDim.x) {
+    const double* src = W.part + (size_t)bk * 8;
+    T tv;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) tv.w[k] = __ldcg(src + k);
+    sv[bk] = tv;
+    spf[bk] = __ldcg(src + 3) != 0.0;
+    sb[bk] = __ldcg(src + 4);
+    spb[bk] = __ldcg(src + 7) != 0.0;
+  }
+  __syncthreads();
+  for (int h = 1; h < G; h <<= 1) {
+    for (int s = 2 * h * threadIdx.x; s + h < G; s += 2 * h * blockDim.x) {
+      T a = sv[s];
+      bool pa = spf[s] != 0;
+      combine<A>(a, pa, sv[s + h], spf[s + h] != 0);
+      sv[s] = a;
+      spf[s] = pa;
+      mw::MW<1> c{{sb[s]}};
+      bool pc = spb[s] != 0;
+      combine<mw::FP64>(c, pc, mw::MW<1>{{sb[s + h]}}, spb[s + h] != 0);
+      sb[s] = c.w[0];
+      spb[s] = pc;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    S->counter = 0;
+    T rho = spf[0] ? sv[0] : A::zero();
+    double bnorm = __dsqrt_rn(spb[0] ? sb[0] : 0.0);
+    S->bnorm = bnorm;
+    S->iters = 0;
+    S->status = ST_CONVERGED;
+    S->done = 0;
+    S->zero_x = 0;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) S->rho[k] = rho.w[k];
+    if (bnorm == 0.0) {
+      S->relres = 0.0;
+      S->done = 1;
+      S->zero_x = 1;
+    } else {
+      bool rzero = true;
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) rzero = rzero && !mw::nonzero(rho.w[k]);
+      S->relres = __ddiv_rn(__dsqrt_rn(A::collapse(rho)), bnorm);
+      if (rzero) {
+        S->relres = 0.0;
+        S->done = 1;
+      } else if (S->maxit <= 0) {
+        S->status = ST_MAXIT;
+        S->done = 1;
+      }
+    }
+  }
+}
+
+// x = 0 when ||b|| = 0.
+template <int Wd>
+__global__ void __launch_bounds__(TPB) k_zero_x(Csr M, Work W) {
+  DevState* S = W.st;
+  if (!S->zero_x) return;
+  const int64_t total = (int64_t)Wd * M.n;
+  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < total; i += (int64_t)gridDim.x * TPB) S->x[i] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// x += alpha p; r += (-alpha) q; normalise r; rho' = r^T r; stop test; beta.
+// ---------------------------------------------------------------------------
+template <class A>
+__global__ void __launch_bounds__(TPB) k_update(Csr M, Work W) {
+  using T = typename A::T;
+  DevState* S = W.st;
+  if (S->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(W, 0);
+    return;
+  }
+  const int64_t n = M.n;
+  double* __restrict__ x = S->x;
+  T al, mal;
+#pragma unroll
+  for (int k = 0; k < A::W; ++k) al.w[k] = S->alpha[k];
+  mal = mw::neg<A>(al);
+  const int64_t ntiles = (n + TPB - 1) / TPB;
+  T acc = A::zero();
+  bool pacc = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i = t * TPB + threadIdx.x;
+    if (i < n) {
+      st<A>(x, n, i, A::muladd(ld<A>(x, n, i), al, ld<A>(W.p, n, i)));
+      T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
+      A::normalize(ri);
+      st<A>(W.r, n, i, ri);
+      T leaf = A::mul(ri, ri);
+      if (pacc) acc = A::add(acc, leaf);
+      else { acc = leaf; pacc = true; }
+    }
+  }
+  block_tree<A>(acc, pacc, 1);
+  T tot;
+  bool ptot = false;
+  if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  if (threadIdx.x == 0) {
+    S->counter = 0;
+    if (!ptot) tot = A::zero();
+    const double relres = __ddiv_rn(__dsqrt_rn(A::collapse(tot)), S->bnorm);
+    S->relres = relres;
+    const int it = S->iters;
+    if (S->hist) S->hist[it - 1] = relres;
+    unsigned cont = 0;
+    if (relres < S->tol) {
+      S->status = ST_CONVERGED;
+      S->done = 1;
+    } else if (!isfinite(relres)) {
+      S->status = ST_BREAKDOWN;
+      S->done = 1;
+    } else if (it >= S->maxit) {
+      S->status = ST_MAXIT;
+      S->done = 1;
+    } else {
+      T rho;
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) rho.w[k] = S->rho[k];
+      T be = A::div(tot, rho);
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) { S->beta[k] = be.w[k]; S->rho[k] = tot.w[k]; }
+      cont = 1;
+    }
+    set_cond(W, cont);
+  }
+}
+
+// p = r + beta p.
+template <class A>
+__global__ void __launch_bounds__(TPB) k_pupdate(Csr M, Work W) {
+  using T = typename A::T;
+  DevState* S = W.st;
+  if (S->done) return;
+  const int64_t n = M.n;
+  T be;
+#pragma unroll
+  for (int k = 0; k < A::W; ++k) be.w[k] = S->beta[k];
+  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB)
+    st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i)));
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of the values: g_k = -collapse(lambda_row(k) * x_col(k)).
+// ---------------------------------------------------------------------------
+template <class A>
+__global__ void __launch_bounds__(TPB) k_grad_values(Csr M, const double* __restrict__ lam,
+                                                    const double* __restrict__ x, double* __restrict__ g) {
+  const int64_t n = M.n;
+  // One warp per row, lanes over the row's entries.
+  const int64_t warps = (int64_t)gridDim.x * NWARP;
+  const int lane = threadIdx.x & 31;
+  for (int64_t row = (int64_t)blockIdx.x * NWARP + (threadIdx.x >> 5); row < n; row += warps) {
+    typename A::T li = ld<A>(lam, n, row);
+    for (int64_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += 32)
+      g[k] = mw::dneg(A::collapse(A::mul(li, ld<A>(x, n, M.col[k]))));
+  }
+}
+
+// Collapse to FP64, lowest word first.
+template <class A>
+__global__ void __launch_bounds__(TPB) k_collapse(const double* __restrict__ xw, int64_t n, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB)
+    y[i] = A::collapse(ld<A>(xw, n, i));
+}
+
+// Stand-alone dot u^T v (tiles of TPB rows, G = gridDim.x blocks); result to out[0..W-1].
+template <class A>
+__global__ void __launch_bounds__(TPB) k_dot(const double* __restrict__ u, const double* __restrict__ v, int64_t n,
+                                             Work W, double* out) {
+  using T = typename A::T;
+  const int64_t ntiles = (n + TPB - 1) / TPB;
+  T acc = A::zero();
+  bool pacc = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i = t * TPB + threadIdx.x;
+    if (i < n) {
+      T leaf = A::mul(ld<A>(u, n, i), ld<A>(v, n, i));
+      if (pacc) acc = A::add(acc, leaf);
+      else { acc = leaf; pacc = true; }
+    }
+  }
+  block_tree<A>(acc, pacc, 1);
+  T tot;
+  bool ptot = false;
+  if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  if (threadIdx.x == 0) {
+    W.st->counter = 0;
+    if (!ptot) tot = A::zero();
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) out[k] = tot.w[k];
+  }
+}
+
+// Element-wise word operations (bit-exactness checks of the word algebra).
+enum WordOp { OP_ADD = 0, OP_MUL = 1, OP_DXMUL = 2, OP_DIV = 3, OP_NORMALIZE = 4, OP_COLLAPSE = 5 };
+template <class A>
+__global__ void __launch_bounds__(TPB) k_word_op(int op, int64_t n, const double* __restrict__ a,
+                                                 const double* __restrict__ b, double* __restrict__ c) {
+  using T = typename A::T;
+  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB) {
+    switch (op) {
+      case OP_ADD: st<A>(c, n, i, A::add(ld<A>(a, n, i), ld<A>(b, n, i))); break;
+      case OP_MUL: st<A>(c, n, i, A::mul(ld<A>(a, n, i), ld<A>(b, n, i))); break;
+      case OP_DXMUL: st<A>(c, n, i, A::dxmul(a[i], ld<A>(b, n, i))); break;
+      case OP_DIV: st<A>(c, n, i, A::div(ld<A>(a, n, i), ld<A>(b, n, i))); break;
+      case OP_NORMALIZE: { T t = ld<A>(a, n, i); A::normalize(t); st<A>(c, n, i, t); } break;
+      case OP_COLLAPSE: c[i] = A::collapse(ld<A>(a, n, i)); break;
+      default: break;
+    }
+  }
+}
+
+// Kernel table of one arithmetic, used by the host runtime.
+struct KernelTable {
+  int words;
+  const void* spmv;
+  const void* init;
+  const void* zero_x;
+  const void* update;
+  const void* pupdate;
+  const void* grad_values;
+  const void* collapse;
+  const void* dot;
+  const void* word_op;
+};
+
+template <class A>
+KernelTable make_table() {
+  KernelTable t;
+  t.words = A::W;
+  t.spmv = (const void*)&k_spmv<A>;
+  t.init = (const void*)&k_init<A>;
+  t.zero_x = (const void*)&k_zero_x<A::W>;
+  t.update = (const void*)&k_update<A>;
+  t.pupdate = (const void*)&k_pupdate<A>;
+  t.grad_values = (const void*)&k_grad_values<A>;
+  t.collapse = (const void*)&k_collapse<A>;
+  t.dot = (const void*)&k_dot<A>;
+  t.word_op = (const void*)&k_word_op<A>;
+  return t;
+}
+
+}  // namespace mwk

@@ -1,0 +1,366 @@
+// Device word algebra for multi-word arithmetic on sm_103a.
+//
+// Sources: Sec. III of Mukunoki & Ozaki, "Sparse Iterative Solvers Using
+// High-Precision Arithmetic with Quasi Multi-Word Algorithms" -- TwoSum
+// (Algorithm 2), QuickTwoSum (Algorithm 3), TwoProdFMA (Algorithm 4), DWadd
+// (Algorithm 5), DWmul (Algorithm 6), QTWadd (Algorithm 7), QTWmul
+// (Algorithm 8), VecSum3 (Algorithm 9), DxQTWmul (Algorithm 10); QDW is DW
+// without the closing QuickTwoSum; FP64 x MW drops the work on zero lower
+// words.  Triple-word (TW) follows the Fabiano-Muller-Picot scheme the paper
+// cites without printing it (VecSum + renormalisation with branches).
+//
+// Every FP64 operation is an explicit round-to-nearest intrinsic
+// (__dadd_rn, __dsub_rn, __dmul_rn, __fma_rn, __ddiv_rn, __dsqrt_rn): those are
+// never contracted or reassociated, so the sequences below are executed
+// exactly as written.  Negation and zero/magnitude tests are done on the bit
+// pattern (integer pipe), which is exact and keeps them off the FP64 pipe:
+// on GB300 the FP64 pipe retires 2 operations per clock per SM while the
+// integer pipe retires 64, so the FP64 instruction count is the cost model.
+#pragma once
+#include <cstdint>
+
+namespace mw {
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double dneg(double a) {
+  return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ULL);
+}
+// |a| >= |b| on the bit patterns (valid for all non-NaN values).
+__device__ __forceinline__ bool mag_ge(double a, double b) {
+  unsigned long long ua = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffULL;
+  unsigned long long ub = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffULL;
+  return ua >= ub;
+}
+// a != 0 (either sign of zero counts as zero; NaN counts as nonzero, as != does).
+__device__ __forceinline__ bool nonzero(double a) {
+  return ((unsigned long long)__double_as_longlong(a) << 1) != 0ULL;
+}
+
+// Algorithm 2, TwoSum.
+__device__ __forceinline__ void two_sum(double a, double b, double& x, double& y) {
+  double s = dadd(a, b);
+  double z = dsub(s, a);
+  double t1 = dsub(a, dsub(s, z));
+  double t2 = dsub(b, z);
+  y = dadd(t1, t2);
+  x = s;
+}
+// Algorithm 3, QuickTwoSum.
+__device__ __forceinline__ void quick_two_sum(double a, double b, double& x, double& y) {
+  double s = dadd(a, b);
+  y = dadd(dsub(a, s), b);
+  x = s;
+}
+// Algorithm 4, TwoProdFMA.
+__device__ __forceinline__ void two_prod(double a, double b, double& x, double& y) {
+  double p = dmul(a, b);
+  y = dfma(a, b, -p);
+  x = p;
+}
+
+template <int W> struct MW { double w[W]; };
+
+// ---------------------------------------------------------------- FP64
+struct FP64 {
+  static constexpr int W = 1;
+  static constexpr bool QUASI = false;
+  using T = MW<1>;
+  static __device__ __forceinline__ T zero() { return T{{0.0}}; }
+  static __device__ __forceinline__ T from(double a) { return T{{a}}; }
+  static __device__ __forceinline__ T add(const T& a, const T& b) { return T{{dadd(a.w[0], b.w[0])}}; }
+  static __device__ __forceinline__ T mul(const T& a, const T& b) { return T{{dmul(a.w[0], b.w[0])}}; }
+  static __device__ __forceinline__ T dxmul(double a, const T& b) { return T{{dmul(a, b.w[0])}}; }
+  static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return T{{dfma(a.w[0], b.w[0], c.w[0])}}; }
+  static __device__ __forceinline__ T dxmuladd(const T& c, double a, const T& b) { return T{{dfma(a, b.w[0], c.w[0])}}; }
+  static __device__ __forceinline__ T div(const T& a, const T& b) { return T{{__ddiv_rn(a.w[0], b.w[0])}}; }
+  static __device__ __forceinline__ void normalize(T&) {}
+  static __device__ __forceinline__ double collapse(const T& a) { return a.w[0]; }
+};
+
+// ---------------------------------------------------------------- DW
+struct DW {
+  static constexpr int W = 2;
+  static constexpr bool QUASI = false;
+  using T = MW<2>;
+  static __device__ __forceinline__ T zero() { return T{{0.0, 0.0}}; }
+  static __device__ __forceinline__ T from(double a) { return T{{a, 0.0}}; }
+  // Algorithm 5: e = fl((e + a2) + b2), then QuickTwoSum.
+  static __device__ __forceinline__ T add(const T& a, const T& b) {
+    double s, e;
+    two_sum(a.w[0], b.w[0], s, e);
+    e = dadd(dadd(e, a.w[1]), b.w[1]);
+    T c;
+    quick_two_sum(s, e, c.w[0], c.w[1]);
+    return c;
+  }
+  // Algorithm 6: fma with a1*b2 first, then a2*b1.
+  static __device__ __forceinline__ T mul(const T& a, const T& b) {
+    double p, e;
+    two_prod(a.w[0], b.w[0], p, e);
+    e = dfma(a.w[0], b.w[1], e);
+    e = dfma(a.w[1], b.w[0], e);
+    T c;
+    quick_two_sum(p, e, c.w[0], c.w[1]);
+    return c;
+  }
+  static __device__ __forceinline__ T dxmul(double a, const T& b) {
+    double p, e;
+    two_prod(a, b.w[0], p, e);
+    e = dfma(a, b.w[1], e);
+    T c;
+    quick_two_sum(p, e, c.w[0], c.w[1]);
+    return c;
+  }
+  static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return add(c, mul(a, b)); }
+  static __device__ __forceinline__ T dxmuladd(const T& c, double a, const T& b) { return add(c, dxmul(a, b)); }
+  static __device__ __forceinline__ T neg(const T& a) { return T{{dneg(a.w[0]), dneg(a.w[1])}}; }
+  static __device__ __forceinline__ T div(const T& a, const T& b) {
+    double q1 = __ddiv_rn(a.w[0], b.w[0]);
+    T r = add(a, neg(dxmul(q1, b)));
+    double q2 = __ddiv_rn(r.w[0], b.w[0]);
+    T c;
+    quick_two_sum(q1, q2, c.w[0], c.w[1]);
+    return c;
+  }
+  static __device__ __forceinline__ void normalize(T&) {}
+  static __device__ __forceinline__ double collapse(const T& a) { return dadd(a.w[0], a.w[1]); }
+};
+
+// ---------------------------------------------------------------- QDW
+template <bool NORM>
+struct QDWt {
+  static constexpr int W = 2;
+  static constexpr bool QUASI = true;
+  using T = MW<2>;
+  static __device__ __forceinline__ T zero() { return T{{0.0, 0.0}}; }
+  static __device__ __forceinline__ T from(double a) { return T{{a, 0.0}}; }
+  static __device__ __forceinline__ T add(const T& a, const T& b) {
+    T c;
+    two_sum(a.w[0], b.w[0], c.w[0], c.w[1]);
+    c.w[1] = dadd(dadd(c.w[1], a.w[1]), b.w[1]);
+    return c;
+  }
+  static __device__ __forceinline__ T mul(const T& a, const T& b) {
+    T c;
+    two_prod(a.w[0], b.w[0], c.w[0], c.w[1]);
+    c.w[1] = dfma(a.w[0], b.w[1], c.w[1]);
+    c.w[1] = dfma(a.w[1], b.w[0], c.w[1]);
+    return c;
+  }
+  static __device__ __forceinline__ T dxmul(double a, const T& b) {
+    T c;
+    two_prod(a, b.w[0], c.w[0], c.w[1]);
+    c.w[1] = dfma(a, b.w[1], c.w[1]);
+    return c;
+  }
+  static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return add(c, mul(a, b)); }
+  static __device__ __forceinline__ T dxmuladd(const T& c, double a, const T& b) { return add(c, dxmul(a, b)); }
+  static __device__ __forceinline__ T neg(const T& a) { return T{{dneg(a.w[0]), dneg(a.w[1])}}; }
+  // QDW normalisation: QuickTwoSum(c1, c2).
+  static __device__ __forceinline__ void renorm(T& a) { quick_two_sum(a.w[0], a.w[1], a.w[0], a.w[1]); }
+  static __device__ __forceinline__ T div(const T& a, const T& b) {
+    double q1 = __ddiv_rn(a.w[0], b.w[0]);
+    T r = add(a, neg(dxmul(q1, b)));
+    renorm(r);
+    double q2 = __ddiv_rn(r.w[0], b.w[0]);
+    T c;
+    quick_two_sum(q1, q2, c.w[0], c.w[1]);
+    return c;
+  }
+  static __device__ __forceinline__ void normalize(T& a) { if (NORM) renorm(a); }
+  static __device__ __forceinline__ double collapse(const T& a) { return dadd(a.w[0], a.w[1]); }
+};
+using QDW = QDWt<true>;
+using QDW_NN = QDWt<false>;
+
+// ---------------------------------------------------------------- QTW
+template <bool NORM>
+struct QTWt {
+  static constexpr int W = 3;
+  static constexpr bool QUASI = true;
+  using T = MW<3>;
+  static __device__ __forceinline__ T zero() { return T{{0.0, 0.0, 0.0}}; }
+  static __device__ __forceinline__ T from(double a) { return T{{a, 0.0, 0.0}}; }
+  // Algorithm 7.
+  static __device__ __forceinline__ T add(const T& a, const T& b) {
+    T c;
+    double e1, e2, e3;
+    two_sum(a.w[0], b.w[0], c.w[0], e1);
+    two_sum(a.w[1], b.w[1], c.w[1], e2);
+    two_sum(c.w[1], e1, c.w[1], e3);
+    c.w[2] = dadd(dadd(dadd(a.w[2], b.w[2]), e2), e3);
+    return c;
+  }
+  // Algorithm 8.
+  static __device__ __forceinline__ T mul(const T& a, const T& b) {
+    T c;
+    double e1, t2, e2, t3, e3, e4, e5;
+    two_prod(a.w[0], b.w[0], c.w[0], e1);
+    two_prod(a.w[0], b.w[1], t2, e2);
+    two_prod(a.w[1], b.w[0], t3, e3);
+    two_sum(t2, t3, c.w[1], e4);
+    two_sum(c.w[1], e1, c.w[1], e5);
+    double f1 = dfma(a.w[2], b.w[0], e2);
+    double f2 = dfma(a.w[1], b.w[1], e3);
+    double f3 = dfma(a.w[0], b.w[2], e4);
+    c.w[2] = dadd(dadd(dadd(f1, f2), f3), e5);
+    return c;
+  }
+  // Algorithm 10.
+  static __device__ __forceinline__ T dxmul(double a, const T& b) {
+    T c;
+    double e1, e2, e5;
+    two_prod(a, b.w[0], c.w[0], e1);
+    two_prod(a, b.w[1], c.w[1], e2);
+    two_sum(c.w[1], e1, c.w[1], e5);
+    c.w[2] = dadd(dfma(a, b.w[2], e2), e5);
+    return c;
+  }
+  static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return add(c, mul(a, b)); }
+  static __device__ __forceinline__ T dxmuladd(const T& c, double a, const T& b) { return add(c, dxmul(a, b)); }
+  static __device__ __forceinline__ T neg(const T& a) { return T{{dneg(a.w[0]), dneg(a.w[1]), dneg(a.w[2])}}; }
+  // Algorithm 9, VecSum3 as printed.
+  static __device__ __forceinline__ void renorm(T& a) {
+    two_sum(a.w[0], a.w[1], a.w[0], a.w[1]);
+    two_sum(a.w[1], a.w[2], a.w[1], a.w[2]);
+  }
+  static __device__ __forceinline__ T div(const T& a, const T& b) {
+    double q1 = __ddiv_rn(a.w[0], b.w[0]);
+    T r = add(a, neg(dxmul(q1, b)));
+    renorm(r);
+    double q2 = __ddiv_rn(r.w[0], b.w[0]);
+    r = add(r, neg(dxmul(q2, b)));
+    renorm(r);
+    double q3 = __ddiv_rn(r.w[0], b.w[0]);
+    T c{{q1, q2, q3}};
+    renorm(c);
+    return c;
+  }
+  static __device__ __forceinline__ void normalize(T& a) { if (NORM) renorm(a); }
+  static __device__ __forceinline__ double collapse(const T& a) { return dadd(a.w[0], dadd(a.w[1], a.w[2])); }
+};
+using QTW = QTWt<true>;
+using QTW_NN = QTWt<false>;
+
+// ---------------------------------------------------------------- TW
+struct TW {
+  static constexpr int W = 3;
+  static constexpr bool QUASI = false;
+  using T = MW<3>;
+  static __device__ __forceinline__ T zero() { return T{{0.0, 0.0, 0.0}}; }
+  static __device__ __forceinline__ T from(double a) { return T{{a, 0.0, 0.0}}; }
+
+  // Error-free VecSum, bottom-up, in place (N compile-time so the array stays
+  // in registers).
+  template <int N>
+  static __device__ __forceinline__ void vecsum(double (&x)[N]) {
+    double s = x[N - 1];
+#pragma unroll
+    for (int i = N - 2; i >= 0; --i) {
+      double hi, lo;
+      two_sum(x[i], s, hi, lo);
+      x[i + 1] = lo;
+      s = hi;
+    }
+    x[0] = s;
+  }
+  // Renormalisation to three words with branches on zero errors.  Written
+  // without dynamic register indexing: the open word index j selects one of
+  // three registers.
+  template <int N>
+  static __device__ __forceinline__ T renorm3(const double (&e)[N]) {
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+    int j = 0;
+    double eps = e[0];
+    bool stop = false;
+#pragma unroll
+    for (int i = 0; i + 1 < N; ++i) {
+      if (!stop) {
+        double hi, lo;
+        quick_two_sum(eps, e[i + 1], hi, lo);
+        if (j == 0) r0 = hi; else if (j == 1) r1 = hi; else r2 = hi;
+        if (nonzero(lo)) {
+          if (j >= 2) stop = true;
+          else { ++j; eps = lo; }
+        } else {
+          eps = hi;
+        }
+      }
+    }
+    if (!stop) { if (j == 0) r0 = eps; else if (j == 1) r1 = eps; else r2 = eps; }
+    return T{{r0, r1, r2}};
+  }
+  static __device__ __forceinline__ T add(const T& a, const T& b) {
+    double z[6];
+    int i = 0, k = 0;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      // Merge by decreasing magnitude, ties from a first.
+      double ai = (i == 0) ? a.w[0] : (i == 1) ? a.w[1] : a.w[2];
+      double bk = (k == 0) ? b.w[0] : (k == 1) ? b.w[1] : b.w[2];
+      bool take_a = (k >= 3) || (i < 3 && mag_ge(ai, bk));
+      z[m] = take_a ? ai : bk;
+      if (take_a) ++i; else ++k;
+    }
+    vecsum<6>(z);
+    return renorm3<6>(z);
+  }
+  static __device__ __forceinline__ T mul(const T& a, const T& b) {
+    double p00, e00, p01, e01, p10, e10;
+    two_prod(a.w[0], b.w[0], p00, e00);
+    two_prod(a.w[0], b.w[1], p01, e01);
+    two_prod(a.w[1], b.w[0], p10, e10);
+    double t, s3, s1, s2;
+    two_sum(p01, p10, t, s3);
+    two_sum(e00, t, s1, s2);
+    double c = dadd(s2, s3);
+    c = dadd(c, e01);
+    c = dadd(c, e10);
+    c = dfma(a.w[2], b.w[0], c);
+    c = dfma(a.w[1], b.w[1], c);
+    c = dfma(a.w[0], b.w[2], c);
+    double z[3] = {p00, s1, c};
+    vecsum<3>(z);
+    return renorm3<3>(z);
+  }
+  static __device__ __forceinline__ T dxmul(double a, const T& b) {
+    double p00, e00, p01, e01;
+    two_prod(a, b.w[0], p00, e00);
+    two_prod(a, b.w[1], p01, e01);
+    double s1, s2;
+    two_sum(e00, p01, s1, s2);
+    double c = dadd(s2, e01);
+    c = dfma(a, b.w[2], c);
+    double z[3] = {p00, s1, c};
+    vecsum<3>(z);
+    return renorm3<3>(z);
+  }
+  static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return add(c, mul(a, b)); }
+  static __device__ __forceinline__ T dxmuladd(const T& c, double a, const T& b) { return add(c, dxmul(a, b)); }
+  static __device__ __forceinline__ T neg(const T& a) { return T{{dneg(a.w[0]), dneg(a.w[1]), dneg(a.w[2])}}; }
+  static __device__ __forceinline__ T div(const T& a, const T& b) {
+    double q1 = __ddiv_rn(a.w[0], b.w[0]);
+    T r = add(a, neg(dxmul(q1, b)));
+    double q2 = __ddiv_rn(r.w[0], b.w[0]);
+    r = add(r, neg(dxmul(q2, b)));
+    double q3 = __ddiv_rn(r.w[0], b.w[0]);
+    double z[3] = {q1, q2, q3};
+    vecsum<3>(z);
+    return renorm3<3>(z);
+  }
+  static __device__ __forceinline__ void normalize(T&) {}
+  static __device__ __forceinline__ double collapse(const T& a) { return dadd(a.w[0], dadd(a.w[1], a.w[2])); }
+};
+
+template <class A>
+__device__ __forceinline__ typename A::T neg(const typename A::T& a) {
+  typename A::T c;
+#pragma unroll
+  for (int k = 0; k < A::W; ++k) c.w[k] = dneg(a.w[k]);
+  return c;
+}
+
+}  // namespace mw

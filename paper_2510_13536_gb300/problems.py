@@ -321,3 +321,44 @@ def batch_specs(nsys: int, seed: int, nmin: int = 1000, nmax: int = 200000):
 def build_batch_system(spec) -> tuple[CSR, np.ndarray]:
     A = laplacian_3d(spec["m"], spec["shift"]) if spec["kind"] == "3d" else laplacian_2d(spec["m"], spec["shift"])
     return A, rhs_uniform(A.n, spec["rhs_seed"])
+
+
+# ---------------------------------------------------------------------------
+# Named workloads (the five configurations the solver is measured on).
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    "c1": "2-D Poisson 5-point, 64x64 (n=4096), b = A*1, x0 = 0, tol 1e-12, maxit 2000",
+    "c2": "3-D Poisson 7-point, 128^3 (n=2,097,152), b = 2U-1, x0 = 0, tol 1e-14, maxit 20000",
+    "c2_twin": "3-D Poisson 7-point, 128^3, b = A*1 (x* = 1), x0 = 0, tol 1e-14, maxit 20000",
+    "c3": "power-law graph Laplacian n=1e6, mean degree 30, max 1000, weights lognormal(0,2), +1e-8 I, b ~ N(0,1)",
+    "c3_twin": "dyadic power-law twin n=1e6 (weights on 2^-20 grid, shift 2^-27), b = A*1 (x* = 1)",
+    "c5": "2-D variable-coefficient diffusion 512x512, theta lognormal(0,1), b, w ~ N(0,1)",
+}
+
+
+def workload(name: str):
+    """(A, b, tol, maxit) of a named workload; see WORKLOADS."""
+    if name == "c1":
+        A = laplacian_2d(64)
+        return A, rhs_ones_exact(A), 1e-12, 2000
+    if name == "c2":
+        A = laplacian_3d(128)
+        return A, rhs_uniform(A.n, SEED_BASE + 2), 1e-14, 20000
+    if name == "c2_twin":
+        A = laplacian_3d(128)
+        return A, rhs_ones_exact(A), 1e-14, 20000
+    if name == "c3":
+        A = power_law_laplacian(1_000_000, SEED_BASE + 3)
+        return A, rhs_normal(A.n, SEED_BASE + 3 + 100), 1e-14, 20000
+    if name == "c3_twin":
+        A = power_law_laplacian(1_000_000, SEED_BASE + 3, dyadic=True)
+        return A, rhs_ones_exact(A), 1e-14, 20000
+    if name == "c5":
+        A = diffusion_2d(512, SEED_BASE + 5)
+        return A, rhs_normal(A.n, SEED_BASE + 5 + 100), 1e-20, 20000
+    raise KeyError(name)
+
+
+def c5_loss_weights(n: int) -> np.ndarray:
+    """w of the loss L = w^T x of the differentiable-solve workload."""
+    return rhs_normal(n, SEED_BASE + 5 + 200)
