@@ -408,11 +408,12 @@ template <class A> inline void store(double* v, int64_t n, int64_t i, const type
 //       and sums their products left to right starting from its first
 //       product; lanes without entries are absent; lanes are combined by the
 //       pairwise tree below.
-//     * dot: leaf i is u_i (x) v_i; rows are cut into tiles of R consecutive
-//       rows (R = T/V in the SpMV, R = T in the vector kernels); a tile's
-//       leaves are combined by the pairwise tree; tile t belongs to block
-//       t mod G, which adds its tiles left to right in increasing t; the G
-//       block values are combined by the pairwise tree (absent blocks skipped).
+//     * dot: leaf i is u_i (x) v_i.  Rows are cut into tiles of R consecutive
+//       rows (R = T/V in the SpMV, R = T in the vector kernels); tile t belongs
+//       to block t mod G.  Slot s of block b adds the leaves of rows t*R + s of
+//       its tiles t = b, b+G, b+2G, ... left to right (starting from the first
+//       one); the R slots of a block are combined by the pairwise tree, then
+//       the G block values by the pairwise tree (absent slots/blocks skipped).
 //   Pairwise tree over slots 0..S-1: for h = 1, 2, 4, ... < S, every slot s
 //   that is a multiple of 2h takes v[s] = v[s] (+) v[s+h] when both are
 //   present (just v[s+h] if only that one is); result in slot 0.
@@ -476,16 +477,20 @@ typename A::T reduce_leaves(const std::vector<typename A::T>& leaf, int64_t R, i
   int64_t ntiles = (n + R - 1) / R;
   std::vector<T> blk(G);
   std::vector<char> bpres(G, 0);
-  for (int64_t t = 0; t < ntiles; ++t) {
-    int64_t r0 = t * R;
-    int64_t cnt = std::min<int64_t>(R, n - r0);
-    std::vector<T> sl(R);
+  for (int b = 0; b < G && b < ntiles; ++b) {
+    std::vector<T> slot(R);
     std::vector<char> pr(R, 0);
-    for (int64_t s = 0; s < cnt; ++s) { sl[s] = leaf[r0 + s]; pr[s] = 1; }
-    pair_tree<A>(sl, pr);
-    int b = (int)(t % G);
-    if (bpres[b]) blk[b] = A::add(blk[b], sl[0]);
-    else { blk[b] = sl[0]; bpres[b] = 1; }
+    for (int64_t t = b; t < ntiles; t += G) {
+      for (int64_t s = 0; s < R; ++s) {
+        int64_t i = t * R + s;
+        if (i >= n) break;
+        if (pr[s]) slot[s] = A::add(slot[s], leaf[i]);
+        else { slot[s] = leaf[i]; pr[s] = 1; }
+      }
+    }
+    pair_tree<A>(slot, pr);
+    blk[b] = slot[0];
+    bpres[b] = 1;
   }
   pair_tree<A>(blk, bpres);
   return blk[0];
