@@ -119,6 +119,31 @@ class ClockSampler:
                 "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None], default=None)}
 
 
+def _kernel_source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("mw_device.cuh", "cg_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2510_13536_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(arith):
+    """DRAM bytes per k_spmv launch from the committed ncu summary, or None when
+    the summary is missing or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"k_spmv_{arith}_c2.md")
+    try:
+        kv = {}
+        for line in open(path):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("kernel_source_digest") != _kernel_source_digest():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def _golden_iters(arith):
     try:
         g = json.load(open(GOLDEN))
@@ -186,6 +211,8 @@ def run_gpu(args):
     from paper_2510_13536_gb300 import solver as mw
 
     A, b_np, tol, maxit = P.workload(WORKLOAD)
+    if args.maxit is not None:
+        maxit = args.maxit
     M = mw.CSRMatrix.from_csr(A)
     dev = torch.device("cuda", torch.cuda.current_device())
     b = torch.as_tensor(b_np, device=dev)
@@ -226,6 +253,12 @@ def run_gpu(args):
     clocks = clk.summary()
     it = iters[-1]
     status, relres = r.status, r.relres
+    if args.only_solve:
+        if rk == 0:
+            print(json.dumps({"metric": METRIC, "value": ms / 1e3, "unit": "s", "ms_per_step": ms, "iters": it,
+                              "status": status, "relres": relres, "steps": args.steps, "warmup": args.warmup,
+                              "maxit": maxit, "plan": list(M.plan), "clocks": clocks, "only_solve": True}))
+        return 0
 
     # DW solve of the same system (QTW / DW time ratio).
     xdw = torch.zeros((2, A.n), dtype=torch.float64, device=dev)
@@ -256,12 +289,7 @@ def run_gpu(args):
     ops = per_nnz * A.nnz + per_row * A.n
     achieved = ops / (spmv_ms * 1e-3)
     spmv_bytes = 12 * A.nnz + 8 * (A.n + 1) + 2 * 8 * w * A.n
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "k_spmv_qtw_c2_traffic.json")))
-        traffic = prof.get("dram_bytes_per_launch")
-    except Exception:
-        pass
+    traffic = _profiled_traffic(arith)
 
     # End to end through the C ABI with host buffers (pinned), copies included.
     bh = torch.empty(A.n, dtype=torch.float64, pin_memory=True)
@@ -327,6 +355,9 @@ def main():
     ap.add_argument("--impl", default="mwcg", choices=["mwcg", "reference"])
     ap.add_argument("--arith", default="qtw", choices=["qtw", "dw", "qdw", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--only-solve", action="store_true",
+                    help="time the solves only (no DW, profile, e2e or CPU legs); used for ncu captures")
+    ap.add_argument("--maxit", type=int, default=None, help="override the iteration limit (ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

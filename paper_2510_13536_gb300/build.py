@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmwcg.so")
 
 SOURCES = ["capi.cu", "batched.cu", "inst_fp64.cu", "inst_dw.cu", "inst_qdw.cu", "inst_tw.cu", "inst_qtw.cu"]
-HEADERS = ["mw_device.cuh", "cg_kernels.cuh", "batched.cuh"]
+HEADERS = ["mw_device.cuh", "mw_int.cuh", "cg_kernels.cuh", "batched.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", INCLUDE, "-I", CSRC]
@@ -55,6 +55,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    # MWCG_NATIVE_EFT=1 builds the printed FP64 sequences for TwoSum/QuickTwoSum
+    # instead of the integer-pipe error recovery (same results, for A/B timing).
+    if os.environ.get("MWCG_NATIVE_EFT") == "1":
+        extra.append("-DMWCG_NATIVE_EFT")
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

@@ -18,6 +18,7 @@
 // integer pipe retires 64, so the FP64 instruction count is the cost model.
 #pragma once
 #include <cstdint>
+#include "mw_int.cuh"
 
 namespace mw {
 
@@ -39,8 +40,12 @@ __device__ __forceinline__ bool nonzero(double a) {
   return ((unsigned long long)__double_as_longlong(a) << 1) != 0ULL;
 }
 
-// Algorithm 2, TwoSum.
-__device__ __forceinline__ void two_sum(double a, double b, double& x, double& y) {
+// Algorithm 2, TwoSum.  x = fl(a+b) on the FP64 pipe; the exact error y is
+// recovered from the bit patterns on the integer pipe (mw_int.cuh), which
+// yields the same number as the printed sequence.  Where that path declines
+// (non-finite, overflow-prone or tiny operands) the printed sequence runs.
+// Building with -DMWCG_NATIVE_EFT keeps the printed sequence everywhere.
+__device__ __forceinline__ void two_sum_printed(double a, double b, double& x, double& y) {
   double s = dadd(a, b);
   double z = dsub(s, a);
   double t1 = dsub(a, dsub(s, z));
@@ -48,11 +53,35 @@ __device__ __forceinline__ void two_sum(double a, double b, double& x, double& y
   y = dadd(t1, t2);
   x = s;
 }
-// Algorithm 3, QuickTwoSum.
+__device__ __forceinline__ void two_sum(double a, double b, double& x, double& y) {
+#if defined(MWCG_NATIVE_EFT)
+  two_sum_printed(a, b, x, y);
+#else
+  const double s = dadd(a, b);
+  double e;
+  if (!mwi::add_error(a, b, s, e)) {
+    const double z = dsub(s, a);
+    e = dadd(dsub(a, dsub(s, z)), dsub(b, z));
+  }
+  x = s;
+  y = e;
+#endif
+}
+// Algorithm 3, QuickTwoSum.  When the exponent of a is at least that of b
+// (or b = 0) the printed sequence returns the exact error, so the integer
+// path is used; otherwise the printed sequence runs as written.
 __device__ __forceinline__ void quick_two_sum(double a, double b, double& x, double& y) {
+#if defined(MWCG_NATIVE_EFT)
   double s = dadd(a, b);
   y = dadd(dsub(a, s), b);
   x = s;
+#else
+  const double s = dadd(a, b);
+  double e;
+  if (!(mwi::quick_exact(a, b) && mwi::add_error(a, b, s, e))) e = dadd(dsub(a, s), b);
+  x = s;
+  y = e;
+#endif
 }
 // Algorithm 4, TwoProdFMA.
 __device__ __forceinline__ void two_prod(double a, double b, double& x, double& y) {

@@ -1,0 +1,115 @@
+// Exact rounding error of an FP64 addition, computed on the integer pipe.
+//
+// TwoSum (Algorithm 2 of the paper) and QuickTwoSum (Algorithm 3, when its
+// precondition holds) return x = fl(a+b) and the exact error y = (a+b) - x,
+// which is an FP64 number whenever no overflow or underflow gets in the way.
+// On GB300 the FP64 pipe retires 2 operations per clock per SM and the
+// integer pipe 64, so recovering y from the bit patterns of a, b and x with
+// ~70 integer instructions is cheaper than the five FP64 operations of the
+// printed sequence that follow fl(a+b).  The result is the same number, so the
+// bits are identical to the printed sequence (which returns +0, never -0,
+// when the error is zero).
+//
+// Derivation (IEEE binary64, round to nearest even): order the operands by
+// magnitude, |h| >= |l|, with biased exponent fields eh >= el.  Every one of
+// h, l and x = fl(h+l) is an integer multiple of u = 2^(el-1075) (x is either
+// exact or at least 2^52 u in magnitude).  With significands mh, ml, mx
+// (hidden bit included) and d = eh - el, dx = ex - el:
+//   |h+l| / u = mh*2^d (+|-) ml,    |x| / u = mx*2^dx,
+// and |y| <= ulp(x)/2 <= 2^55 u, so Y = (|h+l| - |x|) / u is recovered exactly
+// by 64-bit wrap-around arithmetic even though the two terms do not fit.
+// Then y = sign(h) * Y * u, packed by locating Y's leading bit.  Special
+// cases: l = 0 gives y = +0; d > 55 gives x = h and y = l; x = 0 or dx < 0
+// (the sum is exact) gives y = +0.  The integer path declines (returns false)
+// when h is not finite or may overflow (eh >= 2046) or when l is tiny
+// (el < 110, so that y could be subnormal); callers then run the printed
+// FP64 sequence.
+//
+// Host-compilable (plain C++) so that it can also be checked on the CPU.
+#pragma once
+#include <stdint.h>
+#include <string.h>
+
+#if defined(__CUDACC__)
+#define MWI_HD __host__ __device__ __forceinline__
+#else
+#define MWI_HD inline
+#endif
+
+namespace mwi {
+
+MWI_HD uint64_t bits_of(double v) {
+#if defined(__CUDA_ARCH__)
+  return (uint64_t)__double_as_longlong(v);
+#else
+  uint64_t u;
+  memcpy(&u, &v, sizeof u);
+  return u;
+#endif
+}
+
+MWI_HD double from_bits(uint64_t u) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)u);
+#else
+  double v;
+  memcpy(&v, &u, sizeof v);
+  return v;
+#endif
+}
+
+// Index of the most significant set bit of v != 0.
+MWI_HD int msb64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+  return 63 - __clzll((long long)v);
+#else
+  return 63 - __builtin_clzll(v);
+#endif
+}
+
+constexpr uint64_t kAbs = 0x7fffffffffffffffULL;
+constexpr uint64_t kFrac = 0x000fffffffffffffULL;
+constexpr uint64_t kHidden = 0x0010000000000000ULL;
+
+// y = (a + b) - x exactly, given x = fl(a + b).  Returns false when the
+// integer path does not apply (see above); y is then left untouched.
+MWI_HD bool add_error(double a, double b, double x, double& y) {
+  const uint64_t ua = bits_of(a), ub = bits_of(b), ux = bits_of(x);
+  const bool swap = (ua & kAbs) < (ub & kAbs);
+  const uint64_t h = swap ? ub : ua;
+  const uint64_t l = swap ? ua : ub;
+  const int eh = (int)((h >> 52) & 0x7ff);
+  const int el = (int)((l >> 52) & 0x7ff);
+  if (eh >= 2046) return false;                 // inf/NaN or possible overflow
+  if ((l & kAbs) == 0) { y = 0.0; return true; }  // l = +-0: the sum is exact
+  if (el < 110) return false;                   // y might be subnormal
+  const int d = eh - el;
+  if (d > 55) { y = from_bits(l); return true; }  // l is below half an ulp of h: x = h
+  if ((ux & kAbs) == 0) { y = 0.0; return true; }  // exact cancellation
+  const int ex = (int)((ux >> 52) & 0x7ff);
+  const int dx = ex - el;
+  if (dx < 0) { y = 0.0; return true; }         // |x| < 2^52 u: the sum is exact
+  const uint64_t mh = (h & kFrac) | kHidden;
+  const uint64_t ml = (l & kFrac) | kHidden;
+  const uint64_t mx = (ux & kFrac) | kHidden;
+  const uint64_t H = mh << d;                   // d <= 55, wraps modulo 2^64
+  const uint64_t T = (((ua ^ ub) >> 63) == 0) ? H + ml : H - ml;
+  const uint64_t Y = T - (mx << dx);            // dx <= 56
+  if (Y == 0) { y = 0.0; return true; }
+  const bool neg = (int64_t)Y < 0;
+  const uint64_t M = neg ? (uint64_t)0 - Y : Y;   // |Y| < 2^56, at most 53 significant bits
+  const int L = msb64(M);
+  const uint64_t mant = (L <= 52) ? (M << (52 - L)) : (M >> (L - 52));
+  const uint64_t sign = ((h >> 63) ^ (neg ? 1u : 0u)) & 1u;
+  y = from_bits((sign << 63) | ((uint64_t)(L + el - 52) << 52) | (mant & kFrac));
+  return true;
+}
+
+// Precondition under which QuickTwoSum (Algorithm 3) returns the exact error:
+// exponent field of a >= exponent field of b, or b = +-0.
+MWI_HD bool quick_exact(double a, double b) {
+  const uint64_t ua = bits_of(a), ub = bits_of(b);
+  return ((ub & kAbs) == 0) || (((ua >> 52) & 0x7ff) >= ((ub >> 52) & 0x7ff));
+}
+
+}  // namespace mwi

@@ -1,0 +1,142 @@
+"""The integer-pipe rounding-error routine (csrc/mw_int.cuh) checked on the CPU.
+
+mw_int.cuh compiles as plain C++; a small shim exposes it to numpy.  Its
+result must equal, bit for bit, the error term of the printed TwoSum
+(Algorithm 2) and, where QuickTwoSum's precondition holds, of QuickTwoSum
+(Algorithm 3), evaluated here with numpy's IEEE float64 operations; on a
+subset it is also checked against exact rational arithmetic.
+"""
+import ctypes
+import os
+import random
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2510_13536_gb300", "csrc")
+
+SHIM = r"""
+#include "mw_int.cuh"
+extern "C" void add_error_batch(long n, const double* a, const double* b, const double* x, double* y, int* ok) {
+  for (long i = 0; i < n; ++i) { double t = 0.0; ok[i] = mwi::add_error(a[i], b[i], x[i], t) ? 1 : 0; y[i] = t; }
+}
+extern "C" void quick_exact_batch(long n, const double* a, const double* b, int* ok) {
+  for (long i = 0; i < n; ++i) ok[i] = mwi::quick_exact(a[i], b[i]) ? 1 : 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    d = tmp_path_factory.mktemp("mwi")
+    src = d / "shim.cpp"
+    src.write_text(SHIM)
+    lib = d / "libmwi.so"
+    subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-I", CSRC,
+                    "-o", str(lib), str(src)], check=True)
+    L = ctypes.CDLL(str(lib))
+    P = ctypes.c_void_p
+    L.add_error_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
+    L.quick_exact_batch.argtypes = [ctypes.c_long, P, P, P]
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def add_error(L, a, b, x):
+    y = np.zeros_like(a)
+    ok = np.zeros(a.size, dtype=np.int32)
+    L.add_error_batch(a.size, _p(a), _p(b), _p(x), _p(y), _p(ok))
+    return y, ok.astype(bool)
+
+
+def printed_two_sum(a, b):
+    with np.errstate(all="ignore"):
+        s = a + b
+        z = s - a
+        y = (a - (s - z)) + (b - z)
+    return s, y
+
+
+def printed_quick_two_sum(a, b):
+    with np.errstate(all="ignore"):
+        s = a + b
+        y = (a - s) + b
+    return s, y
+
+
+def inputs(seed, n):
+    rng = np.random.default_rng(seed)
+    e = rng.integers(-1000, 1000, size=n)
+    a = rng.uniform(1, 2, size=n) * np.exp2(e) * rng.choice([-1.0, 1.0], size=n)
+    kind = rng.integers(0, 8, size=n)
+    gap = rng.integers(-60, 61, size=n)
+    b = rng.uniform(1, 2, size=n) * np.exp2(np.clip(e + gap, -1074, 1023)) * rng.choice([-1.0, 1.0], size=n)
+    # near cancellation
+    m = kind == 1
+    b[m] = -a[m] * (1 + rng.choice([-1.0, 1.0], size=m.sum()) * rng.uniform(0, 1, m.sum()) *
+                    np.exp2(-rng.integers(1, 54, m.sum())))
+    # exact half-ulp ties and neighbours around the rounding point
+    m = kind == 2
+    k = rng.integers(50, 58, m.sum())
+    b[m] = np.ldexp(np.sign(rng.uniform(-1, 1, m.sum())) * rng.integers(1, 4, m.sum()), np.frexp(a[m])[1] - k)
+    # integers / small dyadics (many exact sums)
+    m = kind == 3
+    a[m] = rng.integers(-2 ** 53, 2 ** 53, m.sum()).astype(np.float64)
+    b[m] = rng.integers(-2 ** 20, 2 ** 20, m.sum()).astype(np.float64)
+    # powers of two against small opposite values
+    m = kind == 4
+    a[m] = np.exp2(rng.integers(-500, 500, m.sum())) * rng.choice([-1.0, 1.0], m.sum())
+    b[m] = -a[m] * rng.uniform(0, 1, m.sum()) * np.exp2(-rng.integers(40, 60, m.sum()))
+    # zeros, signed zeros, tiny and huge values, infinities, NaN
+    m = np.nonzero(kind == 5)[0]
+    sp = np.array([0.0, -0.0, 5e-324, -2.2250738585072014e-308, 1e-300, 1.7e308, -1.7e308, np.inf, -np.inf, np.nan])
+    b[m] = sp[rng.integers(0, sp.size, m.size)]
+    m2 = m[::3]
+    a[m2] = sp[rng.integers(0, sp.size, m2.size)]
+    return a, b
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_matches_printed_two_sum(shim, seed):
+    a, b = inputs(seed, 400_000)
+    for (u, v) in ((a, b), (b, a)):
+        x, y_ref = printed_two_sum(u, v)
+        y, ok = add_error(shim, u, v, x)
+        fin = np.isfinite(u) & np.isfinite(v) & np.isfinite(x)
+        # Where the integer path applies, the bits agree with the printed sequence.
+        assert np.array_equal(y[ok].view(np.uint64), y_ref[ok].view(np.uint64))
+        # It declines only for non-finite/overflow-prone or tiny operands.
+        big = np.maximum(np.abs(u), np.abs(v))
+        small = np.minimum(np.abs(u), np.abs(v))
+        expected_decline = ~fin | (big >= 2.0 ** 1023) | ((small < 2.0 ** (110 - 1023)) & (small != 0))
+        assert np.array_equal(~ok, expected_decline)
+        assert ok.mean() > 0.8
+
+
+def test_matches_printed_quick_two_sum_when_precondition_holds(shim):
+    a, b = inputs(7, 400_000)
+    q = np.zeros(a.size, dtype=np.int32)
+    shim.quick_exact_batch(a.size, _p(a), _p(b), _p(q))
+    q = q.astype(bool)
+    x, y_ref = printed_quick_two_sum(a, b)
+    y, ok = add_error(shim, a, b, x)
+    m = q & ok
+    assert m.sum() > 100_000
+    assert np.array_equal(y[m].view(np.uint64), y_ref[m].view(np.uint64))
+
+
+def test_exact_rational_error(shim):
+    a, b = inputs(11, 20_000)
+    with np.errstate(all="ignore"):
+        x = a + b
+    y, ok = add_error(shim, a, b, x)
+    idx = np.nonzero(ok)[0]
+    for i in idx[::7]:
+        assert Fraction(float(y[i])) == Fraction(float(a[i])) + Fraction(float(b[i])) - Fraction(float(x[i]))
+        assert not (y[i] == 0 and np.signbit(y[i]))        # zero error is +0, as the printed sequence gives
