@@ -214,6 +214,23 @@ def run_gpu(args):
     if args.maxit is not None:
         maxit = args.maxit
     M = mw.CSRMatrix.from_csr(A)
+    if args.kernels_only:
+        import ctypes
+        from paper_2510_13536_gb300 import _capi
+        dev0 = torch.device("cuda", torch.cuda.current_device())
+        bb = torch.as_tensor(b_np, device=dev0)
+        xx = torch.zeros((WORDS[args.arith], A.n), dtype=torch.float64, device=dev0)
+        kms = (ctypes.c_double * 3)()
+        _capi.check(_capi.load().mwcg_profile_kernels(
+            M.handle, ctypes.c_void_p(bb.data_ptr()), ctypes.c_void_p(xx.data_ptr()), mw.arith_id(args.arith),
+            int(args.kernels_only), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), kms))
+        per_nnz, per_row = SPMV_OPS.get(args.arith, (0, 0))
+        ops = per_nnz * A.nnz + per_row * A.n
+        print(json.dumps({"kernels_only": int(args.kernels_only), "arith": args.arith, "plan": list(M.plan),
+                          "kernel_ms": {"spmv_dot": kms[0], "update_dot": kms[1], "p_update": kms[2]},
+                          "spmv_fp64_ops_per_launch": ops,
+                          "spmv_frac_of_fp64_peak": ops / (kms[0] * 1e-3) / FP64_PEAK_OPS if kms[0] else None}))
+        return 0
     dev = torch.device("cuda", torch.cuda.current_device())
     b = torch.as_tensor(b_np, device=dev)
     arith = args.arith
@@ -358,6 +375,9 @@ def main():
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no DW, profile, e2e or CPU legs); used for ncu captures")
     ap.add_argument("--maxit", type=int, default=None, help="override the iteration limit (ncu captures)")
+    ap.add_argument("--kernels-only", type=int, default=0, metavar="N",
+                    help="run N iterations with each kernel launched on its own (mwcg_profile_kernels) and print "
+                         "their mean durations; used for ncu captures")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -141,19 +141,25 @@ int mwcg_solve_history(mwcg_csr* A, const double* b, double* x, int arith, doubl
                        double* hist, void* stream, int32_t* iters_out, double* relres_out);
 
 /* Solve many independent systems in one persistent kernel launch.
- *   nsys             number of systems;
- *   A[s]             handles (distinct or repeated);
+ *   nsys             number of systems (>= 0);
+ *   A[s]             distinct handles (a handle repeated in one batch is
+ *                    MWCG_ERR_ARG: each system uses its handle's workspace);
  *   b[s], x[s]       device pointers as in mwcg_solve (x[s] holds
  *                    mwcg_words(arith[s]) * n_s doubles, x0 on entry);
  *   arith[s], tol[s], maxit[s]  per system (host arrays);
  *   iters_out[s], relres_out[s], status_out[s]  host arrays (may be NULL).
- * Each system runs the same iteration, in the same summation order as
- * mwcg_solve with plan {1, 256, 1} on that matrix (one block per system).
+ * Workers are thread-block clusters of mwcg_batched_cluster_size() CTAs that
+ * take systems from a device queue (largest first) and run each solve to its
+ * end; a system's summation order, and so its result bits, equal those of
+ * mwcg_solve with plan {V of its handle, 256, mwcg_batched_cluster_size()}.
  * Returns MWCG_OK when the launch succeeded (per-system outcomes are in
  * status_out), or an error. */
 int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b, double* const* x,
                        const int32_t* arith, const double* tol, const int32_t* maxit, void* stream,
                        int32_t* iters_out, double* relres_out, int32_t* status_out);
+
+/* Number of CTAs per worker cluster used by mwcg_solve_batched. */
+int mwcg_batched_cluster_size(void);
 
 /* Adjoint of a solve, for L with dL/dx = gx (device double[n]):
  *   lambda = CG(A, gx) in the same arithmetic from lambda0 = 0 (A symmetric,

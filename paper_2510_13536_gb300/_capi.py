@@ -22,7 +22,7 @@ EXPORTS = [
     "mwcg_words", "mwcg_last_error", "mwcg_create_csr", "mwcg_destroy_csr", "mwcg_update_values",
     "mwcg_n", "mwcg_nnz", "mwcg_get_plan", "mwcg_set_plan", "mwcg_solve", "mwcg_solve_host",
     "mwcg_solve_history", "mwcg_solve_batched", "mwcg_adjoint", "mwcg_spmv", "mwcg_dot",
-    "mwcg_word_op", "mwcg_collapse", "mwcg_profile_kernels",
+    "mwcg_word_op", "mwcg_collapse", "mwcg_profile_kernels", "mwcg_batched_cluster_size",
 ]
 
 
@@ -71,6 +71,7 @@ def load(path: str | None = None):
         "mwcg_word_op": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, i64, P, P, P, P]),
         "mwcg_collapse": (ctypes.c_int, [P, i32, i64, P, P]),
         "mwcg_profile_kernels": (ctypes.c_int, [P, P, P, ctypes.c_int, i32, P, P]),
+        "mwcg_batched_cluster_size": (ctypes.c_int, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -55,10 +55,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
-    # MWCG_NATIVE_EFT=1 builds the printed FP64 sequences for TwoSum/QuickTwoSum
-    # instead of the integer-pipe error recovery (same results, for A/B timing).
+    # MWCG_EFT=0|1|2 selects the TwoSum implementation and MWCG_QTS_INT=1 the
+    # integer-pipe QuickTwoSum (same results; for A/B timing); MWCG_NATIVE_EFT=1
+    # is MWCG_EFT=0.
     if os.environ.get("MWCG_NATIVE_EFT") == "1":
         extra.append("-DMWCG_NATIVE_EFT")
+    if os.environ.get("MWCG_EFT") in ("0", "1", "2"):
+        extra.append("-DMWCG_EFT=" + os.environ["MWCG_EFT"])
+    if os.environ.get("MWCG_QTS_INT") == "1":
+        extra.append("-DMWCG_QTS_INT=1")
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

@@ -12,13 +12,21 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
 #include "mwcg.h"
 #include "cg_kernels.cuh"
+#include "batched.cuh"
+
+namespace mwb_host {
+int cluster_size();
+cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int* clusters_out);
+}  // namespace mwb_host
 
 namespace mwk {
 KernelTable table_fp64();
@@ -276,11 +284,49 @@ int ensure_ws(mwcg_csr* A) {
   return MWCG_OK;
 }
 
+// MWCG_EAGER=1 in the environment runs the solve without the CUDA graph: the
+// host launches the same kernels, 16 iterations at a time, and reads the
+// device's stop flag between batches (profilers cannot see kernels inside a
+// graph with conditional nodes).
+bool eager_mode() {
+  const char* e = std::getenv("MWCG_EAGER");
+  return e && e[0] == '1';
+}
+
+int run_eager(mwcg_csr* A, int arith, cudaStream_t s) {
+  const mwk::KernelTable* kt = table(arith);
+  mwk::Csr M = csr_view(A);
+  mwk::Work W = work_view(A, 0, 0);
+  const int G = A->plan.G;
+  const size_t smem = red_smem(G);
+  int mode0 = 0, mode1 = 1;
+  void* a_spmv0[] = {(void*)&M, (void*)&W, (void*)&mode0};
+  void* a_spmv1[] = {(void*)&M, (void*)&W, (void*)&mode1};
+  void* a_mw[] = {(void*)&M, (void*)&W};
+  CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
+  CK(cudaLaunchKernel(kt->init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
+  CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
+  mwk::DevState* h = A->h_st;
+  const int64_t batches = (int64_t)h->maxit / 16 + 2;
+  for (int64_t bt = 0; bt < batches; ++bt) {
+    CK(cudaMemcpyAsync(h, A->st, sizeof *h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->done) break;
+    for (int i = 0; i < 16; ++i) {
+      CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv1, smem, s));
+      CK(cudaLaunchKernel(kt->update, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
+      CK(cudaLaunchKernel(kt->pupdate, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
+    }
+  }
+  return MWCG_OK;
+}
+
 int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
               cudaStream_t s, int32_t* iters_out, double* relres_out) {
   int rc;
   if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
-  if ((rc = ensure_graph(A, arith)) != MWCG_OK) return rc;
+  const bool eager = eager_mode();
+  if (!eager && (rc = ensure_graph(A, arith)) != MWCG_OK) return rc;
   mwk::DevState* h = A->h_st;
   std::memset(h, 0, sizeof *h);
   h->b = b;
@@ -289,7 +335,11 @@ int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, in
   h->tol = tol;
   h->maxit = maxit;
   CK(cudaMemcpyAsync(A->st, h, sizeof *h, cudaMemcpyHostToDevice, s));
-  CK(cudaGraphLaunch(A->graphs[arith].exec, s));
+  if (eager) {
+    if ((rc = run_eager(A, arith, s)) != MWCG_OK) return rc;
+  } else {
+    CK(cudaGraphLaunch(A->graphs[arith].exec, s));
+  }
   CK(cudaMemcpyAsync(h, A->st, sizeof *h, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (iters_out) *iters_out = h->iters;
@@ -647,12 +697,69 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   return err;
 }
 
+int mwcg_batched_cluster_size(void) { return mwb_host::cluster_size(); }
+
 int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b, double* const* x,
                        const int32_t* arith, const double* tol, const int32_t* maxit, void* stream,
                        int32_t* iters_out, double* relres_out, int32_t* status_out) {
-  (void)nsys; (void)A; (void)b; (void)x; (void)arith; (void)tol; (void)maxit; (void)stream;
-  (void)iters_out; (void)relres_out; (void)status_out;
-  return fail(MWCG_ERR_ARG, "mwcg_solve_batched: not built in this library version");
+  g_err.clear();
+  if (nsys < 0) return fail(MWCG_ERR_ARG, "nsys < 0");
+  if (nsys == 0) return MWCG_OK;
+  if (!A || !b || !x || !arith || !tol || !maxit) return fail(MWCG_ERR_ARG, "null argument array");
+  std::set<const mwcg_csr*> seen;
+  for (int s = 0; s < nsys; ++s) {
+    int rc = check_solve_args(A[s], b[s], x[s], arith[s], tol[s], maxit[s]);
+    if (rc != MWCG_OK) return fail(rc, "system %d: %s", s, g_err.c_str());
+    if (!seen.insert(A[s]).second) return fail(MWCG_ERR_ARG, "system %d: matrix handle repeated in the batch", s);
+    if ((rc = ensure_ws(A[s])) != MWCG_OK) return rc;
+  }
+  std::vector<mwb::Sys> hs;
+  std::vector<int> idx;
+  std::vector<double> cost;
+  for (int s = 0; s < nsys; ++s) {
+    if (A[s]->n == 0) {
+      if (iters_out) iters_out[s] = 0;
+      if (relres_out) relres_out[s] = 0.0;
+      if (status_out) status_out[s] = MWCG_OK;
+      continue;
+    }
+    mwb::Sys q{};
+    const int64_t n = A[s]->n;
+    q.rp = A[s]->rp;
+    q.col = A[s]->col;
+    q.val = A[s]->val;
+    q.n = n;
+    q.b = b[s];
+    q.x = x[s];
+    q.r = A[s]->ws;
+    q.p = A[s]->ws + 3 * n;
+    q.q = A[s]->ws + 6 * n;
+    q.tol = tol[s];
+    q.maxit = maxit[s];
+    q.arith = arith[s];
+    q.V = A[s]->plan.V;
+    double mac, add;
+    op_costs(arith[s], mac, add);
+    cost.push_back((double)A[s]->nnz * mac + (double)n * 10.0 * add);
+    idx.push_back(s);
+    hs.push_back(q);
+  }
+  if (hs.empty()) return MWCG_OK;
+  // Largest estimated work first (longest-processing-time order for the queue).
+  std::vector<int> order(hs.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  std::vector<mwb::Sys> qs(hs.size());
+  for (size_t i = 0; i < order.size(); ++i) qs[i] = hs[order[i]];
+  cudaError_t e = mwb_host::launch(qs.data(), (int)qs.size(), S(stream), nullptr);
+  if (e != cudaSuccess) return fail(MWCG_ERR_CUDA, "batched launch: %s", cudaGetErrorString(e));
+  for (size_t i = 0; i < order.size(); ++i) {
+    const int s = idx[order[i]];
+    if (iters_out) iters_out[s] = qs[i].iters;
+    if (relres_out) relres_out[s] = qs[i].relres;
+    if (status_out) status_out[s] = qs[i].status;
+  }
+  return MWCG_OK;
 }
 
 }  // extern "C"

@@ -40,11 +40,12 @@ __device__ __forceinline__ bool nonzero(double a) {
   return ((unsigned long long)__double_as_longlong(a) << 1) != 0ULL;
 }
 
-// Algorithm 2, TwoSum.  x = fl(a+b) on the FP64 pipe; the exact error y is
-// recovered from the bit patterns on the integer pipe (mw_int.cuh), which
-// yields the same number as the printed sequence.  Where that path declines
-// (non-finite, overflow-prone or tiny operands) the printed sequence runs.
-// Building with -DMWCG_NATIVE_EFT keeps the printed sequence everywhere.
+// Algorithm 2, TwoSum, as printed (6 FP64 operations).  Its error term is the
+// exact rounding error of fl(a+b), so two cheaper sequences that produce the
+// same number are also provided (mw_int.cuh): the error recovered from the bit
+// patterns on the integer pipe (1 FP64 operation), and Fast2Sum after ordering
+// the operands by an integer magnitude comparison (3 FP64 operations).  Both
+// fall back to the printed sequence on the operands they do not cover.
 __device__ __forceinline__ void two_sum_printed(double a, double b, double& x, double& y) {
   double s = dadd(a, b);
   double z = dsub(s, a);
@@ -53,10 +54,20 @@ __device__ __forceinline__ void two_sum_printed(double a, double b, double& x, d
   y = dadd(t1, t2);
   x = s;
 }
-__device__ __forceinline__ void two_sum(double a, double b, double& x, double& y) {
+// Implementation of TwoSum, chosen at build time (all return the same bits):
+// MWCG_EFT = 0 the printed sequence (also -DMWCG_NATIVE_EFT), 1 the
+// integer-pipe recovery, 2 Fast2Sum after an integer magnitude ordering.
+#ifndef MWCG_EFT
+#define MWCG_EFT 2
+#endif
 #if defined(MWCG_NATIVE_EFT)
-  two_sum_printed(a, b, x, y);
-#else
+#undef MWCG_EFT
+#define MWCG_EFT 0
+#endif
+struct RnAdd { __device__ __forceinline__ double operator()(double a, double b) const { return __dadd_rn(a, b); } };
+struct RnSub { __device__ __forceinline__ double operator()(double a, double b) const { return __dsub_rn(a, b); } };
+
+__device__ __forceinline__ void two_sum_int(double a, double b, double& x, double& y) {
   const double s = dadd(a, b);
   double e;
   if (!mwi::add_error(a, b, s, e)) {
@@ -65,22 +76,32 @@ __device__ __forceinline__ void two_sum(double a, double b, double& x, double& y
   }
   x = s;
   y = e;
+}
+__device__ __forceinline__ void two_sum_sorted(double a, double b, double& x, double& y) {
+  if (!mwi::sorted_two_sum(a, b, x, y, RnAdd{}, RnSub{})) two_sum_printed(a, b, x, y);
+}
+__device__ __forceinline__ void two_sum(double a, double b, double& x, double& y) {
+#if MWCG_EFT == 0
+  two_sum_printed(a, b, x, y);
+#elif MWCG_EFT == 1
+  two_sum_int(a, b, x, y);
+#else
+  two_sum_sorted(a, b, x, y);
 #endif
 }
-// Algorithm 3, QuickTwoSum.  When the exponent of a is at least that of b
-// (or b = 0) the printed sequence returns the exact error, so the integer
-// path is used; otherwise the printed sequence runs as written.
+// Algorithm 3, QuickTwoSum, as printed (3 FP64 operations; MWCG_QTS_INT=1
+// recovers the error on the integer pipe where the precondition holds).
 __device__ __forceinline__ void quick_two_sum(double a, double b, double& x, double& y) {
-#if defined(MWCG_NATIVE_EFT)
-  double s = dadd(a, b);
-  y = dadd(dsub(a, s), b);
-  x = s;
-#else
+#if defined(MWCG_QTS_INT) && MWCG_QTS_INT == 1
   const double s = dadd(a, b);
   double e;
   if (!(mwi::quick_exact(a, b) && mwi::add_error(a, b, s, e))) e = dadd(dsub(a, s), b);
   x = s;
   y = e;
+#else
+  double s = dadd(a, b);
+  y = dadd(dsub(a, s), b);
+  x = s;
 #endif
 }
 // Algorithm 4, TwoProdFMA.

@@ -16,7 +16,7 @@ import torch
 from . import _capi
 from ._capi import ARITH, WORDS, Plan, check
 
-__all__ = ["CSRMatrix", "SolveResult", "solve", "solve_host", "solve_batched", "adjoint", "spmv", "dot",
+__all__ = ["CSRMatrix", "SolveResult", "solve", "solve_host", "solve_batched", "batched_cluster_size", "adjoint", "spmv", "dot",
            "word_op", "collapse", "words", "arith_id", "MWCGSolve", "solve_differentiable"]
 
 
@@ -185,6 +185,11 @@ def solve_batched(As, bs, arith, tol, maxit, x0s=None):
         _ptr(b)
     check(_capi.load().mwcg_solve_batched(ns, hA, hb, hx, har, htl, hmi, _stream(), it, rr, stt))
     return [SolveResult(xs[s], it[s], rr[s], stt[s]) for s in range(ns)]
+
+
+def batched_cluster_size() -> int:
+    """CTAs per worker cluster of solve_batched (its systems use plan {V, 256, this})."""
+    return int(_capi.load().mwcg_batched_cluster_size())
 
 
 def adjoint(A: CSRMatrix, x: torch.Tensor, gx: torch.Tensor, arith="qtw", tol: float = 1e-20, maxit: int = 20000):
