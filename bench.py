@@ -1,5 +1,9 @@
 """Benchmark: QTW-CG time to relative residual 1e-14 on the 128^3 7-point Poisson system.
 
+Other configurations: --workload c1 c3 c4 c5 (2-D Poisson 64^2 latency case,
+power-law graph Laplacian, 256-system batch vs one-by-one, differentiable
+diffusion solve checked by TW finite differences), one JSON line each.
+
 One step = one complete solve (initialisation + CG iterations until the FP64
 relative residual drops below 1e-14) of the 3-D Poisson system (n = 2,097,152,
 nnz = 14,581,760, b = 2U-1 seeded, x0 = 0) in quasi triple-word arithmetic,
@@ -166,6 +170,200 @@ def oracle_sample(A, b, arith, iters_sample, total_iters):
     per_it = max(t_run - t_init1, 1e-9) / iters_sample
     init = max(t_init1 - per_it, 0.0)
     return init + per_it * total_iters, per_it, init
+
+
+def _timed(torch, fn, reps=1):
+    s = torch.cuda.current_stream()
+    best = None
+    out = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        out = fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return out, best
+
+
+def run_c1(torch, mw, P, cpu):
+    A, b, tol, maxit = P.workload("c1")
+    M = mw.CSRMatrix.from_csr(A)
+    db = torch.as_tensor(b, device="cuda")
+    out = {"workload": "c1: " + P.WORKLOADS["c1"], "plan": list(M.plan)}
+    for ar in ("dw", "fp64"):
+        mw.solve(M, db, ar, tol, maxit)
+        r, ms = _timed(torch, lambda: mw.solve(M, db, ar, tol, maxit), reps=5)
+        err = float(np.max(np.abs(mw.collapse(r.x).cpu().numpy() - 1.0)))
+        out[ar] = {"time_s": ms / 1e3, "iters": r.iters, "status": r.status, "relres": r.relres,
+                   "iters_per_s": r.iters / (ms / 1e3), "us_per_iter": ms * 1e3 / max(r.iters, 1),
+                   "max_forward_error": err}
+        if cpu:
+            import oracle
+            t0 = time.perf_counter()
+            _, it, _, _ = oracle.cg(ar, A, b, tol=tol, maxit=maxit, plan=M.plan)
+            out[ar]["cpu_oracle_s"] = time.perf_counter() - t0
+            out[ar]["cpu_oracle_iters"] = it
+    return out
+
+
+def run_c3(torch, mw, P, cpu):
+    out = {"workload": "c3: " + P.WORKLOADS["c3"]}
+    A, b, tol, maxit = P.workload("c3")
+    M = mw.CSRMatrix.from_csr(A)
+    db = torch.as_tensor(b, device="cuda")
+    lens = np.diff(A.row_ptr)
+    out.update({"n": A.n, "nnz": A.nnz, "mean_row": float(lens.mean()), "max_row": int(lens.max()),
+                "plan": list(M.plan)})
+    # Autotuner check: SpMV kernel time under every lane split V (same G).
+    import ctypes
+    from paper_2510_13536_gb300 import _capi
+    auto = M.plan
+    sweep = {}
+    for ar in ("qtw", "dw", "fp64"):
+        sweep[ar] = {}
+        for V in (1, 2, 4, 8, 16, 32):
+            M.plan = (V, auto[1], auto[2])
+            x = torch.zeros((mw.words(ar), A.n), dtype=torch.float64, device="cuda")
+            kms = (ctypes.c_double * 3)()
+            _capi.check(_capi.load().mwcg_profile_kernels(
+                M.handle, ctypes.c_void_p(db.data_ptr()), ctypes.c_void_p(x.data_ptr()), mw.arith_id(ar), 5,
+                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), kms))
+            sweep[ar][V] = kms[0]
+    M.plan = auto
+    out["spmv_ms_by_V"] = sweep
+    out["auto_V"] = auto[0]
+    for ar in ("fp64", "dw", "qtw"):
+        r, ms = _timed(torch, lambda: mw.solve(M, db, ar, tol, maxit))
+        out[ar] = {"time_s": ms / 1e3, "iters": r.iters, "status": r.status, "relres": r.relres,
+                   "ms_per_iter": ms / max(r.iters, 1)}
+    At, bt, tol_t, maxit_t = P.workload("c3_twin")
+    Mt = mw.CSRMatrix.from_csr(At)
+    dbt = torch.as_tensor(bt, device="cuda")
+    for ar in ("fp64", "dw", "qtw"):
+        r, ms = _timed(torch, lambda: mw.solve(Mt, dbt, ar, tol_t, maxit_t))
+        x = mw.collapse(r.x).cpu().numpy()
+        out[ar + "_twin"] = {"time_s": ms / 1e3, "iters": r.iters, "status": r.status, "relres": r.relres,
+                             "forward_error": float(np.linalg.norm(x - 1) / np.sqrt(At.n))}
+    return out
+
+
+def run_c4(torch, mw, P, cpu):
+    specs = P.batch_specs(256, P.SEED_BASE + 4)
+    systems = [P.build_batch_system(s) for s in specs]
+    Ms = [mw.CSRMatrix.from_csr(A) for A, _ in systems]
+    bs = [torch.as_tensor(b, device="cuda") for _, b in systems]
+    ar = [s["arith"] for s in specs]
+    tol, maxit = 1e-14, 20000
+    nrows = sum(A.n for A, _ in systems)
+    nnz = sum(A.nnz for A, _ in systems)
+    # warm-up (graph instantiation of every handle, module load)
+    mw.solve_batched(Ms[:4], bs[:4], ar[:4], tol, maxit)
+    for M, b, a in zip(Ms, bs, ar):
+        mw.solve(M, b, a, tol, 5)
+    rb, ms_b = _timed(torch, lambda: mw.solve_batched(Ms, bs, ar, tol, maxit))
+    rs, ms_s = _timed(torch, lambda: [mw.solve(M, b, a, tol, maxit) for M, b, a in zip(Ms, bs, ar)])
+    dev = []
+    for x1, x2 in zip(rb, rs):
+        a = mw.collapse(x1.x)
+        c = mw.collapse(x2.x)
+        dev.append(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)))
+    out = {"workload": "c4: 256 Laplacians, n U[1k,200k], 2-D/3-D, shift log-U[1e-6,1e-2], QDW/QTW, tol 1e-14",
+           "systems": len(systems), "rows": nrows, "nnz": nnz, "cluster": mw.batched_cluster_size(),
+           "batched": {"time_s": ms_b / 1e3, "solves_per_s": len(systems) / (ms_b / 1e3),
+                       "converged": sum(r.status == 0 for r in rb), "iters_total": sum(r.iters for r in rb)},
+           "sequential": {"time_s": ms_s / 1e3, "solves_per_s": len(systems) / (ms_s / 1e3),
+                          "converged": sum(r.status == 0 for r in rs), "iters_total": sum(r.iters for r in rs)},
+           "speedup": ms_s / ms_b, "max_rel_diff_batched_vs_sequential": max(dev)}
+    return out
+
+
+def run_c5(torch, mw, P, cpu, n_fd=32):
+    A, b, tol, maxit = P.workload("c5")
+    wv = P.c5_loss_weights(A.n)
+    M = mw.CSRMatrix.from_csr(A)
+    db = torch.as_tensor(b, device="cuda")
+    dw = torch.as_tensor(wv, device="cuda")
+    vals = torch.as_tensor(A.val, device="cuda").clone().requires_grad_(True)
+    bb = db.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x = mw.solve_differentiable(M, vals, bb, "qtw", tol, maxit)
+    L = torch.dot(dw, x)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    g_val = vals.grad.cpu().numpy()
+    g_b = bb.grad.cpu().numpy()
+    # Central differences in TW, symmetric pairs.
+    rng = np.random.Generator(np.random.PCG64(P.SEED_BASE + 5 + 300))
+    rp, cl = A.row_ptr, A.col
+    errs = []
+    Mfd = mw.CSRMatrix.from_csr(A)
+    Mfd.plan = M.plan
+    t0 = time.perf_counter()
+    samples = []
+    for _ in range(n_fd):
+        i = int(rng.integers(A.n))
+        k = int(rng.integers(rp[i], rp[i + 1]))
+        j = int(cl[k])
+        kt = [kk for kk in range(int(rp[j]), int(rp[j + 1])) if int(cl[kk]) == i][0]
+        h = 1e-12 * abs(A.val[k])
+        Ls = []
+        for sgn in (1, -1):
+            v = A.val.copy()
+            v[k] += sgn * h
+            if kt != k:
+                v[kt] += sgn * h
+            Mfd.update_values(v)
+            r = mw.solve(Mfd, db, "tw", 1e-28, 40000)
+            # L = w^T x summed in exact rational arithmetic over the TW words.
+            from fractions import Fraction
+            xw = r.x.cpu().numpy()
+            Ls.append(sum(Fraction(float(wv[t])) * (Fraction(float(xw[0, t])) + Fraction(float(xw[1, t])) +
+                                                     Fraction(float(xw[2, t]))) for t in range(A.n)))
+        from fractions import Fraction
+        hh = Fraction(float(A.val[k] + h)) - Fraction(float(A.val[k]))
+        fd = float((Ls[0] - Ls[1]) / (2 * hh))
+        an = g_val[k] + (g_val[kt] if kt != k else 0.0)
+        errs.append(abs(fd - an) / abs(an))
+        samples.append({"i": i, "j": j, "fd": fd, "adjoint": an})
+    t_fd = time.perf_counter() - t0
+    out = {"workload": "c5: " + P.WORKLOADS["c5"], "n": A.n, "nnz": A.nnz, "arith": "qtw", "tol": tol,
+           "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+           "fd_entries": n_fd, "fd_max_rel_err": max(errs), "fd_median_rel_err": float(np.median(errs)),
+           "fd_target": 1e-8, "fd_seconds": t_fd, "g_b_norm": float(np.linalg.norm(g_b)),
+           "fd_samples": samples[:4]}
+    return out
+
+
+def run_workloads(args):
+    """--workload c1|c3|c4|c5: the other configurations, one JSON line each."""
+    import torch
+    from paper_2510_13536_gb300 import build as _build
+    _build.build()
+    from paper_2510_13536_gb300 import problems as P
+    from paper_2510_13536_gb300 import solver as mw
+    for w in args.workload:
+        t0 = time.perf_counter()
+        if w == "c1":
+            res = run_c1(torch, mw, P, not args.no_cpu)
+        elif w == "c3":
+            res = run_c3(torch, mw, P, not args.no_cpu)
+        elif w == "c4":
+            res = run_c4(torch, mw, P, not args.no_cpu)
+        elif w == "c5":
+            res = run_c5(torch, mw, P, not args.no_cpu, args.fd)
+        else:
+            raise SystemExit(f"unknown workload {w}")
+        res["wall_s"] = time.perf_counter() - t0
+        print(json.dumps({w: res}), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -378,7 +576,12 @@ def main():
     ap.add_argument("--kernels-only", type=int, default=0, metavar="N",
                     help="run N iterations with each kernel launched on its own (mwcg_profile_kernels) and print "
                          "their mean durations; used for ncu captures")
+    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5"],
+                    help="measure another configuration instead of the headline (one JSON line each)")
+    ap.add_argument("--fd", type=int, default=32, help="finite-difference entries checked in c5")
     args = ap.parse_args()
+    if args.workload:
+        return run_workloads(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

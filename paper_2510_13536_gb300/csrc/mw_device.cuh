@@ -56,9 +56,10 @@ __device__ __forceinline__ void two_sum_printed(double a, double b, double& x, d
 }
 // Implementation of TwoSum, chosen at build time (all return the same bits):
 // MWCG_EFT = 0 the printed sequence (also -DMWCG_NATIVE_EFT), 1 the
-// integer-pipe recovery, 2 Fast2Sum after an integer magnitude ordering.
+// integer-pipe recovery (default: fastest on GB300 for every arithmetic),
+// 2 Fast2Sum after an integer magnitude ordering.
 #ifndef MWCG_EFT
-#define MWCG_EFT 2
+#define MWCG_EFT 1
 #endif
 #if defined(MWCG_NATIVE_EFT)
 #undef MWCG_EFT
@@ -67,18 +68,30 @@ __device__ __forceinline__ void two_sum_printed(double a, double b, double& x, d
 struct RnAdd { __device__ __forceinline__ double operator()(double a, double b) const { return __dadd_rn(a, b); } };
 struct RnSub { __device__ __forceinline__ double operator()(double a, double b) const { return __dsub_rn(a, b); } };
 
+// The printed sequences as out-of-line functions, for the rare operands the
+// cheaper paths decline.  Keeping them out of line stops the compiler from
+// executing part of them speculatively on every call (which measured as two
+// extra FP64 additions per TwoSum).
+static __device__ __noinline__ double two_sum_err_slow(double a, double b, double s) {
+  const double z = dsub(s, a);
+  return dadd(dsub(a, dsub(s, z)), dsub(b, z));
+}
+static __device__ __noinline__ double quick_two_sum_err_slow(double a, double b, double s) {
+  return dadd(dsub(a, s), b);
+}
+
 __device__ __forceinline__ void two_sum_int(double a, double b, double& x, double& y) {
   const double s = dadd(a, b);
   double e;
-  if (!mwi::add_error(a, b, s, e)) {
-    const double z = dsub(s, a);
-    e = dadd(dsub(a, dsub(s, z)), dsub(b, z));
-  }
+  if (!mwi::add_error(a, b, s, e)) e = two_sum_err_slow(a, b, s);
   x = s;
   y = e;
 }
 __device__ __forceinline__ void two_sum_sorted(double a, double b, double& x, double& y) {
-  if (!mwi::sorted_two_sum(a, b, x, y, RnAdd{}, RnSub{})) two_sum_printed(a, b, x, y);
+  if (!mwi::sorted_two_sum(a, b, x, y, RnAdd{}, RnSub{})) {
+    x = dadd(a, b);
+    y = two_sum_err_slow(a, b, x);
+  }
 }
 __device__ __forceinline__ void two_sum(double a, double b, double& x, double& y) {
 #if MWCG_EFT == 0
@@ -95,7 +108,7 @@ __device__ __forceinline__ void quick_two_sum(double a, double b, double& x, dou
 #if defined(MWCG_QTS_INT) && MWCG_QTS_INT == 1
   const double s = dadd(a, b);
   double e;
-  if (!(mwi::quick_exact(a, b) && mwi::add_error(a, b, s, e))) e = dadd(dsub(a, s), b);
+  if (!(mwi::quick_exact(a, b) && mwi::add_error(a, b, s, e))) e = quick_two_sum_err_slow(a, b, s);
   x = s;
   y = e;
 #else
