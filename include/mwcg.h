@@ -179,6 +179,33 @@ int mwcg_spmv(mwcg_csr* A, int arith, const double* p, double* q, void* stream);
  * tiles of 256 rows over G blocks (1..1024); out: host double[w]. */
 int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream, double* out);
 
+/* Capacity, in blocks, of the fixed scratch array of mwcg_dot_noalloc. */
+#define MWCG_DOT_NOALLOC_MAX_G 1024
+
+/* mwcg_dot without any device allocation.  The paper has no counterpart: this
+ * is a library-level variant for callers that must not allocate device memory
+ * -- mwcg_dot calls cudaMalloc and cudaFree on every call, and cudaFree
+ * synchronises the whole device, which stalls the other streams of a
+ * latency-critical pipeline; code that runs under a fixed device-memory
+ * budget or a pooled allocator may also be forbidden hidden allocations.
+ * Here the block partials and the ticket counter live in a fixed array
+ * compiled into the library (MWCG_DOT_NOALLOC_MAX_G blocks of 8 doubles plus
+ * one counter block, about 66 KB, held by every GPU that loads the library
+ * until the process exits).  The function calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   arith, n, u, v, G  as in mwcg_dot (u, v device double[w*n]); G in
+ *            1..MWCG_DOT_NOALLOC_MAX_G, larger G returns MWCG_ERR_ARG;
+ *   out      device double[w] (caller-owned), written in stream order; the
+ *            function does not synchronise the stream.
+ * The result bits equal mwcg_dot's for the same arguments.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current, so make the first call on each device before any
+ * stream capture.  All calls share the one array: its counter is cleared at
+ * the start of every call and the partials are rewritten, so calls that
+ * overlap on the GPU (concurrent streams or threads) race and must be
+ * serialised by the caller. */
+int mwcg_dot_noalloc(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream, double* out);
+
 /* Element-wise word operations on device arrays of n elements:
  *   op 0 add c = a + b; 1 mul c = a * b; 2 dxmul c = a (FP64, double[n]) * b;
  *   3 div c = a / b; 4 normalize c = the arithmetic's normalisation of a

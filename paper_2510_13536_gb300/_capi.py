@@ -23,6 +23,7 @@ EXPORTS = [
     "mwcg_n", "mwcg_nnz", "mwcg_get_plan", "mwcg_set_plan", "mwcg_solve", "mwcg_solve_host",
     "mwcg_solve_history", "mwcg_solve_batched", "mwcg_adjoint", "mwcg_spmv", "mwcg_dot",
     "mwcg_word_op", "mwcg_collapse", "mwcg_profile_kernels", "mwcg_batched_cluster_size",
+    "mwcg_dot_noalloc",
 ]
 
 
@@ -72,6 +73,7 @@ def load(path: str | None = None):
         "mwcg_collapse": (ctypes.c_int, [P, i32, i64, P, P]),
         "mwcg_profile_kernels": (ctypes.c_int, [P, P, P, ctypes.c_int, i32, P, P]),
         "mwcg_batched_cluster_size": (ctypes.c_int, []),
+        "mwcg_dot_noalloc": (ctypes.c_int, [ctypes.c_int, i64, P, P, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

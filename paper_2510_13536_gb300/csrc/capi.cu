@@ -99,6 +99,14 @@ bool is_pow2_le32(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 1
 
 }  // namespace
 
+namespace mwcg_detail {
+// Sets the thread's last-error message (used by the other translation units).
+int set_error(int code, const char* msg) {
+  g_err = msg ? msg : "";
+  return code;
+}
+}  // namespace mwcg_detail
+
 struct mwcg_csr {
   int device = 0;
   int64_t n = 0, nnz = 0;
