@@ -223,6 +223,14 @@ int mwcg_word_op(int op, int arith, int64_t n, const double* a, const double* b,
 int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int32_t niters, void* stream,
                          double* ms_out);
 
+/* Throughput probe for the roofline denominators: runs an FP64 FMA (kind 0),
+ * FP64 add (kind 1), 32-bit integer add/xor (kind 2), FP64 add issued as an
+ * FMA with multiplier 1 (kind 3) or FP64 multiply (kind 4) loop on every SM with
+ * eight independent chains per thread and writes the best of three runs in
+ * operations per second (FMA = one operation) to *ops_per_s (host).
+ * scratch: device buffer of at least SMs * 8 * 256 * 8 bytes (overwritten). */
+int mwcg_probe_peak(int kind, void* scratch, int64_t scratch_bytes, void* stream, double* ops_per_s);
+
 /* x64[i] = collapse of element i of the w-word vector xw (device arrays). */
 int mwcg_collapse(const double* xw, int32_t w, int64_t n, double* x64, void* stream);
 

@@ -23,7 +23,7 @@ EXPORTS = [
     "mwcg_n", "mwcg_nnz", "mwcg_get_plan", "mwcg_set_plan", "mwcg_solve", "mwcg_solve_host",
     "mwcg_solve_history", "mwcg_solve_batched", "mwcg_adjoint", "mwcg_spmv", "mwcg_dot",
     "mwcg_word_op", "mwcg_collapse", "mwcg_profile_kernels", "mwcg_batched_cluster_size",
-    "mwcg_dot_noalloc",
+    "mwcg_dot_noalloc", "mwcg_probe_peak",
 ]
 
 
@@ -74,6 +74,7 @@ def load(path: str | None = None):
         "mwcg_profile_kernels": (ctypes.c_int, [P, P, P, ctypes.c_int, i32, P, P]),
         "mwcg_batched_cluster_size": (ctypes.c_int, []),
         "mwcg_dot_noalloc": (ctypes.c_int, [ctypes.c_int, i64, P, P, i32, P, P]),
+        "mwcg_probe_peak": (ctypes.c_int, [ctypes.c_int, P, i64, P, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmwcg.so")
 
-SOURCES = ["capi.cu", "batched.cu", "noalloc.cu", "inst_fp64.cu", "inst_dw.cu", "inst_qdw.cu", "inst_tw.cu", "inst_qtw.cu"]
+SOURCES = ["capi.cu", "batched.cu", "noalloc.cu", "probe.cu", "inst_fp64.cu", "inst_dw.cu", "inst_qdw.cu", "inst_tw.cu", "inst_qtw.cu"]
 HEADERS = ["mw_device.cuh", "mw_int.cuh", "cg_kernels.cuh", "batched.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -64,6 +64,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         extra.append("-DMWCG_EFT=" + os.environ["MWCG_EFT"])
     if os.environ.get("MWCG_QTS_INT") == "1":
         extra.append("-DMWCG_QTS_INT=1")
+    if os.environ.get("MWCG_ADD_FMA") == "1":
+        extra.append("-DMWCG_ADD_FMA=1")
+    if os.environ.get("MWCG_TP_INT") in ("0", "1"):
+        extra.append("-DMWCG_TP_INT=" + os.environ["MWCG_TP_INT"])
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

@@ -44,9 +44,44 @@ namespace mwb_host {
 
 int cluster_size() { return mwb::kCluster; }
 
+namespace {
+int g_small_cluster[64] = {};
+}
+
+// Largest cluster size (16, else 8) with which one cluster of one-CTA-per-SM
+// blocks can be resident on the current device; used for single small
+// systems.  Cached per device.
+int small_cluster_size() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return mwb::kCluster;
+  if (g_small_cluster[dev]) return g_small_cluster[dev];
+  int best = mwb::kCluster;
+  if (cudaFuncSetAttribute(mwb::k_batched, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(mwb::k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mwb::kPadSmem) ==
+          cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(mwb::TPB);
+    cfg.dynamicSmemBytes = mwb::kPadSmem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, mwb::k_batched, &cfg) == cudaSuccess && n >= 1) best = 16;
+  }
+  cudaGetLastError();
+  g_small_cluster[dev] = best;
+  return best;
+}
+
 // Launch the persistent kernel over `nsys` prepared systems (host array, in
-// queue order).  Returns a cudaError_t; outputs are copied back into hsys.
-cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int* clusters_out) {
+// queue order) with clusters of `cluster` CTAs.  Returns a cudaError_t;
+// outputs are copied back into hsys.
+cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* clusters_out) {
   mwb::Sys* dsys = nullptr;
   unsigned* queue = nullptr;
   cudaError_t e = cudaMalloc(&dsys, sizeof(mwb::Sys) * nsys);
@@ -55,10 +90,12 @@ cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int* clusters_out) 
   if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mwb::k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mwb::kPadSmem);
+  if (e == cudaSuccess && cluster > 8)
+    e = cudaFuncSetAttribute(mwb::k_batched, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = mwb::kCluster;
+  attr[0].val.clusterDim.x = cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(mwb::TPB);
@@ -68,12 +105,12 @@ cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int* clusters_out) 
   cfg.numAttrs = 1;
   int nclusters = 0;
   if (e == cudaSuccess) {
-    cfg.gridDim = dim3(mwb::kCluster);
+    cfg.gridDim = dim3(cluster);
     e = cudaOccupancyMaxActiveClusters(&nclusters, mwb::k_batched, &cfg);
   }
   if (e == cudaSuccess) {
     nclusters = std::max(1, std::min(nclusters, nsys));
-    cfg.gridDim = dim3(nclusters * mwb::kCluster);
+    cfg.gridDim = dim3(nclusters * cluster);
     int n = nsys;
     e = cudaLaunchKernelEx(&cfg, mwb::k_batched, dsys, n, queue);
   }

@@ -41,6 +41,7 @@ struct Sys {
   int32_t status;   // out
   int32_t pad;
   double relres;    // out
+  double* hist;     // optional per-iteration FP64 relative residual, or null
 };
 
 struct ClusterCtx {
@@ -90,26 +91,32 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
   __shared__ int pres;
   __shared__ double resf;
   __shared__ int presf;
-  if (threadIdx.x == 0) {
+  // Pairwise tree over the C values in warp 0: level h combines lane s with
+  // lane s+h for s a multiple of 2h (the same order as a sequential tree, at
+  // log2(C) dependent steps instead of C-1).
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     const int C = cc.C;
+    T a = (lane < C) ? sv[lane] : A::zero();
+    bool pa = (lane < C) ? (sp[lane] != 0) : false;
+    mw::MW<1> c{{(lane < C) ? sf[lane] : 0.0}};
+    bool pc = (lane < C) ? (spf[lane] != 0) : false;
     for (int h = 1; h < C; h <<= 1) {
-      for (int s = 0; s + h < C; s += 2 * h) {
-        T a = sv[s];
-        bool pa = sp[s] != 0;
-        mwk::combine<A>(a, pa, sv[s + h], sp[s + h] != 0);
-        sv[s] = a;
-        sp[s] = pa;
-        mw::MW<1> c{{sf[s]}};
-        bool pc = spf[s] != 0;
-        mwk::combine<mw::FP64>(c, pc, mw::MW<1>{{sf[s + h]}}, spf[s + h] != 0);
-        sf[s] = c.w[0];
-        spf[s] = pc;
+      T o = mwk::shfl_down<A>(a, h);
+      bool po = __shfl_down_sync(0xffffffffu, (int)pa, h) != 0;
+      mw::MW<1> oc = mwk::shfl_down<mw::FP64>(c, h);
+      bool poc = __shfl_down_sync(0xffffffffu, (int)pc, h) != 0;
+      if ((lane % (2 * h)) == 0 && lane + h < C) {
+        mwk::combine<A>(a, pa, o, po);
+        mwk::combine<mw::FP64>(c, pc, oc, poc);
       }
     }
-    res = sv[0];
-    pres = sp[0];
-    resf = sf[0];
-    presf = spf[0];
+    if (lane == 0) {
+      res = a;
+      pres = pa;
+      resf = c.w[0];
+      presf = pc;
+    }
   }
   __syncthreads();
   pout = pres != 0;
@@ -195,22 +202,41 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   double bn2;
   T rho = cluster_reduce<A>(cc, slots, buf, acc, pacc, prho, &bn2, &pbn, bb.w[0], pbb);
   buf ^= 1;
-  if (!prho) rho = A::zero();
-  const double bnorm = __dsqrt_rn(pbn ? bn2 : 0.0);
-  int iters = 0, status = mwk::ST_CONVERGED;
-  double relres = 0.0;
-  bool done = false;
-  if (bnorm == 0.0) {
-    for (int64_t i = (int64_t)rank * TPB + threadIdx.x; i < (int64_t)A::W * n; i += (int64_t)C * TPB) S.x[i] = 0.0;
-    done = true;
-  } else {
-    bool rzero = true;
+  // Scalar steps run on one thread per CTA (the FP64 pipe is shared by the
+  // whole SM) and are broadcast through shared memory.  Every CTA's thread 0
+  // computes them from the same inputs, so all CTAs agree.
+  __shared__ double s_sc[8];
+  __shared__ int s_flag[2];
+  if (threadIdx.x == 0) {
+    if (!prho) rho = A::zero();
+    const double bnorm0 = __dsqrt_rn(pbn ? bn2 : 0.0);
+    int fl = 0;                        // 0 run, 1 zero x and stop, 2 stop
+    double rr0 = 0.0;
+    int st0 = mwk::ST_CONVERGED;
+    if (bnorm0 == 0.0) {
+      fl = 1;
+    } else {
+      bool rzero = true;
 #pragma unroll
-    for (int k = 0; k < A::W; ++k) rzero = rzero && !mw::nonzero(rho.w[k]);
-    relres = __ddiv_rn(__dsqrt_rn(A::collapse(rho)), bnorm);
-    if (rzero) { relres = 0.0; done = true; }
-    else if (S.maxit <= 0) { status = mwk::ST_MAXIT; done = true; }
+      for (int k = 0; k < A::W; ++k) rzero = rzero && !mw::nonzero(rho.w[k]);
+      rr0 = __ddiv_rn(__dsqrt_rn(A::collapse(rho)), bnorm0);
+      if (rzero) { rr0 = 0.0; fl = 2; }
+      else if (S.maxit <= 0) { st0 = mwk::ST_MAXIT; fl = 2; }
+    }
+    s_sc[0] = bnorm0;
+    s_sc[1] = rr0;
+    s_flag[0] = fl;
+    s_flag[1] = st0;
   }
+  __syncthreads();
+  const double bnorm = s_sc[0];
+  int iters = 0, status = s_flag[1];
+  double relres = s_sc[1];
+  bool done = s_flag[0] != 0;
+  if (s_flag[0] == 1) {
+    for (int64_t i = (int64_t)rank * TPB + threadIdx.x; i < (int64_t)A::W * n; i += (int64_t)C * TPB) S.x[i] = 0.0;
+  }
+  if (!prho) rho = A::zero();
 
   // ---- CG iterations; every CTA holds the same scalars and decisions.
   while (!done) {
@@ -222,11 +248,24 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     bool ppq;
     T pq = cluster_reduce<A>(cc, slots, buf, acc, pacc, ppq);
     buf ^= 1;
-    if (!ppq) pq = A::zero();
     ++iters;
-    const double pqc = A::collapse(pq);
-    if (!(pqc > 0.0) || !isfinite(pqc)) { status = mwk::ST_BREAKDOWN; break; }
-    const T al = A::div(rho, pq);
+    __syncthreads();                  // everyone has read s_sc / s_flag of the previous step
+    if (threadIdx.x == 0) {
+      if (!ppq) pq = A::zero();
+      const double pqc = A::collapse(pq);
+      const bool brk = !(pqc > 0.0) || !isfinite(pqc);
+      s_flag[0] = brk ? 1 : 0;
+      if (!brk) {
+        const T a1 = A::div(rho, pq);
+#pragma unroll
+        for (int k = 0; k < A::W; ++k) s_sc[k] = a1.w[k];
+      }
+    }
+    __syncthreads();
+    if (s_flag[0]) { status = mwk::ST_BREAKDOWN; break; }
+    T al;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) al.w[k] = s_sc[k];
     const T mal = mw::neg<A>(al);
     acc = A::zero();
     pacc = false;
@@ -246,12 +285,32 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     bool prr;
     T rho1 = cluster_reduce<A>(cc, slots, buf, acc, pacc, prr);
     buf ^= 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (!prr) rho1 = A::zero();
+      const double rr = __ddiv_rn(__dsqrt_rn(A::collapse(rho1)), bnorm);
+      if (S.hist && rank == 0) S.hist[iters - 1] = rr;
+      int fl = 0;
+      if (rr < S.tol) fl = 1;
+      else if (!isfinite(rr)) fl = 2;
+      else if (iters >= S.maxit) fl = 3;
+      else {
+        const T be = A::div(rho1, rho);
+#pragma unroll
+        for (int k = 0; k < A::W; ++k) s_sc[3 + k] = be.w[k];
+      }
+      s_sc[6] = rr;
+      s_flag[0] = fl;
+    }
+    __syncthreads();
+    relres = s_sc[6];
+    if (s_flag[0] == 1) { status = mwk::ST_CONVERGED; break; }
+    if (s_flag[0] == 2) { status = mwk::ST_BREAKDOWN; break; }
+    if (s_flag[0] == 3) { status = mwk::ST_MAXIT; break; }
+    T be;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) be.w[k] = s_sc[3 + k];
     if (!prr) rho1 = A::zero();
-    relres = __ddiv_rn(__dsqrt_rn(A::collapse(rho1)), bnorm);
-    if (relres < S.tol) { status = mwk::ST_CONVERGED; break; }
-    if (!isfinite(relres)) { status = mwk::ST_BREAKDOWN; break; }
-    if (iters >= S.maxit) { status = mwk::ST_MAXIT; break; }
-    const T be = A::div(rho1, rho);
     rho = rho1;
     // p = r + beta p on this CTA's rows (the update tiles).
     for (int64_t t = rank; t < ntiles_v; t += C) {

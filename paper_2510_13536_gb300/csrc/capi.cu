@@ -25,7 +25,8 @@
 
 namespace mwb_host {
 int cluster_size();
-cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int* clusters_out);
+int small_cluster_size();
+cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* clusters_out);
 }  // namespace mwb_host
 
 namespace mwk {
@@ -153,7 +154,7 @@ void op_costs(int arith, double& mac, double& add) {
 // consecutive rows), the longest row's ceil(len/V) multiply-adds plus
 // log2(V) tree adds.  FP64 arithmetic is memory bound: there the cost adds the
 // number of 32-lane load rounds, which favours wider rows.
-mwcg_plan choose_plan(const std::vector<int64_t>& len, int sms, int arith) {
+mwcg_plan choose_plan(const std::vector<int64_t>& len, int sms, int arith, int small_cluster) {
   double mac, add;
   op_costs(arith, mac, add);
   const int64_t n = (int64_t)len.size();
@@ -178,6 +179,11 @@ mwcg_plan choose_plan(const std::vector<int64_t>& len, int sms, int arith) {
   p.T = mwk::TPB;
   const int64_t tiles = (n + mwk::TPB - 1) / mwk::TPB;
   p.G = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)sms, std::min<int64_t>(tiles, kMaxG)));
+  // A system of at most `small_cluster` tiles is solved by one thread-block
+  // cluster in a single launch (see run_solve).  With G >= tiles every tile is
+  // its own block, so G = small_cluster gives the same summation order as
+  // G = tiles.
+  if (tiles <= small_cluster) p.G = small_cluster;
   return p;
 }
 
@@ -329,10 +335,44 @@ int run_eager(mwcg_csr* A, int arith, cudaStream_t s) {
   return MWCG_OK;
 }
 
+// Small systems (at most `small_cluster_size()` tiles of 256 rows, with the
+// plan's G equal to that size) run in one persistent launch of one thread-
+// block cluster: the same summation order as the graph (plan {V, 256, G}),
+// with hardware cluster barriers instead of three kernel launches per
+// iteration.
+int run_cluster(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
+                cudaStream_t s, int32_t* iters_out, double* relres_out) {
+  mwb::Sys q{};
+  const int64_t n = A->n;
+  q.rp = A->rp;
+  q.col = A->col;
+  q.val = A->val;
+  q.n = n;
+  q.b = b;
+  q.x = x;
+  q.r = A->ws;
+  q.p = A->ws + 3 * n;
+  q.q = A->ws + 6 * n;
+  q.tol = tol;
+  q.maxit = maxit;
+  q.arith = arith;
+  q.V = A->plan.V;
+  q.hist = hist;
+  cudaError_t e = mwb_host::launch(&q, 1, s, A->plan.G, nullptr);
+  if (e != cudaSuccess) return fail(MWCG_ERR_CUDA, "cluster solve: %s", cudaGetErrorString(e));
+  if (iters_out) *iters_out = q.iters;
+  if (relres_out) *relres_out = q.relres;
+  return q.status;
+}
+
 int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
               cudaStream_t s, int32_t* iters_out, double* relres_out) {
   int rc;
   if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
+  const int64_t tiles = (A->n + mwk::TPB - 1) / mwk::TPB;
+  const int small = mwb_host::small_cluster_size();
+  if (!eager_mode() && A->plan.G == small && tiles <= small)
+    return run_cluster(A, b, x, arith, tol, maxit, hist, s, iters_out, relres_out);
   const bool eager = eager_mode();
   if (!eager && (rc = ensure_graph(A, arith)) != MWCG_OK) return rc;
   mwk::DevState* h = A->h_st;
@@ -435,7 +475,7 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
     return cleanup(fail(MWCG_ERR_CUDA, "copy to device: %s", cudaGetErrorString(e)));
   A->rowlen.resize(n);
   for (int64_t i = 0; i < n; ++i) A->rowlen[i] = hrp[i + 1] - hrp[i];
-  A->plan = choose_plan(A->rowlen, sm_count_of(A->device), MWCG_QTW);
+  A->plan = choose_plan(A->rowlen, sm_count_of(A->device), MWCG_QTW, mwb_host::small_cluster_size());
   *out = A;
   return MWCG_OK;
 }
@@ -759,7 +799,7 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
   std::vector<mwb::Sys> qs(hs.size());
   for (size_t i = 0; i < order.size(); ++i) qs[i] = hs[order[i]];
-  cudaError_t e = mwb_host::launch(qs.data(), (int)qs.size(), S(stream), nullptr);
+  cudaError_t e = mwb_host::launch(qs.data(), (int)qs.size(), S(stream), mwb_host::cluster_size(), nullptr);
   if (e != cudaSuccess) return fail(MWCG_ERR_CUDA, "batched launch: %s", cudaGetErrorString(e));
   for (size_t i = 0; i < order.size(); ++i) {
     const int s = idx[order[i]];

@@ -22,22 +22,38 @@
 
 namespace mw {
 
+// fl(a+b) = fma(a, 1, b) and fl(a-b) = fma(b, -1, a) exactly (the products
+// are exact, the one rounding is the addition's; zero signs agree as well).
+// With MWCG_ADD_FMA=1 additions are issued that way, through inline PTX so the
+// compiler cannot fold the multiplication away, for GPUs whose FP64 FMA path
+// outruns the FP64 add path.
+#if defined(MWCG_ADD_FMA) && MWCG_ADD_FMA == 1
+__device__ __forceinline__ double dadd(double a, double b) {
+  double r;
+  asm("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(r) : "d"(a), "d"(b));
+  return r;
+}
+__device__ __forceinline__ double dsub(double a, double b) {
+  double r;
+  asm("fma.rn.f64 %0, %1, 0dBFF0000000000000, %2;" : "=d"(r) : "d"(b), "d"(a));
+  return r;
+}
+#else
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+#endif
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double dneg(double a) {
-  return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ULL);
+  return mwi::from_bits(mwi::bits_of(a) ^ 0x8000000000000000ULL);
 }
 // |a| >= |b| on the bit patterns (valid for all non-NaN values).
 __device__ __forceinline__ bool mag_ge(double a, double b) {
-  unsigned long long ua = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffULL;
-  unsigned long long ub = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffULL;
-  return ua >= ub;
+  return (mwi::bits_of(a) & mwi::kAbs) >= (mwi::bits_of(b) & mwi::kAbs);
 }
 // a != 0 (either sign of zero counts as zero; NaN counts as nonzero, as != does).
 __device__ __forceinline__ bool nonzero(double a) {
-  return ((unsigned long long)__double_as_longlong(a) << 1) != 0ULL;
+  return (mwi::bits_of(a) << 1) != 0ULL;
 }
 
 // Algorithm 2, TwoSum, as printed (6 FP64 operations).  Its error term is the
@@ -117,12 +133,37 @@ __device__ __forceinline__ void quick_two_sum(double a, double b, double& x, dou
   x = s;
 #endif
 }
-// Algorithm 4, TwoProdFMA.
-__device__ __forceinline__ void two_prod(double a, double b, double& x, double& y) {
-  double p = dmul(a, b);
+// Algorithm 4, TwoProdFMA.  two_prod_int recovers the error fma(a, b, -p) on
+// the integer pipe instead (mwi::mul_error, same bits), the FMA running only
+// for the operands that path declines.  Measured on GB300 it pays off where
+// the integer pipe has room: the double-word arithmetics use it, the
+// triple-word ones (whose kernels already keep the integer pipe busy) use the
+// FMA.  MWCG_TP_INT=0/1 forces one choice for every arithmetic.
+static __device__ __noinline__ double two_prod_err_slow(double a, double b, double p) { return dfma(a, b, -p); }
+__device__ __forceinline__ void two_prod_fma(double a, double b, double& x, double& y) {
+  const double p = dmul(a, b);
   y = dfma(a, b, -p);
   x = p;
 }
+__device__ __forceinline__ void two_prod_int(double a, double b, double& x, double& y) {
+  const double p = dmul(a, b);
+  double e;
+  if (!mwi::mul_error(a, b, p, e)) e = two_prod_err_slow(a, b, p);
+  y = e;
+  x = p;
+}
+#if defined(MWCG_TP_INT) && MWCG_TP_INT == 1
+#define MWCG_TP_W2 two_prod_int
+#define MWCG_TP_W3 two_prod_int
+#elif defined(MWCG_TP_INT) && MWCG_TP_INT == 0
+#define MWCG_TP_W2 two_prod_fma
+#define MWCG_TP_W3 two_prod_fma
+#else
+#define MWCG_TP_W2 two_prod_int
+#define MWCG_TP_W3 two_prod_fma
+#endif
+__device__ __forceinline__ void two_prod(double a, double b, double& x, double& y) { MWCG_TP_W3(a, b, x, y); }
+__device__ __forceinline__ void two_prod_w2(double a, double b, double& x, double& y) { MWCG_TP_W2(a, b, x, y); }
 
 template <int W> struct MW { double w[W]; };
 
@@ -162,7 +203,7 @@ struct DW {
   // Algorithm 6: fma with a1*b2 first, then a2*b1.
   static __device__ __forceinline__ T mul(const T& a, const T& b) {
     double p, e;
-    two_prod(a.w[0], b.w[0], p, e);
+    two_prod_w2(a.w[0], b.w[0], p, e);
     e = dfma(a.w[0], b.w[1], e);
     e = dfma(a.w[1], b.w[0], e);
     T c;
@@ -171,7 +212,7 @@ struct DW {
   }
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     double p, e;
-    two_prod(a, b.w[0], p, e);
+    two_prod_w2(a, b.w[0], p, e);
     e = dfma(a, b.w[1], e);
     T c;
     quick_two_sum(p, e, c.w[0], c.w[1]);
@@ -208,14 +249,14 @@ struct QDWt {
   }
   static __device__ __forceinline__ T mul(const T& a, const T& b) {
     T c;
-    two_prod(a.w[0], b.w[0], c.w[0], c.w[1]);
+    two_prod_w2(a.w[0], b.w[0], c.w[0], c.w[1]);
     c.w[1] = dfma(a.w[0], b.w[1], c.w[1]);
     c.w[1] = dfma(a.w[1], b.w[0], c.w[1]);
     return c;
   }
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     T c;
-    two_prod(a, b.w[0], c.w[0], c.w[1]);
+    two_prod_w2(a, b.w[0], c.w[0], c.w[1]);
     c.w[1] = dfma(a, b.w[1], c.w[1]);
     return c;
   }

@@ -38,9 +38,15 @@
 
 namespace mwi {
 
+// On the device the reinterpretation goes through an opaque move, so that the
+// compiler cannot turn the integer tests below back into FP64 comparisons
+// (a zero test on the magnitude bits is equivalent to "v == 0.0", and the
+// FP64 pipe is the scarce resource).
 MWI_HD uint64_t bits_of(double v) {
 #if defined(__CUDA_ARCH__)
-  return (uint64_t)__double_as_longlong(v);
+  uint64_t u;
+  asm("mov.b64 %0, %1;" : "=l"(u) : "d"(v));
+  return u;
 #else
   uint64_t u;
   memcpy(&u, &v, sizeof u);
@@ -127,6 +133,41 @@ MWI_HD bool sorted_two_sum(double a, double b, double& x, double& y, Add add, Su
   const double e = sub(l, z);
   x = s;
   y = (((swap ? ua : ub) & kAbs) == 0) ? 0.0 : e;
+  return true;
+}
+
+// Error of an FP64 product, e = a*b - p exactly, given p = fl(a*b): the value
+// TwoProdFMA (Algorithm 4) computes as fma(a, b, -p).  With significands ma, mb
+// (53 bits, hidden bit included), the exact product is M = ma*mb units of
+// u = 2^(ea+eb-2150) and p = mp*2^s units with s in {52, 53}.  |M - mp*2^s| <=
+// 2^52, so the low 64 bits of the two terms (one 64-bit multiplication, no
+// high half) give it exactly under wrap-around arithmetic.  Declines (returns
+// false) for zero, subnormal, non-finite or overflow-prone operands and when
+// the error would be subnormal; callers then use the FMA.
+MWI_HD bool mul_error(double a, double b, double p, double& e) {
+  const uint64_t ua = bits_of(a), ub = bits_of(b), up = bits_of(p);
+  const int ea = (int)((ua >> 52) & 0x7ff);
+  const int eb = (int)((ub >> 52) & 0x7ff);
+  const int ep = (int)((up >> 52) & 0x7ff);
+  if (ea == 2047 || eb == 2047) return false;   // inf or NaN operand
+  if ((ua & kAbs) == 0 || (ub & kAbs) == 0) { e = 0.0; return true; }  // exact zero product: fma gives +0
+  if (ea == 0 || eb == 0 || ep == 0 || ep >= 2046) return false;
+  const int k = ea + eb - 2150;                 // exponent of one unit of M
+  const int sh = ep - ea - eb + 1075;           // p = mp * 2^sh units
+  if (sh < 0 || sh > 63) return false;
+  const uint64_t ma = (ua & kFrac) | kHidden;
+  const uint64_t mb = (ub & kFrac) | kHidden;
+  const uint64_t mp = (up & kFrac) | kHidden;
+  const uint64_t D = ma * mb - (mp << sh);      // low 64 bits; |true value| <= 2^52
+  if (D == 0) { e = 0.0; return true; }
+  const bool neg = (int64_t)D < 0;
+  const uint64_t M = neg ? (uint64_t)0 - D : D;
+  const int L = msb64(M);
+  const int E = L + k + 1023;                   // biased exponent of the error
+  if (E < 1) return false;                      // subnormal error: use the FMA
+  const uint64_t mant = (L <= 52) ? (M << (52 - L)) : (M >> (L - 52));
+  const uint64_t sign = ((ua ^ ub) >> 63 ^ (neg ? 1u : 0u)) & 1u;
+  e = from_bits((sign << 63) | ((uint64_t)E << 52) | (mant & kFrac));
   return true;
 }
 

@@ -331,7 +331,7 @@ WORKLOADS = {
     "c2": "3-D Poisson 7-point, 128^3 (n=2,097,152), b = 2U-1, x0 = 0, tol 1e-14, maxit 20000",
     "c2_twin": "3-D Poisson 7-point, 128^3, b = A*1 (x* = 1), x0 = 0, tol 1e-14, maxit 20000",
     "c3": "power-law graph Laplacian n=1e6, mean degree 30, max 1000, weights lognormal(0,2), +1e-8 I, b ~ N(0,1)",
-    "c3_twin": "dyadic power-law twin n=1e6 (weights on 2^-20 grid, shift 2^-27), b = A*1 (x* = 1)",
+    "c3_twin": "dyadic power-law twin n=1e6 (weights on 2^-20 grid, shift 2^-27), b = A x* exactly, x* random +-1",
     "c5": "2-D variable-coefficient diffusion 512x512, theta lognormal(0,1), b, w ~ N(0,1)",
 }
 
@@ -351,12 +351,32 @@ def workload(name: str):
         A = power_law_laplacian(1_000_000, SEED_BASE + 3)
         return A, rhs_normal(A.n, SEED_BASE + 3 + 100), 1e-14, 20000
     if name == "c3_twin":
+        # x* = 1 is an eigenvector of a shifted Laplacian (CG would finish in one
+        # step), so the exact solution is a seeded random sign vector instead.
         A = power_law_laplacian(1_000_000, SEED_BASE + 3, dyadic=True)
-        return A, rhs_ones_exact(A), 1e-14, 20000
+        xs = random_signs(A.n, SEED_BASE + 3 + 200)
+        return A, matvec_exact(A, xs), 1e-14, 20000
     if name == "c5":
         A = diffusion_2d(512, SEED_BASE + 5)
         return A, rhs_normal(A.n, SEED_BASE + 5 + 100), 1e-20, 20000
     raise KeyError(name)
+
+
+def random_signs(n: int, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.choice(np.array([-1.0, 1.0]), size=n)
+
+
+def matvec_exact(A: CSR, x: np.ndarray) -> np.ndarray:
+    """b = A x as correctly rounded row sums (math.fsum); exact when every
+    product a_ij x_j is exact and the row sum is representable (dyadic entries,
+    x of +-1), as for the power-law twin.  Set-up value, not solver arithmetic."""
+    out = np.empty(A.n)
+    prod = A.val * x[A.col]
+    rp = A.row_ptr
+    for i in range(A.n):
+        out[i] = math.fsum(prod[rp[i]:rp[i + 1]].tolist())
+    return out
 
 
 def c5_loss_weights(n: int) -> np.ndarray:

@@ -32,6 +32,16 @@ extern "C" void sorted_two_sum_batch(long n, const double* a, const double* b, d
     x[i] = s; y[i] = t;
   }
 }
+#include <cmath>
+extern "C" void mul_error_batch(long n, const double* a, const double* b, double* e, double* ref, int* ok) {
+  for (long i = 0; i < n; ++i) {
+    const double p = a[i] * b[i];
+    double t = 0.0;
+    ok[i] = mwi::mul_error(a[i], b[i], p, t) ? 1 : 0;
+    e[i] = t;
+    ref[i] = std::fma(a[i], b[i], -p);
+  }
+}
 extern "C" void quick_exact_batch(long n, const double* a, const double* b, int* ok) {
   for (long i = 0; i < n; ++i) ok[i] = mwi::quick_exact(a[i], b[i]) ? 1 : 0;
 }
@@ -51,6 +61,7 @@ def shim(tmp_path_factory):
     L.add_error_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.quick_exact_batch.argtypes = [ctypes.c_long, P, P, P]
     L.sorted_two_sum_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
+    L.mul_error_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     return L
 
 
@@ -166,3 +177,28 @@ def test_sorted_fast2sum_matches_printed_two_sum(shim, seed):
         assert np.array_equal(~ok, ~(big < 2.0 ** 1023))       # declines only for overflow-prone / non-finite
         assert np.array_equal(x[ok].view(np.uint64), xr[ok].view(np.uint64))
         assert np.array_equal(y[ok].view(np.uint64), yr[ok].view(np.uint64))
+
+
+def test_mul_error_matches_two_prod_fma(shim):
+    """The integer product error equals fma(a, b, -fl(a*b)) (TwoProdFMA) bit for bit."""
+    rng = np.random.default_rng(17)
+    n = 400_000
+    a = rng.uniform(1, 2, n) * np.exp2(rng.integers(-540, 540, n)) * rng.choice([-1.0, 1.0], n)
+    b = rng.uniform(1, 2, n) * np.exp2(rng.integers(-540, 540, n)) * rng.choice([-1.0, 1.0], n)
+    m = rng.integers(0, 6, n)
+    b[m == 1] = 1.0 + np.ldexp(rng.integers(0, 2 ** 20, (m == 1).sum()).astype(float), -52)   # short significands
+    a[m == 2] = np.round(a[m == 2] * 2 ** 10) / 2 ** 10                                     # exact products
+    sp = np.array([0.0, -0.0, 5e-324, 1e-310, 1e308, -1e308, np.inf, np.nan, 1.0, -1.0])
+    k = np.nonzero(m == 3)[0]
+    b[k] = sp[rng.integers(0, sp.size, k.size)]
+    k = np.nonzero(m == 4)[0]                                                               # tiny products
+    a[k] = np.exp2(rng.integers(-1022, -500, k.size)) * rng.uniform(1, 2, k.size)
+    b[k] = np.exp2(rng.integers(-500, -1, k.size)) * rng.uniform(1, 2, k.size)
+    e = np.zeros(n)
+    ref = np.zeros(n)
+    ok = np.zeros(n, dtype=np.int32)
+    with np.errstate(all="ignore"):
+        shim.mul_error_batch(n, _p(a), _p(b), _p(e), _p(ref), _p(ok))
+    ok = ok.astype(bool)
+    assert ok.mean() > 0.7
+    assert np.array_equal(e[ok].view(np.uint64), ref[ok].view(np.uint64))
