@@ -64,8 +64,12 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         extra.append("-DMWCG_EFT=" + os.environ["MWCG_EFT"])
     if os.environ.get("MWCG_QTS_INT") == "1":
         extra.append("-DMWCG_QTS_INT=1")
-    if os.environ.get("MWCG_ADD_FMA") == "1":
-        extra.append("-DMWCG_ADD_FMA=1")
+    for key in ("MWCG_QTW_P_SPMV", "MWCG_QTW_P_VEC", "MWCG_DW_P_SPMV", "MWCG_DW_P_VEC", "MWCG_QDW_P_SPMV",
+                "MWCG_QDW_P_VEC"):
+        if os.environ.get(key, "").isdigit():
+            extra.append(f"-D{key}={os.environ[key]}")
+    if os.environ.get("MWCG_ADD_FMA") in ("1", "2"):
+        extra.append("-DMWCG_ADD_FMA=" + os.environ["MWCG_ADD_FMA"])
     if os.environ.get("MWCG_TP_INT") in ("0", "1"):
         extra.append("-DMWCG_TP_INT=" + os.environ["MWCG_TP_INT"])
 

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <set>
 #include <vector>
@@ -82,6 +83,10 @@ int small_cluster_size() {
 // queue order) with clusters of `cluster` CTAs.  Returns a cudaError_t;
 // outputs are copied back into hsys.
 cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* clusters_out) {
+  // MWCG_BATCH_PAD=0 drops the shared-memory pad that keeps one CTA per SM
+  // (clusters may then share SMs); for tuning runs.
+  const char* pad_env = std::getenv("MWCG_BATCH_PAD");
+  const size_t pad = (pad_env && pad_env[0] == '0') ? 0 : mwb::kPadSmem;
   mwb::Sys* dsys = nullptr;
   unsigned* queue = nullptr;
   cudaError_t e = cudaMalloc(&dsys, sizeof(mwb::Sys) * nsys);
@@ -99,7 +104,7 @@ cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* c
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(mwb::TPB);
-  cfg.dynamicSmemBytes = mwb::kPadSmem;
+  cfg.dynamicSmemBytes = pad;
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;

@@ -559,11 +559,13 @@ struct KernelTable {
   const void* word_op;
 };
 
-template <class A>
+// AS: the arithmetic type used by the SpMV kernel (the same arithmetic, possibly
+// with another pipe-balancing policy; every policy gives the same bits).
+template <class A, class AS = A>
 KernelTable make_table() {
   KernelTable t;
   t.words = A::W;
-  t.spmv = (const void*)&k_spmv<A>;
+  t.spmv = (const void*)&k_spmv<AS>;
   t.init = (const void*)&k_init<A>;
   t.zero_x = (const void*)&k_zero_x<A::W>;
   t.update = (const void*)&k_update<A>;

@@ -27,7 +27,13 @@ namespace mw {
 // With MWCG_ADD_FMA=1 additions are issued that way, through inline PTX so the
 // compiler cannot fold the multiplication away, for GPUs whose FP64 FMA path
 // outruns the FP64 add path.
-#if defined(MWCG_ADD_FMA) && MWCG_ADD_FMA == 1
+#if defined(MWCG_ADD_FMA) && MWCG_ADD_FMA == 2
+// Multiplier read from constant memory, whose value the compiler cannot assume,
+// so the instruction stays an FMA.
+static __constant__ double c_pm_one[2] = {1.0, -1.0};
+__device__ __forceinline__ double dadd(double a, double b) { return __fma_rn(a, c_pm_one[0], b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __fma_rn(b, c_pm_one[1], a); }
+#elif defined(MWCG_ADD_FMA) && MWCG_ADD_FMA == 1
 __device__ __forceinline__ double dadd(double a, double b) {
   double r;
   asm("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(r) : "d"(a), "d"(b));
@@ -118,6 +124,31 @@ __device__ __forceinline__ void two_sum(double a, double b, double& x, double& y
   two_sum_sorted(a, b, x, y);
 #endif
 }
+// Fully integer-pipe variants (mwi::add_rn computes fl(a+b) itself): no FP64
+// instruction at all on the common path.  Used at call sites chosen per
+// kernel to balance the FP64 and integer pipes (see QTWt's policy P).
+static __device__ __noinline__ double dadd_slow(double a, double b) { return dadd(a, b); }
+__device__ __forceinline__ double dadd_int(double a, double b) {
+  double x;
+  if (!mwi::add_rn(a, b, x)) x = dadd_slow(a, b);
+  return x;
+}
+__device__ __forceinline__ void two_sum_fullint(double a, double b, double& x, double& y) {
+  double s, e;
+  if (!mwi::add_rn(a, b, s)) s = dadd_slow(a, b);
+  if (!mwi::add_error(a, b, s, e)) e = two_sum_err_slow(a, b, s);
+  x = s;
+  y = e;
+}
+
+__device__ __forceinline__ void quick_two_sum_fullint(double a, double b, double& x, double& y) {
+  double s, e;
+  if (!mwi::add_rn(a, b, s)) s = dadd_slow(a, b);
+  if (!(mwi::quick_exact(a, b) && mwi::add_error(a, b, s, e))) e = quick_two_sum_err_slow(a, b, s);
+  x = s;
+  y = e;
+}
+
 // Algorithm 3, QuickTwoSum, as printed (3 FP64 operations; MWCG_QTS_INT=1
 // recovers the error on the integer pipe where the precondition holds).
 __device__ __forceinline__ void quick_two_sum(double a, double b, double& x, double& y) {
@@ -184,8 +215,32 @@ struct FP64 {
   static __device__ __forceinline__ double collapse(const T& a) { return a.w[0]; }
 };
 
+// Call-site selectors for the pipe-balancing policies below: with a nonzero
+// flag the operation runs entirely on the integer pipe (same bits).
+template <int P>
+__device__ __forceinline__ void qqs_(double a, double b, double& x, double& y) {
+  if constexpr (P != 0) quick_two_sum_fullint(a, b, x, y); else quick_two_sum(a, b, x, y);
+}
+template <int P>
+__device__ __forceinline__ void qts_(double a, double b, double& x, double& y) {
+  if constexpr (P != 0) two_sum_fullint(a, b, x, y); else two_sum(a, b, x, y);
+}
+template <int P>
+__device__ __forceinline__ double qadd_(double a, double b) {
+  if constexpr (P != 0) return dadd_int(a, b); else return dadd(a, b);
+}
 // ---------------------------------------------------------------- DW
-struct DW {
+// Policy P (bit mask, same results): bit 0 DWadd's TwoSum, bit 1 DWadd's two
+// plain additions, bit 2 DWadd's closing QuickTwoSum, bit 3 the closing
+// QuickTwoSum of DWmul / FP64 x DW, run entirely on the integer pipe.
+#ifndef MWCG_DW_P_SPMV
+#define MWCG_DW_P_SPMV 0
+#endif
+#ifndef MWCG_DW_P_VEC
+#define MWCG_DW_P_VEC 0
+#endif
+template <int P = MWCG_DW_P_VEC>
+struct DWt {
   static constexpr int W = 2;
   static constexpr bool QUASI = false;
   using T = MW<2>;
@@ -194,10 +249,10 @@ struct DW {
   // Algorithm 5: e = fl((e + a2) + b2), then QuickTwoSum.
   static __device__ __forceinline__ T add(const T& a, const T& b) {
     double s, e;
-    two_sum(a.w[0], b.w[0], s, e);
-    e = dadd(dadd(e, a.w[1]), b.w[1]);
+    qts_<P & 1>(a.w[0], b.w[0], s, e);
+    e = qadd_<P & 2>(qadd_<P & 2>(e, a.w[1]), b.w[1]);
     T c;
-    quick_two_sum(s, e, c.w[0], c.w[1]);
+    qqs_<P & 4>(s, e, c.w[0], c.w[1]);
     return c;
   }
   // Algorithm 6: fma with a1*b2 first, then a2*b1.
@@ -207,7 +262,7 @@ struct DW {
     e = dfma(a.w[0], b.w[1], e);
     e = dfma(a.w[1], b.w[0], e);
     T c;
-    quick_two_sum(p, e, c.w[0], c.w[1]);
+    qqs_<P & 8>(p, e, c.w[0], c.w[1]);
     return c;
   }
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
@@ -215,7 +270,7 @@ struct DW {
     two_prod_w2(a, b.w[0], p, e);
     e = dfma(a, b.w[1], e);
     T c;
-    quick_two_sum(p, e, c.w[0], c.w[1]);
+    qqs_<P & 8>(p, e, c.w[0], c.w[1]);
     return c;
   }
   static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return add(c, mul(a, b)); }
@@ -232,9 +287,19 @@ struct DW {
   static __device__ __forceinline__ void normalize(T&) {}
   static __device__ __forceinline__ double collapse(const T& a) { return dadd(a.w[0], a.w[1]); }
 };
+using DW = DWt<>;
+using DW_S = DWt<MWCG_DW_P_SPMV>;
 
 // ---------------------------------------------------------------- QDW
-template <bool NORM>
+// Policy P: bit 0 QDWadd's TwoSum, bit 1 its two plain additions, bit 2 the
+// normalising QuickTwoSum, run entirely on the integer pipe (same bits).
+#ifndef MWCG_QDW_P_SPMV
+#define MWCG_QDW_P_SPMV 0
+#endif
+#ifndef MWCG_QDW_P_VEC
+#define MWCG_QDW_P_VEC 0
+#endif
+template <bool NORM, int P = MWCG_QDW_P_VEC>
 struct QDWt {
   static constexpr int W = 2;
   static constexpr bool QUASI = true;
@@ -243,8 +308,8 @@ struct QDWt {
   static __device__ __forceinline__ T from(double a) { return T{{a, 0.0}}; }
   static __device__ __forceinline__ T add(const T& a, const T& b) {
     T c;
-    two_sum(a.w[0], b.w[0], c.w[0], c.w[1]);
-    c.w[1] = dadd(dadd(c.w[1], a.w[1]), b.w[1]);
+    qts_<P & 1>(a.w[0], b.w[0], c.w[0], c.w[1]);
+    c.w[1] = qadd_<P & 2>(qadd_<P & 2>(c.w[1], a.w[1]), b.w[1]);
     return c;
   }
   static __device__ __forceinline__ T mul(const T& a, const T& b) {
@@ -264,7 +329,7 @@ struct QDWt {
   static __device__ __forceinline__ T dxmuladd(const T& c, double a, const T& b) { return add(c, dxmul(a, b)); }
   static __device__ __forceinline__ T neg(const T& a) { return T{{dneg(a.w[0]), dneg(a.w[1])}}; }
   // QDW normalisation: QuickTwoSum(c1, c2).
-  static __device__ __forceinline__ void renorm(T& a) { quick_two_sum(a.w[0], a.w[1], a.w[0], a.w[1]); }
+  static __device__ __forceinline__ void renorm(T& a) { qqs_<P & 4>(a.w[0], a.w[1], a.w[0], a.w[1]); }
   static __device__ __forceinline__ T div(const T& a, const T& b) {
     double q1 = __ddiv_rn(a.w[0], b.w[0]);
     T r = add(a, neg(dxmul(q1, b)));
@@ -279,9 +344,25 @@ struct QDWt {
 };
 using QDW = QDWt<true>;
 using QDW_NN = QDWt<false>;
+using QDW_S = QDWt<true, MWCG_QDW_P_SPMV>;
+using QDW_NN_S = QDWt<false, MWCG_QDW_P_SPMV>;
 
 // ---------------------------------------------------------------- QTW
-template <bool NORM>
+// Policy P (bit mask, same results for every value): which TwoSums and plain
+// additions run entirely on the integer pipe.  bit 0: QTWadd's TwoSums;
+// bit 1: QTWadd's c3 additions; bit 2: DxQTWmul's TwoSum; bit 3: DxQTWmul's
+// c3 addition; bit 4: QTWmul's TwoSums; bit 5: QTWmul's c3 additions.
+// Measured on GB300 (128^3 Poisson): a full integer addition costs ~50 integer
+// instructions, about 25 clocks of the 64-lane integer pipe per warp against 16
+// of the FP64 pipe for a DADD, so only the SpMV's FP64 x QTW c3 addition gains
+// (2%); every wider choice, and any choice in the vector kernels, is slower.
+#ifndef MWCG_QTW_P_SPMV
+#define MWCG_QTW_P_SPMV 8
+#endif
+#ifndef MWCG_QTW_P_VEC
+#define MWCG_QTW_P_VEC 0
+#endif
+template <bool NORM, int P = MWCG_QTW_P_VEC>
 struct QTWt {
   static constexpr int W = 3;
   static constexpr bool QUASI = true;
@@ -292,10 +373,10 @@ struct QTWt {
   static __device__ __forceinline__ T add(const T& a, const T& b) {
     T c;
     double e1, e2, e3;
-    two_sum(a.w[0], b.w[0], c.w[0], e1);
-    two_sum(a.w[1], b.w[1], c.w[1], e2);
-    two_sum(c.w[1], e1, c.w[1], e3);
-    c.w[2] = dadd(dadd(dadd(a.w[2], b.w[2]), e2), e3);
+    qts_<P & 1>(a.w[0], b.w[0], c.w[0], e1);
+    qts_<P & 1>(a.w[1], b.w[1], c.w[1], e2);
+    qts_<P & 1>(c.w[1], e1, c.w[1], e3);
+    c.w[2] = qadd_<P & 2>(qadd_<P & 2>(qadd_<P & 2>(a.w[2], b.w[2]), e2), e3);
     return c;
   }
   // Algorithm 8.
@@ -305,12 +386,12 @@ struct QTWt {
     two_prod(a.w[0], b.w[0], c.w[0], e1);
     two_prod(a.w[0], b.w[1], t2, e2);
     two_prod(a.w[1], b.w[0], t3, e3);
-    two_sum(t2, t3, c.w[1], e4);
-    two_sum(c.w[1], e1, c.w[1], e5);
+    qts_<P & 16>(t2, t3, c.w[1], e4);
+    qts_<P & 16>(c.w[1], e1, c.w[1], e5);
     double f1 = dfma(a.w[2], b.w[0], e2);
     double f2 = dfma(a.w[1], b.w[1], e3);
     double f3 = dfma(a.w[0], b.w[2], e4);
-    c.w[2] = dadd(dadd(dadd(f1, f2), f3), e5);
+    c.w[2] = qadd_<P & 32>(qadd_<P & 32>(qadd_<P & 32>(f1, f2), f3), e5);
     return c;
   }
   // Algorithm 10.
@@ -319,8 +400,8 @@ struct QTWt {
     double e1, e2, e5;
     two_prod(a, b.w[0], c.w[0], e1);
     two_prod(a, b.w[1], c.w[1], e2);
-    two_sum(c.w[1], e1, c.w[1], e5);
-    c.w[2] = dadd(dfma(a, b.w[2], e2), e5);
+    qts_<P & 4>(c.w[1], e1, c.w[1], e5);
+    c.w[2] = qadd_<P & 8>(dfma(a, b.w[2], e2), e5);
     return c;
   }
   static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return add(c, mul(a, b)); }
@@ -328,8 +409,8 @@ struct QTWt {
   static __device__ __forceinline__ T neg(const T& a) { return T{{dneg(a.w[0]), dneg(a.w[1]), dneg(a.w[2])}}; }
   // Algorithm 9, VecSum3 as printed.
   static __device__ __forceinline__ void renorm(T& a) {
-    two_sum(a.w[0], a.w[1], a.w[0], a.w[1]);
-    two_sum(a.w[1], a.w[2], a.w[1], a.w[2]);
+    qts_<P & 1>(a.w[0], a.w[1], a.w[0], a.w[1]);
+    qts_<P & 1>(a.w[1], a.w[2], a.w[1], a.w[2]);
   }
   static __device__ __forceinline__ T div(const T& a, const T& b) {
     double q1 = __ddiv_rn(a.w[0], b.w[0]);
@@ -348,6 +429,9 @@ struct QTWt {
 };
 using QTW = QTWt<true>;
 using QTW_NN = QTWt<false>;
+// SpMV-kernel instantiations (their own policy).
+using QTW_S = QTWt<true, MWCG_QTW_P_SPMV>;
+using QTW_NN_S = QTWt<false, MWCG_QTW_P_SPMV>;
 
 // ---------------------------------------------------------------- TW
 struct TW {

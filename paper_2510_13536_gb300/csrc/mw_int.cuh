@@ -136,6 +136,52 @@ MWI_HD bool sorted_two_sum(double a, double b, double& x, double& y, Add add, Su
   return true;
 }
 
+// x = fl(a + b) (IEEE binary64, round to nearest, ties to even) on the integer
+// pipe.  Operands ordered by magnitude, |h| >= |l|; significands extended by
+// three guard bits; l aligned to h with the bits shifted out folded into a
+// sticky bit; added or subtracted; renormalised; rounded to nearest even.
+// Zeros follow IEEE (x = -0 only for (-0) + (-0)); l below a quarter ulp of h
+// gives x = h.  Declines (returns false) for non-finite, overflow-prone or
+// subnormal operands and for a subnormal result; callers then use the FP64 add.
+MWI_HD bool add_rn(double a, double b, double& x) {
+  const uint64_t ua = bits_of(a), ub = bits_of(b);
+  const bool swap = (ua & kAbs) < (ub & kAbs);
+  const uint64_t h = swap ? ub : ua;
+  const uint64_t l = swap ? ua : ub;
+  const int eh = (int)((h >> 52) & 0x7ff);
+  const int el = (int)((l >> 52) & 0x7ff);
+  if (eh >= 2046) return false;
+  if ((l & kAbs) == 0) {                        // l = +-0
+    x = ((h & kAbs) == 0) ? from_bits(h & l & ~kAbs) : from_bits(h);
+    return true;
+  }
+  if (el == 0) return false;                    // subnormal operand
+  const int d = eh - el;
+  if (d > 55) { x = from_bits(h); return true; }
+  const uint64_t mh = ((h & kFrac) | kHidden) << 3;          // 56 bits
+  const uint64_t ml = ((l & kFrac) | kHidden) << 3;
+  const uint64_t lost = (d == 0) ? 0 : (ml & ((1ULL << d) - 1));
+  const uint64_t L = (ml >> d) | (lost != 0 ? 1u : 0u);       // sticky in bit 0
+  uint64_t S;
+  int e = eh;
+  if (((ua ^ ub) >> 63) == 0) {
+    S = mh + L;                                 // < 2^57
+    if (S >> 56) { S = (S >> 1) | (S & 1u); ++e; }
+  } else {
+    S = mh - L;
+    if (S == 0) { x = 0.0; return true; }       // exact cancellation: +0
+    const int sh = 55 - msb64(S);               // renormalise (exact when sh > 1)
+    S <<= sh;
+    e -= sh;
+  }
+  const uint64_t g = (S >> 2) & 1u, rest = S & 3u, lsb = (S >> 3) & 1u;
+  uint64_t m = (S >> 3) + ((g && (rest || lsb)) ? 1u : 0u);
+  if (m >> 53) { m >>= 1; ++e; }
+  if (e < 1 || e >= 2047) return false;         // subnormal or overflowing result
+  x = from_bits((h & ~kAbs) | ((uint64_t)e << 52) | (m & kFrac));
+  return true;
+}
+
 // Error of an FP64 product, e = a*b - p exactly, given p = fl(a*b): the value
 // TwoProdFMA (Algorithm 4) computes as fma(a, b, -p).  With significands ma, mb
 // (53 bits, hidden bit included), the exact product is M = ma*mb units of

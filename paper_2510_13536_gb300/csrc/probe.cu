@@ -36,11 +36,10 @@ __global__ void __launch_bounds__(256) k_probe_dadd(double* out, int iters, doub
   out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
-__device__ __forceinline__ double fma_one(double a, double b) {
-  double r;
-  asm("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(r) : "d"(a), "d"(b));
-  return r;
-}
+__constant__ double c_probe_one = 1.0;
+// fl(a + b) issued as an FMA whose multiplier (1.0) comes from constant memory,
+// so that the compiler cannot turn it back into an addition.
+__device__ __forceinline__ double fma_one(double a, double b) { return __fma_rn(a, c_probe_one, b); }
 
 __global__ void __launch_bounds__(256) k_probe_add_as_fma(double* out, int iters, double s) {
   double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,

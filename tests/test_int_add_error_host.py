@@ -42,6 +42,14 @@ extern "C" void mul_error_batch(long n, const double* a, const double* b, double
     ref[i] = std::fma(a[i], b[i], -p);
   }
 }
+extern "C" void add_rn_batch(long n, const double* a, const double* b, double* x, double* ref, int* ok) {
+  for (long i = 0; i < n; ++i) {
+    double t = 0.0;
+    ok[i] = mwi::add_rn(a[i], b[i], t) ? 1 : 0;
+    x[i] = t;
+    ref[i] = a[i] + b[i];
+  }
+}
 extern "C" void quick_exact_batch(long n, const double* a, const double* b, int* ok) {
   for (long i = 0; i < n; ++i) ok[i] = mwi::quick_exact(a[i], b[i]) ? 1 : 0;
 }
@@ -62,6 +70,7 @@ def shim(tmp_path_factory):
     L.quick_exact_batch.argtypes = [ctypes.c_long, P, P, P]
     L.sorted_two_sum_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.mul_error_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
+    L.add_rn_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     return L
 
 
@@ -202,3 +211,28 @@ def test_mul_error_matches_two_prod_fma(shim):
     ok = ok.astype(bool)
     assert ok.mean() > 0.7
     assert np.array_equal(e[ok].view(np.uint64), ref[ok].view(np.uint64))
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_integer_add_matches_ieee_addition(shim, seed):
+    """add_rn equals the IEEE round-to-nearest-even sum bit for bit (ties, cancellation,
+    carries, zeros), declining only for non-finite/overflow-prone/subnormal cases."""
+    a, b = inputs(seed, 500_000)
+    rng = np.random.default_rng(seed)
+    m = rng.integers(0, 4, a.size)
+    # exact ties: b = +-(k + 1/2) ulp(a) and carries into a new binade
+    k = m == 1
+    ulp = np.spacing(np.abs(a[k]))
+    b[k] = np.sign(rng.uniform(-1, 1, k.sum())) * ulp * (rng.integers(0, 4, k.sum()) + 0.5)
+    k = m == 2
+    a[k] = np.nextafter(np.exp2(rng.integers(-100, 100, k.sum())), 0) * rng.choice([-1.0, 1.0], k.sum())
+    b[k] = np.spacing(np.abs(a[k])) * rng.uniform(0.1, 3, k.sum()) * np.sign(a[k]) * rng.choice([-1.0, 1.0], k.sum())
+    for (u, v) in ((a, b), (b, a)):
+        x = np.zeros_like(u)
+        ref = np.zeros_like(u)
+        ok = np.zeros(u.size, dtype=np.int32)
+        with np.errstate(all="ignore"):
+            shim.add_rn_batch(u.size, _p(u), _p(v), _p(x), _p(ref), _p(ok))
+        ok = ok.astype(bool)
+        assert ok.mean() > 0.7
+        assert np.array_equal(x[ok].view(np.uint64), ref[ok].view(np.uint64))
