@@ -141,6 +141,15 @@ __device__ __forceinline__ void two_sum_fullint(double a, double b, double& x, d
   y = e;
 }
 
+// QuickTwoSum with fl(a+b) on the FP64 pipe and the error on the integer pipe
+// where its precondition holds (the printed error otherwise).
+__device__ __forceinline__ void quick_two_sum_interr(double a, double b, double& x, double& y) {
+  const double s = dadd(a, b);
+  double e;
+  if (!(mwi::quick_exact(a, b) && mwi::add_error(a, b, s, e))) e = quick_two_sum_err_slow(a, b, s);
+  x = s;
+  y = e;
+}
 __device__ __forceinline__ void quick_two_sum_fullint(double a, double b, double& x, double& y) {
   double s, e;
   if (!mwi::add_rn(a, b, s)) s = dadd_slow(a, b);
@@ -265,10 +274,15 @@ struct DWt {
     qqs_<P & 8>(p, e, c.w[0], c.w[1]);
     return c;
   }
+  // For a = +-2^k, TwoProdFMA(a, b1) = (a*b1, +0) and fma(a, b2, +0) = a*b2
+  // (+0 if zero) exactly, so both are formed on the integer pipe; the closing
+  // QuickTwoSum runs as printed.
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     double p, e;
-    two_prod_w2(a, b.w[0], p, e);
-    e = dfma(a, b.w[1], e);
+    if (!(mwi::is_pow2(a) && mwi::pow2_scale(a, b.w[0], false, p) && mwi::pow2_scale(a, b.w[1], true, e))) {
+      two_prod_w2(a, b.w[0], p, e);
+      e = dfma(a, b.w[1], e);
+    }
     T c;
     qqs_<P & 8>(p, e, c.w[0], c.w[1]);
     return c;
@@ -321,6 +335,8 @@ struct QDWt {
   }
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     T c;
+    if (mwi::is_pow2(a) && mwi::pow2_scale(a, b.w[0], false, c.w[0]) && mwi::pow2_scale(a, b.w[1], true, c.w[1]))
+      return c;
     two_prod_w2(a, b.w[0], c.w[0], c.w[1]);
     c.w[1] = dfma(a, b.w[1], c.w[1]);
     return c;
@@ -394,9 +410,13 @@ struct QTWt {
     c.w[2] = qadd_<P & 32>(qadd_<P & 32>(qadd_<P & 32>(f1, f2), f3), e5);
     return c;
   }
-  // Algorithm 10.
+  // Algorithm 10.  A power-of-two a (the +-1 entries of a Laplacian, for
+  // instance) takes the exact-scaling path on the integer pipe (same bits).
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     T c;
+    if (mwi::is_pow2(a) && mwi::pow2_scale(a, b.w[0], false, c.w[0]) && mwi::pow2_scale(a, b.w[1], true, c.w[1]) &&
+        mwi::pow2_scale(a, b.w[2], true, c.w[2]))
+      return c;
     double e1, e2, e5;
     two_prod(a, b.w[0], c.w[0], e1);
     two_prod(a, b.w[1], c.w[1], e2);
@@ -434,6 +454,11 @@ using QTW_S = QTWt<true, MWCG_QTW_P_SPMV>;
 using QTW_NN_S = QTWt<false, MWCG_QTW_P_SPMV>;
 
 // ---------------------------------------------------------------- TW
+// Policy MWCG_TW_P (same results): bit 0 the renormalisation's QuickTwoSums
+// take their error term from the integer pipe.
+#ifndef MWCG_TW_P
+#define MWCG_TW_P 0
+#endif
 struct TW {
   static constexpr int W = 3;
   static constexpr bool QUASI = false;
@@ -468,7 +493,8 @@ struct TW {
     for (int i = 0; i + 1 < N; ++i) {
       if (!stop) {
         double hi, lo;
-        quick_two_sum(eps, e[i + 1], hi, lo);
+        if constexpr ((MWCG_TW_P & 1) != 0) quick_two_sum_interr(eps, e[i + 1], hi, lo);
+        else quick_two_sum(eps, e[i + 1], hi, lo);
         if (j == 0) r0 = hi; else if (j == 1) r1 = hi; else r2 = hi;
         if (nonzero(lo)) {
           if (j >= 2) stop = true;

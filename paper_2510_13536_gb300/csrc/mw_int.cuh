@@ -217,6 +217,31 @@ MWI_HD bool mul_error(double a, double b, double p, double& e) {
   return true;
 }
 
+// Multiplication by a power of two.  If a = +-2^k, every product a*b_i is
+// exact, every TwoProdFMA error is +0 and every TwoSum with a +0 operand is
+// exact, so the printed FP64 x QTW product (Algorithm 10) returns
+// (a*b1, a*b2, a*b3) with the two lower words replaced by +0 when they are
+// zero (the printed sequence adds +0 to them), and FP64 x QDW returns
+// (a*b1, a*b2) likewise.  pow2_scale forms a*b from the bit patterns (an
+// exponent add and a sign flip); it declines for a subnormal, infinite or NaN
+// b and when the result would leave the normal range.
+MWI_HD bool is_pow2(double a) {
+  const uint64_t ua = bits_of(a);
+  const int ea = (int)((ua >> 52) & 0x7ff);
+  return (ua & kFrac) == 0 && ea >= 1 && ea <= 2046;
+}
+MWI_HD bool pow2_scale(double a, double b, bool plus_zero, double& out) {
+  const uint64_t ua = bits_of(a), ub = bits_of(b);
+  const uint64_t sign = (ua ^ ub) & ~kAbs;
+  if ((ub & kAbs) == 0) { out = plus_zero ? 0.0 : from_bits(sign); return true; }
+  const int eb = (int)((ub >> 52) & 0x7ff);
+  if (eb == 0 || eb == 2047) return false;
+  const int e = eb + (int)((ua >> 52) & 0x7ff) - 1023;
+  if (e < 1 || e > 2046) return false;
+  out = from_bits(sign | ((uint64_t)e << 52) | (ub & kFrac));
+  return true;
+}
+
 // Precondition under which QuickTwoSum (Algorithm 3) returns the exact error:
 // exponent field of a >= exponent field of b, or b = +-0.
 MWI_HD bool quick_exact(double a, double b) {

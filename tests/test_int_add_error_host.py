@@ -50,6 +50,17 @@ extern "C" void add_rn_batch(long n, const double* a, const double* b, double* x
     ref[i] = a[i] + b[i];
   }
 }
+extern "C" void pow2_dx_batch(long n, int w, const double* a, const double* b, double* c, int* ok) {
+  for (long i = 0; i < n; ++i) {
+    bool g = mwi::is_pow2(a[i]);
+    for (int k = 0; k < w && g; ++k) {
+      double t = 0.0;
+      g = mwi::pow2_scale(a[i], b[k * n + i], k > 0, t);
+      c[k * n + i] = t;
+    }
+    ok[i] = g ? 1 : 0;
+  }
+}
 extern "C" void quick_exact_batch(long n, const double* a, const double* b, int* ok) {
   for (long i = 0; i < n; ++i) ok[i] = mwi::quick_exact(a[i], b[i]) ? 1 : 0;
 }
@@ -71,6 +82,7 @@ def shim(tmp_path_factory):
     L.sorted_two_sum_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.mul_error_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.add_rn_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
+    L.pow2_dx_batch.argtypes = [ctypes.c_long, ctypes.c_int, P, P, P, P]
     return L
 
 
@@ -236,3 +248,31 @@ def test_integer_add_matches_ieee_addition(shim, seed):
         ok = ok.astype(bool)
         assert ok.mean() > 0.7
         assert np.array_equal(x[ok].view(np.uint64), ref[ok].view(np.uint64))
+
+
+@pytest.mark.parametrize("arith,w", [("qtw", 3), ("qdw", 2)])
+def test_power_of_two_product_matches_printed_dxmul(shim, orc, arith, w):
+    """For a = +-2^k the exact-scaling path equals the printed FP64 x MW product
+    (Algorithm 10 / its QDW analogue) of the oracle bit for bit, zero words included."""
+    rng = np.random.default_rng(31 + w)
+    n = 200_000
+    a = np.exp2(rng.integers(-60, 61, n).astype(float)) * rng.choice([-1.0, 1.0], n)
+    a[::7] = rng.uniform(1, 2, a[::7].size)                      # non powers of two: declined
+    a[::11] = rng.choice([1.0, -1.0, 0.5, -2.0], a[::11].size)
+    b = np.empty((w, n))
+    b[0] = rng.uniform(-2, 2, n) * np.exp2(rng.integers(-300, 300, n))
+    for k in range(1, w):
+        b[k] = b[k - 1] * rng.uniform(-1, 1, n) * 2.0 ** -53
+    z = rng.integers(0, 6, n)
+    b[1, z == 1] = 0.0
+    b[1, z == 2] = -0.0
+    b[w - 1, z == 3] = -0.0
+    b[0, z == 4] = -0.0
+    b[:, z == 5] *= 2.0 ** 900                                    # near overflow after scaling
+    c = np.zeros((w, n))
+    ok = np.zeros(n, dtype=np.int32)
+    shim.pow2_dx_batch(n, w, _p(a), _p(np.ascontiguousarray(b)), _p(c), _p(ok))
+    ok = ok.astype(bool)
+    ref = orc.dxmul(arith, a, b)
+    assert ok.mean() > 0.5
+    assert np.array_equal(c[:, ok].view(np.uint64), ref[:, ok].view(np.uint64))
