@@ -32,6 +32,9 @@
 namespace mwk {
 
 constexpr int TPB = 256;                  // threads per block of every kernel
+// Tiles interleaved per thread (A::ILP; never changes the summation order).
+// Measured on GB300: the multi-word kernels are fastest with 1; FP64, which is
+// memory bound, needs several rows' loads in flight per thread.
 constexpr int NWARP = TPB / 32;
 
 enum { ST_CONVERGED = 0, ST_MAXIT = 1, ST_BREAKDOWN = 2, ST_GUARD = 3 };
@@ -220,32 +223,94 @@ __global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
   const int64_t ntiles = (n + R - 1) / R;
   T acc = A::zero();
   bool pacc = false;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t row = t * R + slot;
-    int64_t k0 = 0, k1 = 0;
-    if (row < n) { k0 = M.rp[row]; k1 = M.rp[row + 1]; }
-    const int64_t len = k1 - k0;
-    T sum = A::zero();
-    bool ps = false;
-    int64_t k = k0 + lane_in_row;
-    if (k < k1) {
-      sum = A::dxmul(M.val[k], ld<A>(p, n, M.col[k]));
-      ps = true;
-      for (k += V; k < k1; k += V) sum = A::dxmuladd(sum, M.val[k], ld<A>(p, n, M.col[k]));
+  // A::ILP tiles (t, t+G, ...) per pass: their rows' chains are independent,
+  // so interleaving them hides latency; the dot leaves are still added in
+  // increasing tile order, so the summation order is unchanged.
+  for (int64_t t = blockIdx.x; t < ntiles; t += (int64_t)A::ILP * gridDim.x) {
+    T sum[A::ILP];
+    bool ps[A::ILP];
+    int64_t row[A::ILP], kk[A::ILP], ke[A::ILP], len[A::ILP];
+#pragma unroll
+    for (int u = 0; u < A::ILP; ++u) {
+      const int64_t tu = t + (int64_t)u * gridDim.x;
+      row[u] = tu * R + slot;
+      int64_t k0 = 0, k1 = 0;
+      if (tu < ntiles && row[u] < n) { k0 = M.rp[row[u]]; k1 = M.rp[row[u] + 1]; }
+      len[u] = k1 - k0;
+      kk[u] = k0 + lane_in_row;
+      ke[u] = k1;
+      sum[u] = A::zero();
+      ps[u] = false;
+      if (kk[u] < ke[u]) {
+        sum[u] = A::dxmul(M.val[kk[u]], ld<A>(p, n, M.col[kk[u]]));
+        ps[u] = true;
+        kk[u] += V;
+      }
     }
-    // Pairwise tree over the V lanes of the row (groups are aligned in the warp).
-    for (int h = 1; h < V; h <<= 1) {
-      T o = shfl_down<A>(sum, h);
-      bool po = (lane_in_row % (2 * h)) == 0 && lane_in_row + h < len;
-      if (po) combine<A>(sum, ps, o, true);
+    if constexpr (A::CHUNK == 1) {
+      for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int u = 0; u < A::ILP; ++u) {
+          if (kk[u] < ke[u]) {
+            sum[u] = A::dxmuladd(sum[u], M.val[kk[u]], ld<A>(p, n, M.col[kk[u]]));
+            kk[u] += V;
+          }
+          more = more || (kk[u] < ke[u]);
+        }
+        if (!more) break;
+      }
+    } else {
+      // Memory-bound arithmetic: issue the loads of A::CHUNK entries of every
+      // interleaved row before the first multiply-add; the products are still
+      // added in entry order.
+      for (;;) {
+        bool more = false;
+        double va[A::ILP][A::CHUNK];
+        T pv[A::ILP][A::CHUNK];
+#pragma unroll
+        for (int u = 0; u < A::ILP; ++u) {
+#pragma unroll
+          for (int c = 0; c < A::CHUNK; ++c) {
+            const int64_t k = kk[u] + (int64_t)c * V;
+            va[u][c] = 0.0;
+            if (k < ke[u]) { va[u][c] = M.val[k]; pv[u][c] = ld<A>(p, n, M.col[k]); }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < A::ILP; ++u) {
+#pragma unroll
+          for (int c = 0; c < A::CHUNK; ++c) {
+            if (kk[u] < ke[u]) {
+              sum[u] = A::dxmuladd(sum[u], va[u][c], pv[u][c]);
+              kk[u] += V;
+            }
+          }
+          more = more || (kk[u] < ke[u]);
+        }
+        if (!more) break;
+      }
     }
-    if (lane_in_row == 0 && row < n) {
-      if (!ps) sum = A::zero();
-      st<A>(q, n, row, sum);
-      if (mode == 1) {
-        T leaf = A::mul(ld<A>(p, n, row), sum);
-        if (pacc) acc = A::add(acc, leaf);
-        else { acc = leaf; pacc = true; }
+#pragma unroll
+    for (int u = 0; u < A::ILP; ++u) {
+      // Pairwise tree over the V lanes of the row (groups are aligned in the warp).
+      for (int h = 1; h < V; h <<= 1) {
+        T o = shfl_down<A>(sum[u], h);
+        bool po = (lane_in_row % (2 * h)) == 0 && lane_in_row + h < len[u];
+        if (po) combine<A>(sum[u], ps[u], o, true);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < A::ILP; ++u) {
+      const int64_t tu = t + (int64_t)u * gridDim.x;
+      if (lane_in_row == 0 && tu < ntiles && row[u] < n) {
+        if (!ps[u]) sum[u] = A::zero();
+        st<A>(q, n, row[u], sum[u]);
+        if (mode == 1) {
+          T leaf = A::mul(ld<A>(p, n, row[u]), sum[u]);
+          if (pacc) acc = A::add(acc, leaf);
+          else { acc = leaf; pacc = true; }
+        }
       }
     }
   }
@@ -414,16 +479,62 @@ __global__ void __launch_bounds__(TPB) k_update(Csr M, Work W) {
   const int64_t ntiles = (n + TPB - 1) / TPB;
   T acc = A::zero();
   bool pacc = false;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t i = t * TPB + threadIdx.x;
-    if (i < n) {
-      st<A>(x, n, i, A::muladd(ld<A>(x, n, i), al, ld<A>(W.p, n, i)));
-      T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
-      A::normalize(ri);
-      st<A>(W.r, n, i, ri);
-      T leaf = A::mul(ri, ri);
-      if (pacc) acc = A::add(acc, leaf);
-      else { acc = leaf; pacc = true; }
+  if constexpr (A::ILP == 1) {
+    // One row at a time: loads, update and store interleave (fewer live registers).
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int64_t i = t * TPB + threadIdx.x;
+      if (i < n) {
+        st<A>(x, n, i, A::muladd(ld<A>(x, n, i), al, ld<A>(W.p, n, i)));
+        T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
+        A::normalize(ri);
+        st<A>(W.r, n, i, ri);
+        T leaf = A::mul(ri, ri);
+        if (pacc) acc = A::add(acc, leaf);
+        else { acc = leaf; pacc = true; }
+      }
+    }
+  } else {
+    for (int64_t t = blockIdx.x; t < ntiles; t += (int64_t)A::ILP * gridDim.x) {
+      T leaf[A::ILP], xs[A::ILP], ps_[A::ILP], rs[A::ILP], qs[A::ILP];
+      bool valid[A::ILP];
+      int64_t idx[A::ILP];
+      // All loads first (several rows' loads in flight), then compute, then store.
+#pragma unroll
+      for (int u = 0; u < A::ILP; ++u) {
+        const int64_t tu = t + (int64_t)u * gridDim.x;
+        idx[u] = tu * TPB + threadIdx.x;
+        valid[u] = tu < ntiles && idx[u] < n;
+        if (valid[u]) {
+          xs[u] = ld<A>(x, n, idx[u]);
+          ps_[u] = ld<A>(W.p, n, idx[u]);
+          rs[u] = ld<A>(W.r, n, idx[u]);
+          qs[u] = ld<A>(W.q, n, idx[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < A::ILP; ++u) {
+        leaf[u] = A::zero();
+        if (valid[u]) {
+          xs[u] = A::muladd(xs[u], al, ps_[u]);
+          rs[u] = A::muladd(rs[u], mal, qs[u]);
+          A::normalize(rs[u]);
+          leaf[u] = A::mul(rs[u], rs[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < A::ILP; ++u) {
+        if (valid[u]) {
+          st<A>(x, n, idx[u], xs[u]);
+          st<A>(W.r, n, idx[u], rs[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < A::ILP; ++u) {
+        if (valid[u]) {
+          if (pacc) acc = A::add(acc, leaf[u]);
+          else { acc = leaf[u]; pacc = true; }
+        }
+      }
     }
   }
   block_tree<A>(acc, pacc, 1);
@@ -470,8 +581,25 @@ __global__ void __launch_bounds__(TPB) k_pupdate(Csr M, Work W) {
   T be;
 #pragma unroll
   for (int k = 0; k < A::W; ++k) be.w[k] = S->beta[k];
-  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB)
-    st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i)));
+  const int64_t stride = (int64_t)gridDim.x * TPB;
+  if constexpr (A::ILP == 1) {
+    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride)
+      st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i)));
+    return;
+  }
+  for (int64_t i0 = (int64_t)blockIdx.x * TPB + threadIdx.x; i0 < n; i0 += (int64_t)A::ILP * stride) {
+    T rr[A::ILP], pp[A::ILP];
+#pragma unroll
+    for (int u = 0; u < A::ILP; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < n) { rr[u] = ld<A>(W.r, n, i); pp[u] = ld<A>(W.p, n, i); }
+    }
+#pragma unroll
+    for (int u = 0; u < A::ILP; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < n) st<A>(W.p, n, i, A::muladd(rr[u], be, pp[u]));
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

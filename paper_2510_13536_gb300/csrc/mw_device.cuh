@@ -208,7 +208,18 @@ __device__ __forceinline__ void two_prod_w2(double a, double b, double& x, doubl
 template <int W> struct MW { double w[W]; };
 
 // ---------------------------------------------------------------- FP64
+#ifndef MWCG_ILP_FP64
+#define MWCG_ILP_FP64 4
+#endif
+#ifndef MWCG_ILP_MW
+#define MWCG_ILP_MW 1
+#endif
+#ifndef MWCG_CHUNK_FP64
+#define MWCG_CHUNK_FP64 2
+#endif
 struct FP64 {
+  static constexpr int ILP = MWCG_ILP_FP64;   // rows in flight per thread (memory bound)
+  static constexpr int CHUNK = MWCG_CHUNK_FP64; // SpMV entries loaded ahead per row
   static constexpr int W = 1;
   static constexpr bool QUASI = false;
   using T = MW<1>;
@@ -250,6 +261,8 @@ __device__ __forceinline__ double qadd_(double a, double b) {
 #endif
 template <int P = MWCG_DW_P_VEC>
 struct DWt {
+  static constexpr int ILP = MWCG_ILP_MW;
+  static constexpr int CHUNK = 1;
   static constexpr int W = 2;
   static constexpr bool QUASI = false;
   using T = MW<2>;
@@ -315,6 +328,8 @@ using DW_S = DWt<MWCG_DW_P_SPMV>;
 #endif
 template <bool NORM, int P = MWCG_QDW_P_VEC>
 struct QDWt {
+  static constexpr int ILP = MWCG_ILP_MW;
+  static constexpr int CHUNK = 1;
   static constexpr int W = 2;
   static constexpr bool QUASI = true;
   using T = MW<2>;
@@ -380,6 +395,8 @@ using QDW_NN_S = QDWt<false, MWCG_QDW_P_SPMV>;
 #endif
 template <bool NORM, int P = MWCG_QTW_P_VEC>
 struct QTWt {
+  static constexpr int ILP = MWCG_ILP_MW;
+  static constexpr int CHUNK = 1;
   static constexpr int W = 3;
   static constexpr bool QUASI = true;
   using T = MW<3>;
@@ -460,6 +477,8 @@ using QTW_NN_S = QTWt<false, MWCG_QTW_P_SPMV>;
 #define MWCG_TW_P 0
 #endif
 struct TW {
+  static constexpr int ILP = MWCG_ILP_MW;
+  static constexpr int CHUNK = 1;
   static constexpr int W = 3;
   static constexpr bool QUASI = false;
   using T = MW<3>;
