@@ -164,6 +164,14 @@ def _profiled_traffic(arith):
         return None
 
 
+def _golden_plan():
+    """Summation plan of the recorded full solve (the GB300 solver's plan)."""
+    try:
+        return tuple(json.load(open(GOLDEN))["plan"])
+    except Exception:
+        return (1, 256, 456)
+
+
 def _golden_iters(arith):
     try:
         g = json.load(open(GOLDEN))
@@ -172,16 +180,16 @@ def _golden_iters(arith):
         return None, None
 
 
-def oracle_sample(A, b, arith, iters_sample, total_iters):
+def oracle_sample(A, b, arith, iters_sample, total_iters, plan):
     """Time the CPU oracle (single thread) on `iters_sample` iterations of the
     workload and scale to `total_iters` iterations.  Returns (seconds, per_iter, detail)."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
-    oracle.cg(arith, A, b, tol=0.0, maxit=1, plan=(1, 256, 304))
+    oracle.cg(arith, A, b, tol=0.0, maxit=1, plan=plan)
     t_init1 = time.perf_counter() - t0                      # init + 1 iteration
     t0 = time.perf_counter()
-    oracle.cg(arith, A, b, tol=0.0, maxit=1 + iters_sample, plan=(1, 256, 304))
+    oracle.cg(arith, A, b, tol=0.0, maxit=1 + iters_sample, plan=plan)
     t_run = time.perf_counter() - t0                        # init + 1 + k iterations
     per_it = max(t_run - t_init1, 1e-9) / iters_sample
     init = max(t_init1 - per_it, 0.0)
@@ -397,7 +405,7 @@ def run_reference(args):
         return 0
     vals = []
     for s in range(args.warmup + args.steps):
-        est, per_it, init = oracle_sample(A, b, "qtw", 2, iters)
+        est, per_it, init = oracle_sample(A, b, "qtw", 2, iters, _golden_plan())
         if s >= args.warmup:
             vals.append(est)
     v = statistics.median(vals)
@@ -554,7 +562,7 @@ def run_gpu(args):
         gi, src = _golden_iters(arith)
         tot = gi if gi is not None else it
         src = src or "iteration count of this run (oracle count missing)"
-        est, per_it, init = oracle_sample(A, b_np, arith, 2, tot)
+        est, per_it, init = oracle_sample(A, b_np, arith, 2, tot, M.plan)
         cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
                "sample": f"2 CG iterations + init of the full system, single thread, scaled to {tot} iterations "
                          f"({src}); {per_it:.3f} s per iteration"}

@@ -178,7 +178,9 @@ mwcg_plan choose_plan(const std::vector<int64_t>& len, int sms, int arith, int s
   p.V = bestV;
   p.T = mwk::TPB;
   const int64_t tiles = (n + mwk::TPB - 1) / mwk::TPB;
-  p.G = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)sms, std::min<int64_t>(tiles, kMaxG)));
+  // One resident wave: the kernels' launch bounds keep A::MINB = 3 blocks of
+  // 256 threads per SM within the register file.
+  p.G = (int)std::max<int64_t>(1, std::min<int64_t>(3 * (int64_t)sms, std::min<int64_t>(tiles, kMaxG)));
   // A system of at most `small_cluster` tiles is solved by one thread-block
   // cluster in a single launch (see run_solve).  With G >= tiles every tile is
   // its own block, so G = small_cluster gives the same summation order as

@@ -195,7 +195,7 @@ __device__ __forceinline__ bool grid_reduce(const Work& W, const typename A::T& 
 // q = A p (mode 1, fused with p^T q and the alpha step) or q = A x0 (mode 0).
 // ---------------------------------------------------------------------------
 template <class A>
-__global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
+__global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) {
   using T = typename A::T;
   DevState* S = W.st;
   if (mode == 1 && S->done) {
@@ -223,15 +223,15 @@ __global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
   const int64_t ntiles = (n + R - 1) / R;
   T acc = A::zero();
   bool pacc = false;
-  // A::ILP tiles (t, t+G, ...) per pass: their rows' chains are independent,
+  // A::ILP_SPMV tiles (t, t+G, ...) per pass: their rows' chains are independent,
   // so interleaving them hides latency; the dot leaves are still added in
   // increasing tile order, so the summation order is unchanged.
-  for (int64_t t = blockIdx.x; t < ntiles; t += (int64_t)A::ILP * gridDim.x) {
-    T sum[A::ILP];
-    bool ps[A::ILP];
-    int64_t row[A::ILP], kk[A::ILP], ke[A::ILP], len[A::ILP];
+  for (int64_t t = blockIdx.x; t < ntiles; t += (int64_t)A::ILP_SPMV * gridDim.x) {
+    T sum[A::ILP_SPMV];
+    bool ps[A::ILP_SPMV];
+    int64_t row[A::ILP_SPMV], kk[A::ILP_SPMV], ke[A::ILP_SPMV], len[A::ILP_SPMV];
 #pragma unroll
-    for (int u = 0; u < A::ILP; ++u) {
+    for (int u = 0; u < A::ILP_SPMV; ++u) {
       const int64_t tu = t + (int64_t)u * gridDim.x;
       row[u] = tu * R + slot;
       int64_t k0 = 0, k1 = 0;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
       for (;;) {
         bool more = false;
 #pragma unroll
-        for (int u = 0; u < A::ILP; ++u) {
+        for (int u = 0; u < A::ILP_SPMV; ++u) {
           if (kk[u] < ke[u]) {
             sum[u] = A::dxmuladd(sum[u], M.val[kk[u]], ld<A>(p, n, M.col[kk[u]]));
             kk[u] += V;
@@ -266,10 +266,10 @@ __global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
       // added in entry order.
       for (;;) {
         bool more = false;
-        double va[A::ILP][A::CHUNK];
-        T pv[A::ILP][A::CHUNK];
+        double va[A::ILP_SPMV][A::CHUNK];
+        T pv[A::ILP_SPMV][A::CHUNK];
 #pragma unroll
-        for (int u = 0; u < A::ILP; ++u) {
+        for (int u = 0; u < A::ILP_SPMV; ++u) {
 #pragma unroll
           for (int c = 0; c < A::CHUNK; ++c) {
             const int64_t k = kk[u] + (int64_t)c * V;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
           }
         }
 #pragma unroll
-        for (int u = 0; u < A::ILP; ++u) {
+        for (int u = 0; u < A::ILP_SPMV; ++u) {
 #pragma unroll
           for (int c = 0; c < A::CHUNK; ++c) {
             if (kk[u] < ke[u]) {
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
       }
     }
 #pragma unroll
-    for (int u = 0; u < A::ILP; ++u) {
+    for (int u = 0; u < A::ILP_SPMV; ++u) {
       // Pairwise tree over the V lanes of the row (groups are aligned in the warp).
       for (int h = 1; h < V; h <<= 1) {
         T o = shfl_down<A>(sum[u], h);
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(TPB) k_spmv(Csr M, Work W, int mode) {
       }
     }
 #pragma unroll
-    for (int u = 0; u < A::ILP; ++u) {
+    for (int u = 0; u < A::ILP_SPMV; ++u) {
       const int64_t tu = t + (int64_t)u * gridDim.x;
       if (lane_in_row == 0 && tu < ntiles && row[u] < n) {
         if (!ps[u]) sum[u] = A::zero();
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(TPB) k_zero_x(Csr M, Work W) {
 // x += alpha p; r += (-alpha) q; normalise r; rho' = r^T r; stop test; beta.
 // ---------------------------------------------------------------------------
 template <class A>
-__global__ void __launch_bounds__(TPB) k_update(Csr M, Work W) {
+__global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
   if (S->done) {
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(TPB) k_update(Csr M, Work W) {
 
 // p = r + beta p.
 template <class A>
-__global__ void __launch_bounds__(TPB) k_pupdate(Csr M, Work W) {
+__global__ void __launch_bounds__(TPB, A::MINB) k_pupdate(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
   if (S->done) return;

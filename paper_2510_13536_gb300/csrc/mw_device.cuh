@@ -209,10 +209,19 @@ template <int W> struct MW { double w[W]; };
 
 // ---------------------------------------------------------------- FP64
 #ifndef MWCG_ILP_FP64
-#define MWCG_ILP_FP64 4
+#define MWCG_ILP_FP64 2
 #endif
 #ifndef MWCG_ILP_MW
 #define MWCG_ILP_MW 1
+#endif
+#ifndef MWCG_ILP_SPMV_MW
+#define MWCG_ILP_SPMV_MW 1
+#endif
+#ifndef MWCG_MINB_FP64
+#define MWCG_MINB_FP64 3
+#endif
+#ifndef MWCG_MINB_MW
+#define MWCG_MINB_MW 3
 #endif
 #ifndef MWCG_CHUNK_FP64
 #define MWCG_CHUNK_FP64 2
@@ -220,6 +229,8 @@ template <int W> struct MW { double w[W]; };
 struct FP64 {
   static constexpr int ILP = MWCG_ILP_FP64;   // rows in flight per thread (memory bound)
   static constexpr int CHUNK = MWCG_CHUNK_FP64; // SpMV entries loaded ahead per row
+  static constexpr int ILP_SPMV = MWCG_ILP_FP64;
+  static constexpr int MINB = MWCG_MINB_FP64;  // blocks per SM the register budget must allow
   static constexpr int W = 1;
   static constexpr bool QUASI = false;
   using T = MW<1>;
@@ -263,6 +274,8 @@ template <int P = MWCG_DW_P_VEC>
 struct DWt {
   static constexpr int ILP = MWCG_ILP_MW;
   static constexpr int CHUNK = 1;
+  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_MW;
+  static constexpr int MINB = MWCG_MINB_MW;
   static constexpr int W = 2;
   static constexpr bool QUASI = false;
   using T = MW<2>;
@@ -330,6 +343,8 @@ template <bool NORM, int P = MWCG_QDW_P_VEC>
 struct QDWt {
   static constexpr int ILP = MWCG_ILP_MW;
   static constexpr int CHUNK = 1;
+  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_MW;
+  static constexpr int MINB = MWCG_MINB_MW;
   static constexpr int W = 2;
   static constexpr bool QUASI = true;
   using T = MW<2>;
@@ -397,6 +412,8 @@ template <bool NORM, int P = MWCG_QTW_P_VEC>
 struct QTWt {
   static constexpr int ILP = MWCG_ILP_MW;
   static constexpr int CHUNK = 1;
+  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_MW;
+  static constexpr int MINB = MWCG_MINB_MW;
   static constexpr int W = 3;
   static constexpr bool QUASI = true;
   using T = MW<3>;
@@ -479,6 +496,8 @@ using QTW_NN_S = QTWt<false, MWCG_QTW_P_SPMV>;
 struct TW {
   static constexpr int ILP = MWCG_ILP_MW;
   static constexpr int CHUNK = 1;
+  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_MW;
+  static constexpr int MINB = MWCG_MINB_MW;
   static constexpr int W = 3;
   static constexpr bool QUASI = false;
   using T = MW<3>;
