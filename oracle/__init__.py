@@ -62,6 +62,8 @@ def lib():
         L.orc_dot.restype = i32
         L.orc_cg.argtypes = [i32, i64, P, P, P, P, P, d, i32, i32, i32, i32, P, P, P]
         L.orc_cg.restype = i32
+        L.orc_cg_norm.argtypes = [i32, i64, P, P, P, P, P, d, i32, i32, i32, i32, i32, ctypes.c_uint32, P, P, P]
+        L.orc_cg_norm.restype = i32
         L.orc_grad_values.argtypes = [i32, i64, P, P, P, P, P]
         L.orc_grad_values.restype = i32
         L.orc_words.argtypes = [i32]
@@ -186,11 +188,17 @@ def dot(arith, u, v, R: int = 0, G: int = 1):
     return out
 
 
-def cg(arith, A, b, x0=None, tol=1e-12, maxit=1000, plan=None, history=False):
+# Normalisation places of the policy (see NormPolicy in mwcg_oracle.cpp).
+NORM_R, NORM_X, NORM_P, NORM_Q, NORM_SUM = 1, 2, 4, 8, 16
+
+
+def cg(arith, A, b, x0=None, tol=1e-12, maxit=1000, plan=None, history=False, norm=None):
     """Algorithm 1 in the given arithmetic.
 
     ``plan`` = (V, T, G) mirrors the CUDA summation order; None is the plain
-    order.  Returns (x[w, n], iters, relres, status[, history]).
+    order.  ``norm`` = (every, mask) is the normalisation policy of the quasi
+    arithmetics (None: Sec. IV-D's r after its AXPY, every iteration).
+    Returns (x[w, n], iters, relres, status[, history]).
     """
     k = arith_id(arith)
     w = WORDS[k]
@@ -201,9 +209,15 @@ def cg(arith, A, b, x0=None, tol=1e-12, maxit=1000, plan=None, history=False):
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
     hist = np.full(max(maxit, 1), np.nan) if history else None
-    st = lib().orc_cg(k, A.n, _p(rp), _p(col), _p(val), _p(b), _p(x), float(tol), int(maxit),
-                      int(V), int(T), int(G), ctypes.byref(it), ctypes.byref(rr),
-                      _p(hist) if history else None)
+    if norm is None:
+        st = lib().orc_cg(k, A.n, _p(rp), _p(col), _p(val), _p(b), _p(x), float(tol), int(maxit),
+                          int(V), int(T), int(G), ctypes.byref(it), ctypes.byref(rr),
+                          _p(hist) if history else None)
+    else:
+        every, mask = norm
+        st = lib().orc_cg_norm(k, A.n, _p(rp), _p(col), _p(val), _p(b), _p(x), float(tol), int(maxit),
+                               int(V), int(T), int(G), int(every), int(mask), ctypes.byref(it),
+                               ctypes.byref(rr), _p(hist) if history else None)
     if st < 0:
         raise ValueError(arith)
     if history:
@@ -222,10 +236,10 @@ def grad_values(arith, A, lam, x):
     return g
 
 
-def adjoint(arith, A, x, gx, tol, maxit, plan=None):
+def adjoint(arith, A, x, gx, tol, maxit, plan=None, norm=None):
     """Gradients of L with dL/dx = gx: (g_b = lambda collapsed, g_val, lambda, iters, relres, status)."""
     k = arith_id(arith)
-    lam, it, rr, st = cg(k, A, gx, None, tol, maxit, plan)
+    lam, it, rr, st = cg(k, A, gx, None, tol, maxit, plan, norm=norm)
     g_b = collapse(k, lam) if WORDS[k] > 1 else lam[0].copy()
     g_val = grad_values(k, A, lam, x)
     return g_b, g_val, lam, it, rr, st

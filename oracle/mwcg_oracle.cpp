@@ -9,7 +9,8 @@
 // High-Precision Arithmetic with Quasi Multi-Word Algorithms" (Mukunoki and
 // Ozaki): word algorithms of Sec. III (Algorithms 2-10), the solver of
 // Algorithm 1 with the implementation choices of Sec. IV-C (FP64 relative
-// residual) and Sec. IV-D (normalise r once per iteration, after its AXPY).
+// residual) and Sec. IV-D (normalise r once per iteration, after its AXPY),
+// and, as an extension, other normalisation frequencies and placements.
 // Where the paper is silent the reading taken is stated at the function.
 //
 // Build: plain C++17, -O2 -ffp-contract=off, no fast-math.  Every FP64
@@ -432,15 +433,36 @@ void pair_tree(std::vector<typename A::T>& v, std::vector<char>& present) {
 
 struct Plan { int V; int T; int G; };
 
+// Normalisation policy (an extension of Sec. IV-D, which normalises r once
+// per iteration after its AXPY and leaves the frequency and placement open).
+// On iterations it with every > 0 and it % every == 0 the masked places are
+// normalised with the arithmetic's normalisation (QuickTwoSum for QDW,
+// VecSum3 for QTW; nothing for the other arithmetics):
+//   NORM_R   r_i after the AXPY of Algorithm 1 line 8 (the paper's placement)
+//   NORM_X   x_i after the AXPY of line 7
+//   NORM_P   p_i after the update of line 14
+//   NORM_Q   q_i = (A p)_i once the row is complete, before the p^T q leaf
+//   NORM_SUM the SpMV row's running sum after every addition into it (each
+//            lane's accumulation and each lane-tree combine)
+// every = 0 never normalises.  The default {1, NORM_R} is Sec. IV-D.
+enum : unsigned { NORM_R = 1, NORM_X = 2, NORM_P = 4, NORM_Q = 8, NORM_SUM = 16 };
+struct NormPolicy { int every; unsigned mask; };
+inline unsigned norm_at(const NormPolicy& np, int it) {
+  return (np.every > 0 && it % np.every == 0) ? np.mask : 0u;
+}
+
 template <class A>
 typename A::T spmv_row(const int64_t* rp, const int32_t* col, const double* val,
-                       const double* p, int64_t n, int64_t i, int V) {
+                       const double* p, int64_t n, int64_t i, int V, bool sum_norm = false) {
   using T = typename A::T;
   int64_t s = rp[i], e = rp[i + 1];
   if (s == e) return A::zero();
   if (V <= 1) {
     T acc = A::dxmul(val[s], load<A>(p, n, col[s]));
-    for (int64_t k = s + 1; k < e; ++k) acc = A::dxmuladd(acc, val[k], load<A>(p, n, col[k]));
+    for (int64_t k = s + 1; k < e; ++k) {
+      acc = A::dxmuladd(acc, val[k], load<A>(p, n, col[k]));
+      if (sum_norm) A::normalize(acc);
+    }
     return acc;
   }
   std::vector<T> lane(V);
@@ -449,18 +471,37 @@ typename A::T spmv_row(const int64_t* rp, const int32_t* col, const double* val,
     int64_t k = s + l;
     if (k >= e) continue;
     T acc = A::dxmul(val[k], load<A>(p, n, col[k]));
-    for (k += V; k < e; k += V) acc = A::dxmuladd(acc, val[k], load<A>(p, n, col[k]));
+    for (k += V; k < e; k += V) {
+      acc = A::dxmuladd(acc, val[k], load<A>(p, n, col[k]));
+      if (sum_norm) A::normalize(acc);
+    }
     lane[l] = acc;
     present[l] = 1;
   }
-  pair_tree<A>(lane, present);
+  // Pairwise tree over the lanes; with sum_norm every combine is normalised.
+  for (size_t h = 1; h < (size_t)V; h <<= 1) {
+    for (size_t l = 0; l + h < (size_t)V; l += 2 * h) {
+      if (!present[l + h]) continue;
+      if (present[l]) {
+        lane[l] = A::add(lane[l], lane[l + h]);
+        if (sum_norm) A::normalize(lane[l]);
+      } else {
+        lane[l] = lane[l + h];
+        present[l] = 1;
+      }
+    }
+  }
   return lane[0];
 }
 
 template <class A>
 void spmv(const int64_t* rp, const int32_t* col, const double* val, const double* p,
-          double* q, int64_t n, int V) {
-  for (int64_t i = 0; i < n; ++i) store<A>(q, n, i, spmv_row<A>(rp, col, val, p, n, i, V));
+          double* q, int64_t n, int V, unsigned nm = 0) {
+  for (int64_t i = 0; i < n; ++i) {
+    auto qi = spmv_row<A>(rp, col, val, p, n, i, V, (nm & NORM_SUM) != 0);
+    if (nm & NORM_Q) A::normalize(qi);
+    store<A>(q, n, i, qi);
+  }
 }
 
 // Reduce per-row leaves (already computed) in the plain or mirrored order.
@@ -535,7 +576,8 @@ struct CGResult { int status; int iters; double relres; };
 
 template <class A>
 CGResult cg(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
-            const double* b, double* x, double tol, int maxit, Plan plan, double* hist) {
+            const double* b, double* x, double tol, int maxit, Plan plan, double* hist,
+            NormPolicy np = NormPolicy{1, NORM_R}) {
   using T = typename A::T;
   const int W = A::W;
   const bool plain = plan.V <= 0;
@@ -567,7 +609,8 @@ CGResult cg(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
   if (maxit <= 0) { res.status = ST_MAXIT; return res; }
 
   for (;;) {
-    spmv<A>(rp, col, val, p.data(), q.data(), n, V);
+    const unsigned nm = norm_at(np, res.iters + 1);     // this iteration's normalisations
+    spmv<A>(rp, col, val, p.data(), q.data(), n, V, nm);
     T pq = dot<A>(p.data(), q.data(), n, Rs, G, plain);
     res.iters += 1;
     double pqc = A::collapse(pq);
@@ -575,9 +618,11 @@ CGResult cg(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
     T alpha = A::div(rho, pq);
     T malpha = neg<A>(alpha);
     for (int64_t i = 0; i < n; ++i) {
-      store<A>(x, n, i, A::muladd(load<A>(x, n, i), alpha, load<A>(p.data(), n, i)));
+      T xi = A::muladd(load<A>(x, n, i), alpha, load<A>(p.data(), n, i));
+      if (nm & NORM_X) A::normalize(xi);
+      store<A>(x, n, i, xi);
       T ri = A::muladd(load<A>(r.data(), n, i), malpha, load<A>(q.data(), n, i));
-      A::normalize(ri);
+      if (nm & NORM_R) A::normalize(ri);
       store<A>(r.data(), n, i, ri);
     }
     T rho1 = dot<A>(r.data(), r.data(), n, Rv, G, plain);
@@ -588,8 +633,11 @@ CGResult cg(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
     if (!std::isfinite(relres)) { res.status = ST_BREAKDOWN; return res; }
     if (res.iters >= maxit) { res.status = ST_MAXIT; return res; }
     T beta = A::div(rho1, rho);
-    for (int64_t i = 0; i < n; ++i)
-      store<A>(p.data(), n, i, A::muladd(load<A>(r.data(), n, i), beta, load<A>(p.data(), n, i)));
+    for (int64_t i = 0; i < n; ++i) {
+      T pi = A::muladd(load<A>(r.data(), n, i), beta, load<A>(p.data(), n, i));
+      if (nm & NORM_P) A::normalize(pi);
+      store<A>(p.data(), n, i, pi);
+    }
     rho = rho1;
   }
 }
@@ -686,6 +734,16 @@ template <class A> struct OpCG {
     return r.status;
   }
 };
+template <class A> struct OpCGNorm {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                 int every, unsigned mask, int* iters, double* relres, double* hist) {
+    CGResult r = cg<A>(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist, NormPolicy{every, mask});
+    *iters = r.iters;
+    *relres = r.relres;
+    return r.status;
+  }
+};
 template <class A> struct OpGrad {
   static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* lam,
                  const double* x, double* g) {
@@ -751,6 +809,13 @@ int orc_cg(int arith, int64_t n, const int64_t* rp, const int32_t* col, const do
            const double* b, double* x, double tol, int maxit, int V, int T, int G,
            int* iters, double* relres, double* hist) {
   return dispatch<OpCG>(arith, n, rp, col, val, b, x, tol, maxit, V, T, G, iters, relres, hist);
+}
+// Algorithm 1 under a normalisation policy {every, mask} (NORM_* bits above).
+int orc_cg_norm(int arith, int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                int every, unsigned mask, int* iters, double* relres, double* hist) {
+  return dispatch<OpCGNorm>(arith, n, rp, col, val, b, x, tol, maxit, V, T, G, every, mask, iters,
+                            relres, hist);
 }
 int orc_grad_values(int arith, int64_t n, const int64_t* rp, const int32_t* col,
                     const double* lam, const double* x, double* g) {
