@@ -275,6 +275,56 @@ def run_c3(torch, mw, P, cpu):
     return out
 
 
+NORM_POLICIES = [(1, "r"), (0, ""), (2, "r"), (1, "r+x"), (1, "r+p"), (1, "r+q"), (1, "r+sum"),
+                 (1, "r+x+p+q+sum"), (2, "r+x+p+q+sum"), (4, "r+x+p+q+sum")]
+
+
+def _forward_error(x, xs):
+    """||x - x*||_2 / ||x*||_2 with x multi-word: the leading word's difference
+    from x* = +-1 is exact (Sterbenz) wherever it matters, the lower words add."""
+    e = x[0] - xs
+    for k in range(1, x.shape[0]):
+        e = e + x[k]
+    return float(np.linalg.norm(e) / np.linalg.norm(xs))
+
+
+def run_norm(torch, mw, P, cpu):
+    """Normalisation frequency and placement of the quasi arithmetics (the open
+    question of Sec. VI): iterations, time and forward error per policy, on
+    exact-solution systems; DW and TW (normalised by every operation) alongside."""
+    out = {"policies": "(every k iterations, places): r/x after their AXPYs, p after its update, "
+                       "q = A p per row, sum = the SpMV running sum after every addition"}
+    from paper_2510_13536_gb300 import _capi
+    for name, (tq, tt, maxit) in (("norm_poisson", (1e-26, 1e-38, 6000)),
+                                  ("norm_diffusion", (1e-26, 1e-38, 40000))):
+        A, b, xs = P.exact_solution_system(name)
+        M = mw.CSRMatrix.from_csr(A)
+        db = torch.as_tensor(b, device="cuda")
+        res = {"workload": P.NORM_SYSTEMS[name], "n": A.n, "nnz": A.nnz, "plan": list(M.plan), "runs": []}
+        for ar, tol in (("qdw", tq), ("qtw", tt)):
+            for every, places in NORM_POLICIES:
+                mask = sum(_capi.NORM[k] for k in places.split("+") if k)
+                M.normalization = (every, mask)
+                mw.solve(M, db, ar, tol, 2)                      # graph build, module load
+                r, ms = _timed(torch, lambda: mw.solve(M, db, ar, tol, maxit, history=True))
+                h = r.history.cpu().numpy() if r.iters else np.array([np.nan])
+                res["runs"].append({"arith": ar, "every": every, "places": places or "none", "tol": tol,
+                                    "iters": r.iters, "status": r.status, "time_s": ms / 1e3,
+                                    "ms_per_iter": ms / max(r.iters, 1), "min_relres": float(np.nanmin(h)),
+                                    "forward_error": _forward_error(r.x.cpu().numpy(), xs)})
+        M.normalization = (1, 1)
+        for ar, tol in (("dw", tq), ("tw", tt)):
+            mw.solve(M, db, ar, tol, 2)
+            r, ms = _timed(torch, lambda: mw.solve(M, db, ar, tol, maxit, history=True))
+            h = r.history.cpu().numpy() if r.iters else np.array([np.nan])
+            res["runs"].append({"arith": ar, "every": "every op", "places": "all", "tol": tol,
+                                "iters": r.iters, "status": r.status, "time_s": ms / 1e3,
+                                "ms_per_iter": ms / max(r.iters, 1), "min_relres": float(np.nanmin(h)),
+                                "forward_error": _forward_error(r.x.cpu().numpy(), xs)})
+        out[name] = res
+    return out
+
+
 def run_c4(torch, mw, P, cpu):
     specs = P.batch_specs(256, P.SEED_BASE + 4)
     systems = [P.build_batch_system(s) for s in specs]
@@ -385,6 +435,8 @@ def run_workloads(args):
             res = run_c4(torch, mw, P, not args.no_cpu)
         elif w == "c5":
             res = run_c5(torch, mw, P, not args.no_cpu, args.fd)
+        elif w == "norm":
+            res = run_norm(torch, mw, P, not args.no_cpu)
         else:
             raise SystemExit(f"unknown workload {w}")
         res["wall_s"] = time.perf_counter() - t0
@@ -613,7 +665,7 @@ def main():
     ap.add_argument("--kernels-only", type=int, default=0, metavar="N",
                     help="run N iterations with each kernel launched on its own (mwcg_profile_kernels) and print "
                          "their mean durations; used for ncu captures")
-    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5"],
+    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm"],
                     help="measure another configuration instead of the headline (one JSON line each)")
     ap.add_argument("--fd", type=int, default=32, help="finite-difference entries checked in c5")
     ap.add_argument("--plan", default=None, help="override the summation plan V,T,G (ncu / tuning runs)")

@@ -113,6 +113,33 @@ int mwcg_get_plan(const mwcg_csr* A, mwcg_plan* out);
 /* Pin a plan (V power of two in 1..32, T = 256, G in 1..1024); MWCG_ERR_ARG otherwise. */
 int mwcg_set_plan(mwcg_csr* A, const mwcg_plan* plan);
 
+/* Normalisation policy of the quasi arithmetics (QDW, QTW), per matrix handle.
+ * Sec. IV-D normalises the residual r once per iteration, right after its
+ * AXPY (Algorithm 1 line 8), and Sec. VI leaves the frequency and placement
+ * of normalisation open; this generalises it.  On CG iteration it (1-based)
+ * with every > 0 and it % every == 0, each place in mask is normalised with
+ * the arithmetic's normalisation (QuickTwoSum for QDW, VecSum3 for QTW):
+ *   MWCG_NORM_R    r_i after its AXPY (line 8)             -- the default
+ *   MWCG_NORM_X    x_i after its AXPY (line 7)
+ *   MWCG_NORM_P    p_i after its update (line 14)
+ *   MWCG_NORM_Q    q_i = (A p)_i once its row is complete (line 5), before
+ *                  it enters p^T q
+ *   MWCG_NORM_SUM  the SpMV row's running sum after every addition into it
+ *                  (each lane's accumulation and each lane-tree combine)
+ * every = 0 never normalises (bit-identical to MWCG_QDW_NN / MWCG_QTW_NN).
+ * The default is every = 1, mask = MWCG_NORM_R.  DW, TW and FP64 results are
+ * unaffected (their operations are normalised or single-word), as are the NN
+ * arithmetics (never normalised).  The policy applies to every later solve on
+ * the handle (mwcg_solve*, mwcg_adjoint, mwcg_solve_batched).
+ * Errors: every < 0 or unknown mask bits -> MWCG_ERR_ARG (policy unchanged). */
+#define MWCG_NORM_R 1u
+#define MWCG_NORM_X 2u
+#define MWCG_NORM_P 4u
+#define MWCG_NORM_Q 8u
+#define MWCG_NORM_SUM 16u
+int mwcg_set_normalization(mwcg_csr* A, int32_t every, uint32_t mask);
+int mwcg_get_normalization(const mwcg_csr* A, int32_t* every, uint32_t* mask);
+
 /* Solve A x = b by CG in the given arithmetic (Algorithm 1).
  *   b        device double[n];
  *   x        device double[w*n] (w = mwcg_words(arith)): x0 on entry, the

@@ -23,8 +23,11 @@ EXPORTS = [
     "mwcg_n", "mwcg_nnz", "mwcg_get_plan", "mwcg_set_plan", "mwcg_solve", "mwcg_solve_host",
     "mwcg_solve_history", "mwcg_solve_batched", "mwcg_adjoint", "mwcg_spmv", "mwcg_dot",
     "mwcg_word_op", "mwcg_collapse", "mwcg_profile_kernels", "mwcg_batched_cluster_size",
-    "mwcg_dot_noalloc", "mwcg_probe_peak",
+    "mwcg_dot_noalloc", "mwcg_probe_peak", "mwcg_set_normalization", "mwcg_get_normalization",
 ]
+
+# Normalisation places of the quasi arithmetics' policy (MWCG_NORM_* in mwcg.h).
+NORM = {"r": 1, "x": 2, "p": 4, "q": 8, "sum": 16}
 
 
 class Plan(ctypes.Structure):
@@ -62,6 +65,9 @@ def load(path: str | None = None):
         "mwcg_nnz": (i64, [P]),
         "mwcg_get_plan": (ctypes.c_int, [P, ctypes.POINTER(Plan)]),
         "mwcg_set_plan": (ctypes.c_int, [P, ctypes.POINTER(Plan)]),
+        "mwcg_set_normalization": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_uint32]),
+        "mwcg_get_normalization": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32),
+                                                  ctypes.POINTER(ctypes.c_uint32)]),
         "mwcg_solve": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, pi32, pd]),
         "mwcg_solve_host": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, pi32, pd]),
         "mwcg_solve_history": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, P, pi32, pd]),

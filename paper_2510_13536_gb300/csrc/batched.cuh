@@ -42,6 +42,8 @@ struct Sys {
   int32_t pad;
   double relres;    // out
   double* hist;     // optional per-iteration FP64 relative residual, or null
+  int32_t norm_every;   // normalisation policy (mwk::norm_at)
+  uint32_t norm_mask;
 };
 
 struct ClusterCtx {
@@ -138,8 +140,10 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   const int rank = cc.rank, C = cc.C;
   int buf = 0;
 
-  // q = A p (mode 0: p = x0, no dot) or fused with p^T q (mode 1).
-  auto spmv = [&](const double* __restrict__ p, bool dot, T& acc, bool& pacc) {
+  // q = A p (mode 0: p = x0, no dot) or fused with p^T q (mode 1); nm: the
+  // iteration's normalisation places (NORM_SUM, NORM_Q apply here).
+  auto spmv = [&](const double* __restrict__ p, bool dot, T& acc, bool& pacc, uint32_t nm) {
+    const bool nsum = (nm & mwk::NORM_SUM) != 0;
     for (int64_t t = rank; t < ntiles_s; t += C) {
       const int64_t row = t * R + slot;
       int64_t k0 = 0, k1 = 0;
@@ -151,15 +155,21 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
       if (k < k1) {
         sum = A::dxmul(S.val[k], mwk::ld<A>(p, n, S.col[k]));
         ps = true;
-        for (k += V; k < k1; k += V) sum = A::dxmuladd(sum, S.val[k], mwk::ld<A>(p, n, S.col[k]));
+        for (k += V; k < k1; k += V) {
+          sum = A::dxmuladd(sum, S.val[k], mwk::ld<A>(p, n, S.col[k]));
+          if (nsum) A::normalize(sum);
+        }
       }
       for (int h = 1; h < V; h <<= 1) {
         T o = mwk::shfl_down<A>(sum, h);
         bool po = (lane_in_row % (2 * h)) == 0 && lane_in_row + h < len;
+        const bool add = po && ps;
         if (po) mwk::combine<A>(sum, ps, o, true);
+        if (add && nsum) A::normalize(sum);
       }
       if (lane_in_row == 0 && row < n) {
         if (!ps) sum = A::zero();
+        if (nm & mwk::NORM_Q) A::normalize(sum);
         mwk::st<A>(S.q, n, row, sum);
         if (dot) {
           T leaf = A::mul(mwk::ld<A>(p, n, row), sum);
@@ -174,7 +184,7 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   {
     T dummy = A::zero();
     bool pd = false;
-    spmv(S.x, false, dummy, pd);
+    spmv(S.x, false, dummy, pd, 0u);
   }
   cc.cl.sync();                       // q = A x0 complete in global memory
   T acc = A::zero();
@@ -243,7 +253,8 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     cc.cl.sync();                     // p (and r, x) complete before the gathers
     acc = A::zero();
     pacc = false;
-    spmv(S.p, true, acc, pacc);
+    const uint32_t nm = mwk::norm_at(S.norm_every, S.norm_mask, iters + 1);
+    spmv(S.p, true, acc, pacc, nm);
     mwk::block_tree<A>(acc, pacc, V);
     bool ppq;
     T pq = cluster_reduce<A>(cc, slots, buf, acc, pacc, ppq);
@@ -272,9 +283,11 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     for (int64_t t = rank; t < ntiles_v; t += C) {
       const int64_t i = t * TPB + threadIdx.x;
       if (i < n) {
-        mwk::st<A>(S.x, n, i, A::muladd(mwk::ld<A>(S.x, n, i), al, mwk::ld<A>(S.p, n, i)));
+        T xi = A::muladd(mwk::ld<A>(S.x, n, i), al, mwk::ld<A>(S.p, n, i));
+        if (nm & mwk::NORM_X) A::normalize(xi);
+        mwk::st<A>(S.x, n, i, xi);
         T ri = A::muladd(mwk::ld<A>(S.r, n, i), mal, mwk::ld<A>(S.q, n, i));
-        A::normalize(ri);
+        if (nm & mwk::NORM_R) A::normalize(ri);
         mwk::st<A>(S.r, n, i, ri);
         T leaf = A::mul(ri, ri);
         if (pacc) acc = A::add(acc, leaf);
@@ -315,7 +328,11 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     // p = r + beta p on this CTA's rows (the update tiles).
     for (int64_t t = rank; t < ntiles_v; t += C) {
       const int64_t i = t * TPB + threadIdx.x;
-      if (i < n) mwk::st<A>(S.p, n, i, A::muladd(mwk::ld<A>(S.r, n, i), be, mwk::ld<A>(S.p, n, i)));
+      if (i < n) {
+        T pi = A::muladd(mwk::ld<A>(S.r, n, i), be, mwk::ld<A>(S.p, n, i));
+        if (nm & mwk::NORM_P) A::normalize(pi);
+        mwk::st<A>(S.p, n, i, pi);
+      }
     }
   }
   if (rank == 0 && threadIdx.x == 0) {

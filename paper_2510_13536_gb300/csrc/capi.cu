@@ -88,6 +88,7 @@ struct GraphCache {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   mwcg_plan plan{0, 0, 0};
+  bool pol = false;            // built with the policy-following loop kernels
 };
 
 int sm_count_of(int dev) {
@@ -124,6 +125,8 @@ struct mwcg_csr {
   double* hx = nullptr;
   GraphCache graphs[7];
   std::vector<int64_t> rowlen;  // host copy of row lengths (plan selection)
+  int32_t norm_every = 1;       // normalisation policy of the quasi arithmetics
+  uint32_t norm_mask = mwk::NORM_R;
 };
 
 namespace {
@@ -236,10 +239,26 @@ mwk::Work work_view(const mwcg_csr* A, unsigned long long cond, int has_cond) {
   return W;
 }
 
+// The loop kernels: the default instantiations implement the default
+// normalisation policy {1, NORM_R} with no run-time tests; any other policy
+// runs the instantiations that read it from the DevState.
+struct LoopKernels {
+  const void* spmv;
+  const void* update;
+  const void* pupdate;
+  bool pol;
+};
+LoopKernels loop_kernels(const mwcg_csr* A, const mwk::KernelTable* kt) {
+  const bool pol = !(A->norm_every == 1 && A->norm_mask == mwk::NORM_R);
+  if (pol) return {kt->spmv_pol, kt->update_pol, kt->pupdate_pol, true};
+  return {kt->spmv, kt->update, kt->pupdate, false};
+}
+
 // Build (or reuse) the graph of a whole solve in one arithmetic.
 int ensure_graph(mwcg_csr* A, int arith) {
   GraphCache& gc = A->graphs[arith];
-  if (gc.exec && gc.plan.V == A->plan.V && gc.plan.G == A->plan.G) return MWCG_OK;
+  const LoopKernels lk = loop_kernels(A, table(arith));
+  if (gc.exec && gc.plan.V == A->plan.V && gc.plan.G == A->plan.G && gc.pol == lk.pol) return MWCG_OK;
   if (gc.exec) cudaGraphExecDestroy(gc.exec);
   if (gc.graph) cudaGraphDestroy(gc.graph);
   gc = GraphCache{};
@@ -276,9 +295,9 @@ int ensure_graph(mwcg_csr* A, int arith) {
     return fail(MWCG_ERR_CUDA, "cudaGraphAddNode(while): %s", cudaGetErrorString(e));
   }
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if ((rc = add_kernel(&b0, body, nullptr, 0, kt->spmv, G, smem, M, W, mode1)) ||
-      (rc = add_kernel(&b1, body, &b0, 1, kt->update, G, smem, M, W)) ||
-      (rc = add_kernel(&b2, body, &b1, 1, kt->pupdate, G, 0, M, W))) {
+  if ((rc = add_kernel(&b0, body, nullptr, 0, lk.spmv, G, smem, M, W, mode1)) ||
+      (rc = add_kernel(&b1, body, &b0, 1, lk.update, G, smem, M, W)) ||
+      (rc = add_kernel(&b2, body, &b1, 1, lk.pupdate, G, 0, M, W))) {
     cudaGraphDestroy(g);
     return rc;
   }
@@ -291,6 +310,7 @@ int ensure_graph(mwcg_csr* A, int arith) {
   gc.graph = g;
   gc.exec = ex;
   gc.plan = A->plan;
+  gc.pol = lk.pol;
   return MWCG_OK;
 }
 
@@ -322,6 +342,7 @@ int run_eager(mwcg_csr* A, int arith, cudaStream_t s) {
   CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
   CK(cudaLaunchKernel(kt->init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
+  const LoopKernels lk = loop_kernels(A, kt);
   mwk::DevState* h = A->h_st;
   const int64_t batches = (int64_t)h->maxit / 16 + 2;
   for (int64_t bt = 0; bt < batches; ++bt) {
@@ -329,9 +350,9 @@ int run_eager(mwcg_csr* A, int arith, cudaStream_t s) {
     CK(cudaStreamSynchronize(s));
     if (h->done) break;
     for (int i = 0; i < 16; ++i) {
-      CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv1, smem, s));
-      CK(cudaLaunchKernel(kt->update, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
-      CK(cudaLaunchKernel(kt->pupdate, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
+      CK(cudaLaunchKernel(lk.spmv, dim3(G), dim3(mwk::TPB), a_spmv1, smem, s));
+      CK(cudaLaunchKernel(lk.update, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
+      CK(cudaLaunchKernel(lk.pupdate, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
     }
   }
   return MWCG_OK;
@@ -360,6 +381,8 @@ int run_cluster(mwcg_csr* A, const double* b, double* x, int arith, double tol, 
   q.arith = arith;
   q.V = A->plan.V;
   q.hist = hist;
+  q.norm_every = A->norm_every;
+  q.norm_mask = A->norm_mask;
   cudaError_t e = mwb_host::launch(&q, 1, s, A->plan.G, nullptr);
   if (e != cudaSuccess) return fail(MWCG_ERR_CUDA, "cluster solve: %s", cudaGetErrorString(e));
   if (iters_out) *iters_out = q.iters;
@@ -384,6 +407,8 @@ int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, in
   h->hist = hist;
   h->tol = tol;
   h->maxit = maxit;
+  h->norm_every = A->norm_every;
+  h->norm_mask = A->norm_mask;
   CK(cudaMemcpyAsync(A->st, h, sizeof *h, cudaMemcpyHostToDevice, s));
   if (eager) {
     if ((rc = run_eager(A, arith, s)) != MWCG_OK) return rc;
@@ -527,6 +552,22 @@ int mwcg_set_plan(mwcg_csr* A, const mwcg_plan* p) {
   if (!is_pow2_le32(p->V) || p->T != mwk::TPB || p->G < 1 || p->G > kMaxG)
     return fail(MWCG_ERR_ARG, "invalid plan V=%d T=%d G=%d", p->V, p->T, p->G);
   A->plan = *p;
+  return MWCG_OK;
+}
+
+int mwcg_set_normalization(mwcg_csr* A, int32_t every, uint32_t mask) {
+  if (!A) return fail(MWCG_ERR_ARG, "null matrix handle");
+  if (every < 0) return fail(MWCG_ERR_ARG, "every = %d < 0", (int)every);
+  if (mask & ~(uint32_t)mwk::NORM_ALL) return fail(MWCG_ERR_ARG, "unknown normalisation bits 0x%x", (unsigned)mask);
+  A->norm_every = every;
+  A->norm_mask = mask;
+  return MWCG_OK;
+}
+
+int mwcg_get_normalization(const mwcg_csr* A, int32_t* every, uint32_t* mask) {
+  if (!A || !every || !mask) return fail(MWCG_ERR_ARG, "null argument");
+  *every = A->norm_every;
+  *mask = A->norm_mask;
   return MWCG_OK;
 }
 
@@ -702,6 +743,8 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   h->x = x;
   h->tol = 0.0;
   h->maxit = niters;
+  h->norm_every = A->norm_every;
+  h->norm_mask = A->norm_mask;
   CK(cudaMemcpyAsync(A->st, h, sizeof *h, cudaMemcpyHostToDevice, s));
   mwk::Csr M = csr_view(A);
   mwk::Work W = work_view(A, 0, 0);
@@ -714,16 +757,17 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
   CK(cudaLaunchKernel(kt->init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
+  const LoopKernels lk = loop_kernels(A, kt);
   std::vector<cudaEvent_t> ev(3 * (size_t)niters + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   int err = MWCG_OK;
   cudaError_t ce = cudaEventRecord(ev[0], s);
   for (int i = 0; i < niters && ce == cudaSuccess; ++i) {
-    ce = cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv1, smem, s);
+    ce = cudaLaunchKernel(lk.spmv, dim3(G), dim3(mwk::TPB), a_spmv1, smem, s);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * i + 1], s);
-    if (ce == cudaSuccess) ce = cudaLaunchKernel(kt->update, dim3(G), dim3(mwk::TPB), a_mw, smem, s);
+    if (ce == cudaSuccess) ce = cudaLaunchKernel(lk.update, dim3(G), dim3(mwk::TPB), a_mw, smem, s);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * i + 2], s);
-    if (ce == cudaSuccess) ce = cudaLaunchKernel(kt->pupdate, dim3(G), dim3(mwk::TPB), a_mw, 0, s);
+    if (ce == cudaSuccess) ce = cudaLaunchKernel(lk.pupdate, dim3(G), dim3(mwk::TPB), a_mw, 0, s);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev[3 * i + 3], s);
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -788,6 +832,8 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
     q.maxit = maxit[s];
     q.arith = arith[s];
     q.V = A[s]->plan.V;
+    q.norm_every = A[s]->norm_every;
+    q.norm_mask = A[s]->norm_mask;
     double mac, add;
     op_costs(arith[s], mac, add);
     cost.push_back((double)A[s]->nnz * mac + (double)n * 10.0 * add);

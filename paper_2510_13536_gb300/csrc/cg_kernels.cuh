@@ -59,7 +59,25 @@ struct DevState {
   int32_t zero_x;
   uint32_t counter;         // last-block election
   uint32_t guard;           // loop passes seen by block 0 of k_spmv (hang guard)
+  int32_t norm_every;       // normalisation policy (quasi arithmetics): every k iterations, 0 never
+  uint32_t norm_mask;       // NORM_* places
 };
+
+// Normalisation places (an extension of Sec. IV-D, which normalises r after
+// its AXPY once per iteration and leaves frequency and placement open).  On
+// iteration it (1-based) with every > 0 and it % every == 0 the masked places
+// are normalised with A::normalize (QuickTwoSum for QDW, VecSum3 for QTW; the
+// other arithmetics' normalize is the identity):
+//   NORM_R   r_i after its AXPY (Algorithm 1 line 8; the default policy {1, R})
+//   NORM_X   x_i after its AXPY (line 7)
+//   NORM_P   p_i after its update (line 14)
+//   NORM_Q   q_i = (A p)_i once the row is complete, before the p^T q leaf
+//   NORM_SUM the SpMV row's running sum after every addition into it (each
+//            lane's accumulation and each lane-tree combine)
+enum : uint32_t { NORM_R = 1, NORM_X = 2, NORM_P = 4, NORM_Q = 8, NORM_SUM = 16, NORM_ALL = 31 };
+__host__ __device__ __forceinline__ uint32_t norm_at(int32_t every, uint32_t mask, int it) {
+  return (every > 0 && it % every == 0) ? mask : 0u;
+}
 
 struct Csr {
   const int64_t* __restrict__ rp;
@@ -194,7 +212,11 @@ __device__ __forceinline__ bool grid_reduce(const Work& W, const typename A::T& 
 // ---------------------------------------------------------------------------
 // q = A p (mode 1, fused with p^T q and the alpha step) or q = A x0 (mode 0).
 // ---------------------------------------------------------------------------
-template <class A>
+// POL: the instantiation that follows the handle's normalisation policy
+// (DevState norm_every / norm_mask).  The default instantiation implements
+// the default policy {1, NORM_R} with no tests at all: it never normalises
+// in the SpMV, and k_update normalises r on every iteration.
+template <class A, bool POL = false>
 __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) {
   using T = typename A::T;
   DevState* S = W.st;
@@ -217,6 +239,10 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
   double* __restrict__ q = W.q;
   const int64_t n = M.n;
   const int V = W.V;
+  // This iteration's normalisations (the init SpMV, mode 0, has none).  Every
+  // block reads iters before its ticket; the last block increments it after.
+  const uint32_t nm = (POL && mode == 1) ? norm_at(S->norm_every, S->norm_mask, S->iters + 1) : 0u;
+  const bool nsum = POL && (nm & NORM_SUM);
   const int R = TPB / V;
   const int lane_in_row = threadIdx.x % V;
   const int slot = threadIdx.x / V;
@@ -254,6 +280,9 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
         for (int u = 0; u < A::ILP_SPMV; ++u) {
           if (kk[u] < ke[u]) {
             sum[u] = A::dxmuladd(sum[u], M.val[kk[u]], ld<A>(p, n, M.col[kk[u]]));
+            if constexpr (POL) {
+              if (nsum) A::normalize(sum[u]);
+            }
             kk[u] += V;
           }
           more = more || (kk[u] < ke[u]);
@@ -297,7 +326,14 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
       for (int h = 1; h < V; h <<= 1) {
         T o = shfl_down<A>(sum[u], h);
         bool po = (lane_in_row % (2 * h)) == 0 && lane_in_row + h < len[u];
-        if (po) combine<A>(sum[u], ps[u], o, true);
+        if constexpr (POL) {
+          // A combine into a present lane is an addition: normalise it.
+          const bool add = po && ps[u];
+          if (po) combine<A>(sum[u], ps[u], o, true);
+          if (add && nsum) A::normalize(sum[u]);
+        } else {
+          if (po) combine<A>(sum[u], ps[u], o, true);
+        }
       }
     }
 #pragma unroll
@@ -305,6 +341,9 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
       const int64_t tu = t + (int64_t)u * gridDim.x;
       if (lane_in_row == 0 && tu < ntiles && row[u] < n) {
         if (!ps[u]) sum[u] = A::zero();
+        if constexpr (POL) {
+          if (nm & NORM_Q) A::normalize(sum[u]);
+        }
         st<A>(q, n, row[u], sum[u]);
         if (mode == 1) {
           T leaf = A::mul(ld<A>(p, n, row[u]), sum[u]);
@@ -461,8 +500,9 @@ __global__ void __launch_bounds__(TPB) k_zero_x(Csr M, Work W) {
 
 // ---------------------------------------------------------------------------
 // x += alpha p; r += (-alpha) q; normalise r; rho' = r^T r; stop test; beta.
+// POL as for k_spmv: the default instantiation normalises r every iteration.
 // ---------------------------------------------------------------------------
-template <class A>
+template <class A, bool POL = false>
 __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
@@ -477,6 +517,7 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   for (int k = 0; k < A::W; ++k) al.w[k] = S->alpha[k];
   mal = mw::neg<A>(al);
   const int64_t ntiles = (n + TPB - 1) / TPB;
+  const uint32_t nm = POL ? norm_at(S->norm_every, S->norm_mask, S->iters) : (uint32_t)NORM_R;
   T acc = A::zero();
   bool pacc = false;
   if constexpr (A::ILP == 1) {
@@ -484,9 +525,11 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const int64_t i = t * TPB + threadIdx.x;
       if (i < n) {
-        st<A>(x, n, i, A::muladd(ld<A>(x, n, i), al, ld<A>(W.p, n, i)));
+        T xi = A::muladd(ld<A>(x, n, i), al, ld<A>(W.p, n, i));
+        if (nm & NORM_X) A::normalize(xi);
+        st<A>(x, n, i, xi);
         T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
-        A::normalize(ri);
+        if (nm & NORM_R) A::normalize(ri);
         st<A>(W.r, n, i, ri);
         T leaf = A::mul(ri, ri);
         if (pacc) acc = A::add(acc, leaf);
@@ -516,8 +559,9 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
         leaf[u] = A::zero();
         if (valid[u]) {
           xs[u] = A::muladd(xs[u], al, ps_[u]);
+          if (nm & NORM_X) A::normalize(xs[u]);
           rs[u] = A::muladd(rs[u], mal, qs[u]);
-          A::normalize(rs[u]);
+          if (nm & NORM_R) A::normalize(rs[u]);
           leaf[u] = A::mul(rs[u], rs[u]);
         }
       }
@@ -571,8 +615,8 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   }
 }
 
-// p = r + beta p.
-template <class A>
+// p = r + beta p (POL: normalise p where the policy says so).
+template <class A, bool POL = false>
 __global__ void __launch_bounds__(TPB, A::MINB) k_pupdate(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
@@ -582,9 +626,13 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_pupdate(Csr M, Work W) {
 #pragma unroll
   for (int k = 0; k < A::W; ++k) be.w[k] = S->beta[k];
   const int64_t stride = (int64_t)gridDim.x * TPB;
+  const bool np_ = POL && (norm_at(S->norm_every, S->norm_mask, S->iters) & NORM_P) != 0;
   if constexpr (A::ILP == 1) {
-    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride)
-      st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i)));
+    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride) {
+      T pi = A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i));
+      if (np_) A::normalize(pi);
+      st<A>(W.p, n, i, pi);
+    }
     return;
   }
   for (int64_t i0 = (int64_t)blockIdx.x * TPB + threadIdx.x; i0 < n; i0 += (int64_t)A::ILP * stride) {
@@ -597,7 +645,11 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_pupdate(Csr M, Work W) {
 #pragma unroll
     for (int u = 0; u < A::ILP; ++u) {
       const int64_t i = i0 + u * stride;
-      if (i < n) st<A>(W.p, n, i, A::muladd(rr[u], be, pp[u]));
+      if (i < n) {
+        T pi = A::muladd(rr[u], be, pp[u]);
+        if (np_) A::normalize(pi);
+        st<A>(W.p, n, i, pi);
+      }
     }
   }
 }
@@ -677,6 +729,9 @@ __global__ void __launch_bounds__(TPB) k_word_op(int op, int64_t n, const double
 struct KernelTable {
   int words;
   const void* spmv;
+  const void* spmv_pol;     // the three loop kernels under a non-default normalisation policy
+  const void* update_pol;
+  const void* pupdate_pol;
   const void* init;
   const void* zero_x;
   const void* update;
@@ -694,6 +749,15 @@ KernelTable make_table() {
   KernelTable t;
   t.words = A::W;
   t.spmv = (const void*)&k_spmv<AS>;
+  if constexpr (A::NORMALISES) {
+    t.spmv_pol = (const void*)&k_spmv<AS, true>;
+    t.update_pol = (const void*)&k_update<A, true>;
+    t.pupdate_pol = (const void*)&k_pupdate<A, true>;
+  } else {                  // the policy cannot change these arithmetics' results
+    t.spmv_pol = t.spmv;
+    t.update_pol = t.update;
+    t.pupdate_pol = t.pupdate;
+  }
   t.init = (const void*)&k_init<A>;
   t.zero_x = (const void*)&k_zero_x<A::W>;
   t.update = (const void*)&k_update<A>;

@@ -233,6 +233,7 @@ struct FP64 {
   static constexpr int MINB = MWCG_MINB_FP64;  // blocks per SM the register budget must allow
   static constexpr int W = 1;
   static constexpr bool QUASI = false;
+  static constexpr bool NORMALISES = false;   // A::normalize is the identity
   using T = MW<1>;
   static __device__ __forceinline__ T zero() { return T{{0.0}}; }
   static __device__ __forceinline__ T from(double a) { return T{{a}}; }
@@ -278,6 +279,7 @@ struct DWt {
   static constexpr int MINB = MWCG_MINB_MW;
   static constexpr int W = 2;
   static constexpr bool QUASI = false;
+  static constexpr bool NORMALISES = false;   // A::normalize is the identity
   using T = MW<2>;
   static __device__ __forceinline__ T zero() { return T{{0.0, 0.0}}; }
   static __device__ __forceinline__ T from(double a) { return T{{a, 0.0}}; }
@@ -347,6 +349,7 @@ struct QDWt {
   static constexpr int MINB = MWCG_MINB_MW;
   static constexpr int W = 2;
   static constexpr bool QUASI = true;
+  static constexpr bool NORMALISES = NORM;   // false for the NN variants
   using T = MW<2>;
   static __device__ __forceinline__ T zero() { return T{{0.0, 0.0}}; }
   static __device__ __forceinline__ T from(double a) { return T{{a, 0.0}}; }
@@ -416,6 +419,7 @@ struct QTWt {
   static constexpr int MINB = MWCG_MINB_MW;
   static constexpr int W = 3;
   static constexpr bool QUASI = true;
+  static constexpr bool NORMALISES = NORM;   // false for the NN variants
   using T = MW<3>;
   static __device__ __forceinline__ T zero() { return T{{0.0, 0.0, 0.0}}; }
   static __device__ __forceinline__ T from(double a) { return T{{a, 0.0, 0.0}}; }
@@ -500,6 +504,7 @@ struct TW {
   static constexpr int MINB = MWCG_MINB_MW;
   static constexpr int W = 3;
   static constexpr bool QUASI = false;
+  static constexpr bool NORMALISES = false;   // A::normalize is the identity
   using T = MW<3>;
   static __device__ __forceinline__ T zero() { return T{{0.0, 0.0, 0.0}}; }
   static __device__ __forceinline__ T from(double a) { return T{{a, 0.0, 0.0}}; }

@@ -196,7 +196,12 @@ def power_law_laplacian(n: int, seed: int, mean_deg: float = 30.0, max_deg: floa
     return A
 
 
-def diffusion_2d(m: int, seed: int, sigma: float = 1.0) -> CSR:
+def _on_grid(v: np.ndarray, e: int = 20) -> np.ndarray:
+    """Round to the 2^-e grid (at least one grid step)."""
+    return np.maximum(np.round(v * 2.0 ** e), 1.0) * 2.0 ** -e
+
+
+def diffusion_2d(m: int, seed: int, sigma: float = 1.0, dyadic: bool = False) -> CSR:
     """Cell-centred variable-coefficient diffusion on an m×m grid, 5-point.
 
     Cell coefficients θ are lognormal(0, sigma).  An interior face between
@@ -204,12 +209,15 @@ def diffusion_2d(m: int, seed: int, sigma: float = 1.0) -> CSR:
     is a Dirichlet face with coefficient θ of its cell.  Row c holds
     ``sum of its face coefficients`` on the diagonal and ``-coefficient`` for
     each interior neighbour, so A is symmetric, irreducibly diagonally
-    dominant and SPD.
+    dominant and SPD.  ``dyadic=True`` rounds every face coefficient to the
+    2^-20 grid first, so that the diagonal sums, and A·x for x of ±1, are exact.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     theta = rng.lognormal(0.0, sigma, size=(m, m))
     hx = 2.0 * theta[:, 1:] * theta[:, :-1] / (theta[:, 1:] + theta[:, :-1])   # faces (y, x+1/2)
     hy = 2.0 * theta[1:, :] * theta[:-1, :] / (theta[1:, :] + theta[:-1, :])   # faces (y+1/2, x)
+    if dyadic:
+        hx, hy, theta = _on_grid(hx), _on_grid(hy), _on_grid(theta)
     diag = np.zeros((m, m))
     diag[:, 1:] += hx
     diag[:, :-1] += hx
@@ -360,6 +368,46 @@ def workload(name: str):
         A = diffusion_2d(512, SEED_BASE + 5)
         return A, rhs_normal(A.n, SEED_BASE + 5 + 100), 1e-20, 20000
     raise KeyError(name)
+
+
+def matvec_grid_exact(A: CSR, x: np.ndarray, e: int = 20) -> np.ndarray:
+    """b = A x for entries on the 2^-e grid and x of ±1, summed in FP64.
+
+    Every product is a multiple of 2^-e, so a row sum is exact when the sum
+    of the products' magnitudes stays below 2^(53-e); that is checked."""
+    prod = A.val * x[A.col]
+    if not np.all(np.round(prod * 2.0 ** e) == prod * 2.0 ** e):
+        raise ValueError("entries are not on the 2^-e grid")
+    starts = A.row_ptr[:-1]
+    nonempty = A.row_ptr[1:] > starts
+    mag = np.zeros(A.n)
+    out = np.zeros(A.n)
+    if A.nnz:
+        mag[nonempty] = np.add.reduceat(np.abs(prod), starts[nonempty])
+        out[nonempty] = np.add.reduceat(prod, starts[nonempty])
+    if np.any(mag >= 2.0 ** (53 - e)):
+        raise ValueError("row sums could round")
+    return out
+
+
+NORM_SYSTEMS = {
+    "norm_poisson": "3-D Poisson 7-point 128^3, x* random +-1, b = A x* (integers, exact)",
+    "norm_diffusion": "2-D diffusion 256^2, theta lognormal(0,1), coefficients on the 2^-20 grid, "
+                      "x* random +-1, b = A x* (exact)",
+}
+
+
+def exact_solution_system(name: str):
+    """(A, b, x*) with b = A x* exactly, for the normalisation-policy sweep."""
+    if name == "norm_poisson":
+        A = laplacian_3d(128)
+        xs = random_signs(A.n, SEED_BASE + 6)
+    elif name == "norm_diffusion":
+        A = diffusion_2d(256, SEED_BASE + 7, dyadic=True)
+        xs = random_signs(A.n, SEED_BASE + 7 + 200)
+    else:
+        raise KeyError(name)
+    return A, matvec_grid_exact(A, xs), xs
 
 
 def random_signs(n: int, seed: int) -> np.ndarray:

@@ -89,6 +89,21 @@ class CSRMatrix:
         p = Plan(*[int(v) for v in vtg])
         check(_capi.load().mwcg_set_plan(self._h, ctypes.byref(p)))
 
+    @property
+    def normalization(self) -> tuple[int, int]:
+        """(every, mask) of the quasi arithmetics' normalisation policy (mwcg.h)."""
+        e, m = ctypes.c_int32(0), ctypes.c_uint32(0)
+        check(_capi.load().mwcg_get_normalization(self._h, ctypes.byref(e), ctypes.byref(m)))
+        return (e.value, m.value)
+
+    @normalization.setter
+    def normalization(self, policy):
+        """policy = (every, mask), mask an int or an iterable of "r", "x", "p", "q", "sum"."""
+        every, mask = policy
+        if not isinstance(mask, int):
+            mask = sum(_capi.NORM[k] for k in set(mask))
+        check(_capi.load().mwcg_set_normalization(self._h, int(every), int(mask)))
+
     def update_values(self, val) -> None:
         L = _capi.load()
         if isinstance(val, torch.Tensor) and val.is_cuda:
