@@ -276,7 +276,7 @@ def run_c3(torch, mw, P, cpu):
 
 
 NORM_POLICIES = [(1, "r"), (0, ""), (2, "r"), (1, "r+x"), (1, "r+p"), (1, "r+q"), (1, "r+sum"),
-                 (1, "r+x+p+q+sum"), (2, "r+x+p+q+sum"), (4, "r+x+p+q+sum")]
+                 (1, "r+x+p+q+sum"), (2, "r+x+p+q+sum"), (2, "r+p"), (4, "r+p"), (8, "r+p")]
 
 
 def _forward_error(x, xs):

@@ -212,6 +212,26 @@ __device__ __forceinline__ bool grid_reduce(const Work& W, const typename A::T& 
 // ---------------------------------------------------------------------------
 // q = A p (mode 1, fused with p^T q and the alpha step) or q = A x0 (mode 0).
 // ---------------------------------------------------------------------------
+// Entries kk[u], kk[u] + V, ... < ke[u] of the interleaved rows added into
+// sum[u] left to right; NS: normalise the running sum after every addition.
+template <class A, bool NS>
+__device__ __forceinline__ void row_accumulate(const Csr& M, const double* __restrict__ p, int64_t n, int V,
+                                               typename A::T* sum, int64_t* kk, const int64_t* ke) {
+  for (;;) {
+    bool more = false;
+#pragma unroll
+    for (int u = 0; u < A::ILP_SPMV; ++u) {
+      if (kk[u] < ke[u]) {
+        sum[u] = A::dxmuladd(sum[u], M.val[kk[u]], ld<A>(p, n, M.col[kk[u]]));
+        if constexpr (NS) A::normalize(sum[u]);
+        kk[u] += V;
+      }
+      more = more || (kk[u] < ke[u]);
+    }
+    if (!more) break;
+  }
+}
+
 // POL: the instantiation that follows the handle's normalisation policy
 // (DevState norm_every / norm_mask).  The default instantiation implements
 // the default policy {1, NORM_R} with no tests at all: it never normalises
@@ -274,21 +294,10 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
       }
     }
     if constexpr (A::CHUNK == 1) {
-      for (;;) {
-        bool more = false;
-#pragma unroll
-        for (int u = 0; u < A::ILP_SPMV; ++u) {
-          if (kk[u] < ke[u]) {
-            sum[u] = A::dxmuladd(sum[u], M.val[kk[u]], ld<A>(p, n, M.col[kk[u]]));
-            if constexpr (POL) {
-              if (nsum) A::normalize(sum[u]);
-            }
-            kk[u] += V;
-          }
-          more = more || (kk[u] < ke[u]);
-        }
-        if (!more) break;
-      }
+      // The normalising loop is a separate copy (a test inside the loop would
+      // be if-converted and cost every entry the normalisation's issue slots).
+      if (nsum) row_accumulate<A, true>(M, p, n, V, sum, kk, ke);
+      else row_accumulate<A, false>(M, p, n, V, sum, kk, ke);
     } else {
       // Memory-bound arithmetic: issue the loads of A::CHUNK entries of every
       // interleaved row before the first multiply-add; the products are still
@@ -498,6 +507,31 @@ __global__ void __launch_bounds__(TPB) k_zero_x(Csr M, Work W) {
   for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < total; i += (int64_t)gridDim.x * TPB) S->x[i] = 0.0;
 }
 
+// One row per thread and tile: x += alpha p, r += (-alpha) q (normalised where
+// NX / NR say), and the r^T r leaf added into the thread's slot.
+template <class A, bool NX, bool NR>
+__device__ __forceinline__ void update_rows(const Csr& M, const Work& W, double* __restrict__ x,
+                                            const typename A::T& al, const typename A::T& mal,
+                                            typename A::T& acc, bool& pacc) {
+  using T = typename A::T;
+  const int64_t n = M.n;
+  const int64_t ntiles = (n + TPB - 1) / TPB;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i = t * TPB + threadIdx.x;
+    if (i < n) {
+      T xi = A::muladd(ld<A>(x, n, i), al, ld<A>(W.p, n, i));
+      if constexpr (NX) A::normalize(xi);
+      st<A>(x, n, i, xi);
+      T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
+      if constexpr (NR) A::normalize(ri);
+      st<A>(W.r, n, i, ri);
+      T leaf = A::mul(ri, ri);
+      if (pacc) acc = A::add(acc, leaf);
+      else { acc = leaf; pacc = true; }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // x += alpha p; r += (-alpha) q; normalise r; rho' = r^T r; stop test; beta.
 // POL as for k_spmv: the default instantiation normalises r every iteration.
@@ -521,19 +555,16 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   T acc = A::zero();
   bool pacc = false;
   if constexpr (A::ILP == 1) {
-    // One row at a time: loads, update and store interleave (fewer live registers).
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const int64_t i = t * TPB + threadIdx.x;
-      if (i < n) {
-        T xi = A::muladd(ld<A>(x, n, i), al, ld<A>(W.p, n, i));
-        if (nm & NORM_X) A::normalize(xi);
-        st<A>(x, n, i, xi);
-        T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
-        if (nm & NORM_R) A::normalize(ri);
-        st<A>(W.r, n, i, ri);
-        T leaf = A::mul(ri, ri);
-        if (pacc) acc = A::add(acc, leaf);
-        else { acc = leaf; pacc = true; }
+    // One loop copy per combination of the x / r normalisations (see
+    // row_accumulate); the default instantiation has only {r}.
+    if constexpr (!POL) {
+      update_rows<A, false, true>(M, W, x, al, mal, acc, pacc);
+    } else {
+      switch (((nm & NORM_X) ? 1 : 0) | ((nm & NORM_R) ? 2 : 0)) {
+        case 0: update_rows<A, false, false>(M, W, x, al, mal, acc, pacc); break;
+        case 1: update_rows<A, true, false>(M, W, x, al, mal, acc, pacc); break;
+        case 2: update_rows<A, false, true>(M, W, x, al, mal, acc, pacc); break;
+        default: update_rows<A, true, true>(M, W, x, al, mal, acc, pacc); break;
       }
     }
   } else {
@@ -628,10 +659,15 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_pupdate(Csr M, Work W) {
   const int64_t stride = (int64_t)gridDim.x * TPB;
   const bool np_ = POL && (norm_at(S->norm_every, S->norm_mask, S->iters) & NORM_P) != 0;
   if constexpr (A::ILP == 1) {
-    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride) {
-      T pi = A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i));
-      if (np_) A::normalize(pi);
-      st<A>(W.p, n, i, pi);
+    if (np_) {                // separate loop copies, as in row_accumulate
+      for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride) {
+        T pi = A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i));
+        A::normalize(pi);
+        st<A>(W.p, n, i, pi);
+      }
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride)
+        st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i)));
     }
     return;
   }
