@@ -64,6 +64,8 @@ def lib():
         L.orc_cg.restype = i32
         L.orc_cg_norm.argtypes = [i32, i64, P, P, P, P, P, d, i32, i32, i32, i32, i32, ctypes.c_uint32, P, P, P]
         L.orc_cg_norm.restype = i32
+        L.orc_pcg_jacobi.argtypes = [i32, i64, P, P, P, P, P, d, i32, i32, i32, i32, i32, ctypes.c_uint32, P, P, P]
+        L.orc_pcg_jacobi.restype = i32
         L.orc_grad_values.argtypes = [i32, i64, P, P, P, P, P]
         L.orc_grad_values.restype = i32
         L.orc_words.argtypes = [i32]
@@ -192,12 +194,14 @@ def dot(arith, u, v, R: int = 0, G: int = 1):
 NORM_R, NORM_X, NORM_P, NORM_Q, NORM_SUM = 1, 2, 4, 8, 16
 
 
-def cg(arith, A, b, x0=None, tol=1e-12, maxit=1000, plan=None, history=False, norm=None):
+def cg(arith, A, b, x0=None, tol=1e-12, maxit=1000, plan=None, history=False, norm=None, precond=None):
     """Algorithm 1 in the given arithmetic.
 
     ``plan`` = (V, T, G) mirrors the CUDA summation order; None is the plain
     order.  ``norm`` = (every, mask) is the normalisation policy of the quasi
     arithmetics (None: Sec. IV-D's r after its AXPY, every iteration).
+    ``precond`` = "jacobi" runs Jacobi-preconditioned CG (status 3: a
+    diagonal entry missing or not positive).
     Returns (x[w, n], iters, relres, status[, history]).
     """
     k = arith_id(arith)
@@ -209,7 +213,14 @@ def cg(arith, A, b, x0=None, tol=1e-12, maxit=1000, plan=None, history=False, no
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
     hist = np.full(max(maxit, 1), np.nan) if history else None
-    if norm is None:
+    if precond not in (None, "none", "jacobi"):
+        raise ValueError(precond)
+    if precond == "jacobi":
+        every, mask = norm if norm is not None else (1, NORM_R)
+        st = lib().orc_pcg_jacobi(k, A.n, _p(rp), _p(col), _p(val), _p(b), _p(x), float(tol), int(maxit),
+                                  int(V), int(T), int(G), int(every), int(mask), ctypes.byref(it),
+                                  ctypes.byref(rr), _p(hist) if history else None)
+    elif norm is None:
         st = lib().orc_cg(k, A.n, _p(rp), _p(col), _p(val), _p(b), _p(x), float(tol), int(maxit),
                           int(V), int(T), int(G), ctypes.byref(it), ctypes.byref(rr),
                           _p(hist) if history else None)
@@ -236,10 +247,10 @@ def grad_values(arith, A, lam, x):
     return g
 
 
-def adjoint(arith, A, x, gx, tol, maxit, plan=None, norm=None):
+def adjoint(arith, A, x, gx, tol, maxit, plan=None, norm=None, precond=None):
     """Gradients of L with dL/dx = gx: (g_b = lambda collapsed, g_val, lambda, iters, relres, status)."""
     k = arith_id(arith)
-    lam, it, rr, st = cg(k, A, gx, None, tol, maxit, plan, norm=norm)
+    lam, it, rr, st = cg(k, A, gx, None, tol, maxit, plan, norm=norm, precond=precond)
     g_b = collapse(k, lam) if WORDS[k] > 1 else lam[0].copy()
     g_val = grad_values(k, A, lam, x)
     return g_b, g_val, lam, it, rr, st

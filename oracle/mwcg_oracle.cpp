@@ -642,6 +642,107 @@ CGResult cg(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Jacobi-preconditioned CG (an extension: Sec. VI names preconditioning as
+// future work).  The textbook PCG recurrence with M^-1 = diag(w),
+// w_i = fl(1 / a_ii) in FP64, the preconditioner being FP64 like A:
+//   r0 = b - A x0, z0 = w (x) r0, p0 = z0, rho0 = r0^T z0
+//   loop: q = A p; alpha = rho / p^T q; x = x + alpha p; r = r + (-alpha) q;
+//         [normalisations of the policy]; z = w (x) r; rho' = r^T z;
+//         stop test; beta = rho' / rho; p = z + beta p
+// w (x) r is the arithmetic's FP64 x multi-word product (dxmul).  Readings:
+//  * The stopping residual stays an FP64 quantity (Sec. IV-C):
+//    sqrt(sum_i fl(c_i c_i)) / ||b||_2 with c_i = collapse(r_i), the sum an
+//    FP64 dot in the plan's order.  rho = r^T z is not a residual norm.
+//  * A diagonal entry that is missing, not positive or not finite makes the
+//    preconditioner undefined: status ST_BADPREC, x0 untouched, no iteration.
+//  * Breakdown, maxit, zero b / zero r0 and the normalisation policy are as
+//    in cg() above.
+// ---------------------------------------------------------------------------
+enum { ST_BADPREC = 3 };
+
+template <class A>
+CGResult pcg_jacobi(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                    const double* b, double* x, double tol, int maxit, Plan plan, double* hist,
+                    NormPolicy np) {
+  using T = typename A::T;
+  const int W = A::W;
+  const bool plain = plan.V <= 0;
+  const int V = plain ? 1 : plan.V;
+  const int64_t Rs = plain ? 1 : std::max(1, plan.T / V);
+  const int64_t Rv = plain ? 1 : plan.T;
+  const int G = plain ? 1 : plan.G;
+  CGResult res{ST_CONVERGED, 0, 0.0};
+
+  std::vector<double> w(n);
+  for (int64_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    bool found = false;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (col[k] == i) { d = val[k]; found = true; break; }
+    if (!found || !(d > 0.0) || !std::isfinite(d)) { res.status = ST_BADPREC; return res; }
+    w[i] = fdiv(1.0, d);
+  }
+  double bn = fsqrt(bnorm2(b, n, Rv, G, plain));
+  if (bn == 0.0) {
+    for (int64_t i = 0; i < W * n; ++i) x[i] = 0.0;
+    return res;
+  }
+  std::vector<double> r(W * n), z(W * n), p(W * n), q(W * n), c(n);
+  spmv<A>(rp, col, val, x, q.data(), n, V);
+  bool rzero = true;
+  for (int64_t i = 0; i < n; ++i) {
+    T ri = A::add(A::from(b[i]), neg<A>(load<A>(q.data(), n, i)));
+    for (int k = 0; k < W; ++k) rzero = rzero && (ri.w[k] == 0.0);
+    store<A>(r.data(), n, i, ri);
+    store<A>(z.data(), n, i, A::dxmul(w[i], ri));
+  }
+  if (rzero) return res;
+  if (maxit <= 0) {
+    for (int64_t i = 0; i < n; ++i) c[i] = A::collapse(load<A>(r.data(), n, i));
+    res.relres = fdiv(fsqrt(dot<FP64>(c.data(), c.data(), n, Rv, G, plain).w[0]), bn);
+    res.status = ST_MAXIT;
+    return res;
+  }
+  p = z;
+  T rho = dot<A>(r.data(), z.data(), n, Rv, G, plain);
+
+  for (;;) {
+    const unsigned nm = norm_at(np, res.iters + 1);
+    spmv<A>(rp, col, val, p.data(), q.data(), n, V, nm);
+    T pq = dot<A>(p.data(), q.data(), n, Rs, G, plain);
+    res.iters += 1;
+    double pqc = A::collapse(pq);
+    if (!(pqc > 0.0) || !std::isfinite(pqc)) { res.status = ST_BREAKDOWN; return res; }
+    T alpha = A::div(rho, pq);
+    T malpha = neg<A>(alpha);
+    for (int64_t i = 0; i < n; ++i) {
+      T xi = A::muladd(load<A>(x, n, i), alpha, load<A>(p.data(), n, i));
+      if (nm & NORM_X) A::normalize(xi);
+      store<A>(x, n, i, xi);
+      T ri = A::muladd(load<A>(r.data(), n, i), malpha, load<A>(q.data(), n, i));
+      if (nm & NORM_R) A::normalize(ri);
+      store<A>(r.data(), n, i, ri);
+      store<A>(z.data(), n, i, A::dxmul(w[i], ri));
+      c[i] = A::collapse(ri);
+    }
+    T rho1 = dot<A>(r.data(), z.data(), n, Rv, G, plain);
+    double relres = fdiv(fsqrt(dot<FP64>(c.data(), c.data(), n, Rv, G, plain).w[0]), bn);
+    res.relres = relres;
+    if (hist) hist[res.iters - 1] = relres;
+    if (relres < tol) { res.status = ST_CONVERGED; return res; }
+    if (!std::isfinite(relres)) { res.status = ST_BREAKDOWN; return res; }
+    if (res.iters >= maxit) { res.status = ST_MAXIT; return res; }
+    T beta = A::div(rho1, rho);
+    for (int64_t i = 0; i < n; ++i) {
+      T pi = A::muladd(load<A>(z.data(), n, i), beta, load<A>(p.data(), n, i));
+      if (nm & NORM_P) A::normalize(pi);
+      store<A>(p.data(), n, i, pi);
+    }
+    rho = rho1;
+  }
+}
+
 // Gradient of L = w^T x through A x = b (values only, sparsity kept):
 // dL/dval_k = -lambda_row(k) * x_col(k), lambda the adjoint solution, formed
 // as the arithmetic's product lambda_i * x_j and collapsed to FP64.
@@ -744,6 +845,17 @@ template <class A> struct OpCGNorm {
     return r.status;
   }
 };
+template <class A> struct OpPCG {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                 int every, unsigned mask, int* iters, double* relres, double* hist) {
+    CGResult r = pcg_jacobi<A>(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist,
+                               NormPolicy{every, mask});
+    *iters = r.iters;
+    *relres = r.relres;
+    return r.status;
+  }
+};
 template <class A> struct OpGrad {
   static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* lam,
                  const double* x, double* g) {
@@ -816,6 +928,13 @@ int orc_cg_norm(int arith, int64_t n, const int64_t* rp, const int32_t* col, con
                 int every, unsigned mask, int* iters, double* relres, double* hist) {
   return dispatch<OpCGNorm>(arith, n, rp, col, val, b, x, tol, maxit, V, T, G, every, mask, iters,
                             relres, hist);
+}
+// Jacobi-preconditioned CG (status 3: undefined preconditioner).
+int orc_pcg_jacobi(int arith, int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                   const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                   int every, unsigned mask, int* iters, double* relres, double* hist) {
+  return dispatch<OpPCG>(arith, n, rp, col, val, b, x, tol, maxit, V, T, G, every, mask, iters,
+                         relres, hist);
 }
 int orc_grad_values(int arith, int64_t n, const int64_t* rp, const int32_t* col,
                     const double* lam, const double* x, double* g) {

@@ -119,3 +119,32 @@ def fnorm(v) -> float:
     mpmath.mp.prec = 400
     return float(mpmath.sqrt(sum(mpmath.mpf(x.numerator) / x.denominator * mpmath.mpf(x.numerator) / x.denominator
                                  for x in v)))
+
+
+def pcg_exact(M, b, w, iters: int):
+    """Textbook preconditioned CG (x0 = 0, M^-1 = diag(w)) in exact rationals;
+    w holds FP64 numbers, taken exactly.  Returns the iterates x_1..x_k and
+    the squared residual norms r_k^T r_k."""
+    n = len(M)
+    wf = [Fraction(float(v)) for v in w]
+    x = [Fraction(0)] * n
+    r = [Fraction(float(v)) for v in b]
+    z = [wf[i] * r[i] for i in range(n)]
+    p = z[:]
+    rho = sum(r[i] * z[i] for i in range(n))
+    xs, rrs = [], []
+    for _ in range(iters):
+        q = [sum(M[i][j] * p[j] for j in range(n) if M[i][j] != 0) for i in range(n)]
+        alpha = rho / sum(p[i] * q[i] for i in range(n))
+        x = [x[i] + alpha * p[i] for i in range(n)]
+        r = [r[i] - alpha * q[i] for i in range(n)]
+        z = [wf[i] * r[i] for i in range(n)]
+        rho1 = sum(r[i] * z[i] for i in range(n))
+        xs.append(x[:])
+        rrs.append(sum(v * v for v in r))
+        if rho1 == 0:
+            break
+        beta = rho1 / rho
+        p = [z[i] + beta * p[i] for i in range(n)]
+        rho = rho1
+    return xs, rrs
