@@ -325,6 +325,30 @@ def run_norm(torch, mw, P, cpu):
     return out
 
 
+def run_pcg(torch, mw, P, cpu):
+    """Jacobi-preconditioned CG against Algorithm 1 on three workloads: the
+    3-D Poisson system (constant diagonal: the preconditioner only rescales),
+    the variable-coefficient diffusion system and the power-law graph
+    Laplacian (degrees 5..1000: the diagonal spans three orders of magnitude)."""
+    out = {}
+    for name in ("c2", "c5", "c3"):
+        A, b, tol, maxit = P.workload(name)
+        tol = 1e-14
+        M = mw.CSRMatrix.from_csr(A)
+        db = torch.as_tensor(b, device="cuda")
+        res = {"workload": name + ": " + P.WORKLOADS[name], "tol": tol, "maxit": maxit, "plan": list(M.plan)}
+        for ar in ("fp64", "dw", "qtw"):
+            for pc in ("none", "jacobi"):
+                M.preconditioner = pc
+                mw.solve(M, db, ar, tol, 2)                  # graph build, weights
+                r, ms = _timed(torch, lambda: mw.solve(M, db, ar, tol, maxit))
+                res[f"{ar}_{pc}"] = {"iters": r.iters, "status": r.status, "relres": r.relres, "time_s": ms / 1e3,
+                                     "ms_per_iter": ms / max(r.iters, 1)}
+            M.preconditioner = "none"
+        out[name] = res
+    return out
+
+
 def run_c4(torch, mw, P, cpu):
     specs = P.batch_specs(256, P.SEED_BASE + 4)
     systems = [P.build_batch_system(s) for s in specs]
@@ -437,6 +461,8 @@ def run_workloads(args):
             res = run_c5(torch, mw, P, not args.no_cpu, args.fd)
         elif w == "norm":
             res = run_norm(torch, mw, P, not args.no_cpu)
+        elif w == "pcg":
+            res = run_pcg(torch, mw, P, not args.no_cpu)
         else:
             raise SystemExit(f"unknown workload {w}")
         res["wall_s"] = time.perf_counter() - t0
@@ -665,7 +691,7 @@ def main():
     ap.add_argument("--kernels-only", type=int, default=0, metavar="N",
                     help="run N iterations with each kernel launched on its own (mwcg_profile_kernels) and print "
                          "their mean durations; used for ncu captures")
-    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm"],
+    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm", "pcg"],
                     help="measure another configuration instead of the headline (one JSON line each)")
     ap.add_argument("--fd", type=int, default=32, help="finite-difference entries checked in c5")
     ap.add_argument("--plan", default=None, help="override the summation plan V,T,G (ncu / tuning runs)")

@@ -53,6 +53,7 @@ enum {
   MWCG_OK = 0,              /* converged: relres < tol                                  */
   MWCG_NOT_CONVERGED = 1,   /* maxit iterations done without reaching tol               */
   MWCG_BREAKDOWN = 2,       /* collapse(p^T q) not > 0, or a non-finite residual        */
+  MWCG_BAD_PRECONDITIONER = 3, /* Jacobi: a diagonal entry missing, <= 0 or not finite; x0 untouched */
   MWCG_ERR_ARG = -1,        /* invalid argument (sizes, pointers, CSR structure, plan)  */
   MWCG_ERR_CUDA = -2,       /* a CUDA runtime call failed                               */
   MWCG_ERR_GUARD = -3,      /* device loop guard tripped (internal consistency failure) */
@@ -139,6 +140,27 @@ int mwcg_set_plan(mwcg_csr* A, const mwcg_plan* plan);
 #define MWCG_NORM_SUM 16u
 int mwcg_set_normalization(mwcg_csr* A, int32_t every, uint32_t mask);
 int mwcg_get_normalization(const mwcg_csr* A, int32_t* every, uint32_t* mask);
+
+/* Preconditioner of every later solve on the handle (mwcg_solve*,
+ * mwcg_adjoint, mwcg_solve_batched).  The paper's solver is unpreconditioned
+ * CG (Algorithm 1; Sec. VI names preconditioning as future work):
+ *   MWCG_PREC_NONE    Algorithm 1 (the default);
+ *   MWCG_PREC_JACOBI  preconditioned CG with M^-1 = diag(w), w_i = fl(1/a_ii)
+ *                     in FP64 (the preconditioner is FP64 like A): z = w (x) r
+ *                     is the arithmetic's FP64 x multi-word product,
+ *                     rho = r^T z in the arithmetic, p = z + beta p.  The
+ *                     stopping residual stays FP64 (Sec. IV-C):
+ *                     sqrt(sum_i collapse(r_i)^2) / ||b||_2, summed in FP64 in
+ *                     the plan's order.  The normalisation policy applies as
+ *                     in CG.  w is built on the device at the first solve
+ *                     after this call or after mwcg_update_values; a diagonal
+ *                     entry that is missing, not positive or not finite makes
+ *                     the solve return MWCG_BAD_PRECONDITIONER with x0 untouched.
+ * Errors: unknown kind -> MWCG_ERR_ARG. */
+#define MWCG_PREC_NONE 0
+#define MWCG_PREC_JACOBI 1
+int mwcg_set_preconditioner(mwcg_csr* A, int kind);
+int mwcg_get_preconditioner(const mwcg_csr* A, int* kind);
 
 /* Solve A x = b by CG in the given arithmetic (Algorithm 1).
  *   b        device double[n];

@@ -690,22 +690,20 @@ CGResult pcg_jacobi(int64_t n, const int64_t* rp, const int32_t* col, const doub
   }
   std::vector<double> r(W * n), z(W * n), p(W * n), q(W * n), c(n);
   spmv<A>(rp, col, val, x, q.data(), n, V);
-  bool rzero = true;
   for (int64_t i = 0; i < n; ++i) {
     T ri = A::add(A::from(b[i]), neg<A>(load<A>(q.data(), n, i)));
-    for (int k = 0; k < W; ++k) rzero = rzero && (ri.w[k] == 0.0);
     store<A>(r.data(), n, i, ri);
     store<A>(z.data(), n, i, A::dxmul(w[i], ri));
-  }
-  if (rzero) return res;
-  if (maxit <= 0) {
-    for (int64_t i = 0; i < n; ++i) c[i] = A::collapse(load<A>(r.data(), n, i));
-    res.relres = fdiv(fsqrt(dot<FP64>(c.data(), c.data(), n, Rv, G, plain).w[0]), bn);
-    res.status = ST_MAXIT;
-    return res;
+    c[i] = A::collapse(ri);
   }
   p = z;
   T rho = dot<A>(r.data(), z.data(), n, Rv, G, plain);
+  // r0 = 0 is detected as in cg(): every word of rho0 = r0^T z0 is zero.
+  bool rzero = true;
+  for (int k = 0; k < W; ++k) rzero = rzero && (rho.w[k] == 0.0);
+  if (rzero) return res;
+  res.relres = fdiv(fsqrt(dot<FP64>(c.data(), c.data(), n, Rv, G, plain).w[0]), bn);
+  if (maxit <= 0) { res.status = ST_MAXIT; return res; }
 
   for (;;) {
     const unsigned nm = norm_at(np, res.iters + 1);

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "libmwcg.so")
 
 ARITH = {"fp64": 0, "dw": 1, "qdw": 2, "tw": 3, "qtw": 4, "qdw_nn": 5, "qtw_nn": 6}
 WORDS = {0: 1, 1: 2, 2: 2, 3: 3, 4: 3, 5: 2, 6: 3}
-STATUS = {0: "converged", 1: "not_converged", 2: "breakdown"}
+STATUS = {0: "converged", 1: "not_converged", 2: "breakdown", 3: "bad_preconditioner"}
+PRECOND = {"none": 0, "jacobi": 1}
 ERRORS = {-1: "MWCG_ERR_ARG", -2: "MWCG_ERR_CUDA", -3: "MWCG_ERR_GUARD", -4: "MWCG_ERR_NOMEM"}
 
 # Every symbol declared in include/mwcg.h.
@@ -24,6 +25,7 @@ EXPORTS = [
     "mwcg_solve_history", "mwcg_solve_batched", "mwcg_adjoint", "mwcg_spmv", "mwcg_dot",
     "mwcg_word_op", "mwcg_collapse", "mwcg_profile_kernels", "mwcg_batched_cluster_size",
     "mwcg_dot_noalloc", "mwcg_probe_peak", "mwcg_set_normalization", "mwcg_get_normalization",
+    "mwcg_set_preconditioner", "mwcg_get_preconditioner",
 ]
 
 # Normalisation places of the quasi arithmetics' policy (MWCG_NORM_* in mwcg.h).
@@ -66,6 +68,8 @@ def load(path: str | None = None):
         "mwcg_get_plan": (ctypes.c_int, [P, ctypes.POINTER(Plan)]),
         "mwcg_set_plan": (ctypes.c_int, [P, ctypes.POINTER(Plan)]),
         "mwcg_set_normalization": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_uint32]),
+        "mwcg_set_preconditioner": (ctypes.c_int, [P, ctypes.c_int]),
+        "mwcg_get_preconditioner": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),
         "mwcg_get_normalization": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32),
                                                   ctypes.POINTER(ctypes.c_uint32)]),
         "mwcg_solve": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, pi32, pd]),

@@ -12,31 +12,10 @@
 namespace mwb {
 
 constexpr int kCluster = 8;                 // CTAs per worker cluster (portable maximum)
-constexpr size_t kPadSmem = 120 * 1024;     // dynamic shared memory that keeps one CTA per SM
 
-__global__ void __launch_bounds__(TPB, 1) k_batched(Sys* __restrict__ sys, int nsys, unsigned* queue) {
-  __shared__ Slots slots;
-  __shared__ int s_next;
-  cgx::cluster_group cl = cgx::this_cluster();
-  const ClusterCtx cc{cl, (int)cl.block_rank(), (int)cl.num_blocks()};
-  for (;;) {
-    if (cc.rank == 0 && threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
-    cl.sync();
-    const int sid = *cl.map_shared_rank(&s_next, 0);
-    cl.sync();                               // every CTA has read s_next before it is overwritten
-    if (sid >= nsys) break;
-    Sys& S = sys[sid];
-    switch (S.arith) {
-      case 0: solve_cluster<mw::FP64>(cc, &slots, S); break;
-      case 1: solve_cluster<mw::DW>(cc, &slots, S); break;
-      case 2: solve_cluster<mw::QDW>(cc, &slots, S); break;
-      case 3: solve_cluster<mw::TW>(cc, &slots, S); break;
-      case 4: solve_cluster<mw::QTW>(cc, &slots, S); break;
-      case 5: solve_cluster<mw::QDW_NN>(cc, &slots, S); break;
-      default: solve_cluster<mw::QTW_NN>(cc, &slots, S); break;
-    }
-  }
-}
+// Defined in batched_pcg.cu (run_group<true>).
+cudaError_t run_group_pcg(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int cluster, size_t pad,
+                          int* nclusters);
 
 }  // namespace mwb
 
@@ -57,8 +36,8 @@ int small_cluster_size() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return mwb::kCluster;
   if (g_small_cluster[dev]) return g_small_cluster[dev];
   int best = mwb::kCluster;
-  if (cudaFuncSetAttribute(mwb::k_batched, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-      cudaFuncSetAttribute(mwb::k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mwb::kPadSmem) ==
+  if (cudaFuncSetAttribute(mwb::k_batched<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(mwb::k_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mwb::kPadSmem) ==
           cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -72,7 +51,7 @@ int small_cluster_size() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, mwb::k_batched, &cfg) == cudaSuccess && n >= 1) best = 16;
+    if (cudaOccupancyMaxActiveClusters(&n, mwb::k_batched<false>, &cfg) == cudaSuccess && n >= 1) best = 16;
   }
   cudaGetLastError();
   g_small_cluster[dev] = best;
@@ -80,47 +59,44 @@ int small_cluster_size() {
 }
 
 // Launch the persistent kernel over `nsys` prepared systems (host array, in
-// queue order) with clusters of `cluster` CTAs.  Returns a cudaError_t;
-// outputs are copied back into hsys.
+// queue order) with clusters of `cluster` CTAs.  Systems without and with a
+// Jacobi preconditioner run as two consecutive launches (one kernel
+// instantiation each), each in queue order.  Returns a cudaError_t; outputs
+// are copied back into hsys.
 cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* clusters_out) {
   // MWCG_BATCH_PAD=0 drops the shared-memory pad that keeps one CTA per SM
   // (clusters may then share SMs); for tuning runs.
   const char* pad_env = std::getenv("MWCG_BATCH_PAD");
   const size_t pad = (pad_env && pad_env[0] == '0') ? 0 : mwb::kPadSmem;
+  std::vector<mwb::Sys> grp[2];
+  std::vector<int> where[2];
+  for (int i = 0; i < nsys; ++i) {
+    const int g = hsys[i].w ? 1 : 0;
+    grp[g].push_back(hsys[i]);
+    where[g].push_back(i);
+  }
   mwb::Sys* dsys = nullptr;
   unsigned* queue = nullptr;
   cudaError_t e = cudaMalloc(&dsys, sizeof(mwb::Sys) * nsys);
-  if (e == cudaSuccess) e = cudaMalloc(&queue, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dsys, hsys, sizeof(mwb::Sys) * nsys, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mwb::k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mwb::kPadSmem);
-  if (e == cudaSuccess && cluster > 8)
-    e = cudaFuncSetAttribute(mwb::k_batched, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(mwb::TPB);
-  cfg.dynamicSmemBytes = pad;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int nclusters = 0;
-  if (e == cudaSuccess) {
-    cfg.gridDim = dim3(cluster);
-    e = cudaOccupancyMaxActiveClusters(&nclusters, mwb::k_batched, &cfg);
+  if (e == cudaSuccess) e = cudaMalloc(&queue, 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s);
+  int nclusters = 0, off = 0;
+  for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
+    const int n = (int)grp[g].size();
+    if (n == 0) continue;
+    e = cudaMemcpyAsync(dsys + off, grp[g].data(), sizeof(mwb::Sys) * n, cudaMemcpyHostToDevice, s);
+    int nc = 0;
+    if (e == cudaSuccess)
+      e = g ? mwb::run_group_pcg(dsys + off, n, queue + g, s, cluster, pad, &nc)
+            : mwb::run_group<false>(dsys + off, n, queue + g, s, cluster, pad, &nc);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grp[g].data(), dsys + off, sizeof(mwb::Sys) * n, cudaMemcpyDeviceToHost, s);
+    nclusters = std::max(nclusters, nc);
+    off += n;
   }
-  if (e == cudaSuccess) {
-    nclusters = std::max(1, std::min(nclusters, nsys));
-    cfg.gridDim = dim3(nclusters * cluster);
-    int n = nsys;
-    e = cudaLaunchKernelEx(&cfg, mwb::k_batched, dsys, n, queue);
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hsys, dsys, sizeof(mwb::Sys) * nsys, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess)
+    for (int g = 0; g < 2; ++g)
+      for (size_t k = 0; k < grp[g].size(); ++k) hsys[where[g][k]] = grp[g][k];
   cudaFree(dsys);
   cudaFree(queue);
   if (clusters_out) *clusters_out = nclusters;

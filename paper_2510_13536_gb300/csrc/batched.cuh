@@ -44,6 +44,7 @@ struct Sys {
   double* hist;     // optional per-iteration FP64 relative residual, or null
   int32_t norm_every;   // normalisation policy (mwk::norm_at)
   uint32_t norm_mask;
+  const double* w;      // Jacobi weights (preconditioned CG), or null
 };
 
 struct ClusterCtx {
@@ -53,17 +54,21 @@ struct ClusterCtx {
 };
 
 // Partial slots in shared memory: [2 buffers][8 doubles] (3 words, presence,
-// FP64 value, presence).
+// FP64 value 1, FP64 value 2, presence 2, presence 1).
 struct Slots {
   double v[2][8];
 };
 
 // Reduce per-CTA values across the cluster: every CTA returns the same result.
+// Up to two FP64 values ride along (fv/pf into fp64/pfp64, fv2/pf2 into
+// fp64_2/pfp64_2), reduced by the same tree.
 template <class A>
 __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Slots* slots, int buf,
                                                         const typename A::T& v, bool pv, bool& pout,
                                                         double* fp64 = nullptr, bool* pfp64 = nullptr,
-                                                        double fv = 0.0, bool pf = false) {
+                                                        double fv = 0.0, bool pf = false,
+                                                        double* fp64_2 = nullptr, bool* pfp64_2 = nullptr,
+                                                        double fv2 = 0.0, bool pf2 = false) {
   using T = typename A::T;
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -71,12 +76,16 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
     slots->v[buf][3] = pv ? 1.0 : 0.0;
     slots->v[buf][4] = fv;
     slots->v[buf][7] = pf ? 1.0 : 0.0;
+    slots->v[buf][5] = fv2;
+    slots->v[buf][6] = pf2 ? 1.0 : 0.0;
   }
   cc.cl.sync();
   __shared__ T sv[32];
   __shared__ int sp[32];
   __shared__ double sf[32];
   __shared__ int spf[32];
+  __shared__ double sf2[32];
+  __shared__ int spf2[32];
   // Gather the C values (C <= 32) into this CTA's shared memory, then tree.
   if (threadIdx.x < (unsigned)cc.C) {
     Slots* rs = cc.cl.map_shared_rank(slots, (int)threadIdx.x);
@@ -87,12 +96,14 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
     sp[threadIdx.x] = rs->v[buf][3] != 0.0;
     sf[threadIdx.x] = rs->v[buf][4];
     spf[threadIdx.x] = rs->v[buf][7] != 0.0;
+    sf2[threadIdx.x] = rs->v[buf][5];
+    spf2[threadIdx.x] = rs->v[buf][6] != 0.0;
   }
   __syncthreads();
   __shared__ T res;
   __shared__ int pres;
-  __shared__ double resf;
-  __shared__ int presf;
+  __shared__ double resf, resf2;
+  __shared__ int presf, presf2;
   // Pairwise tree over the C values in warp 0: level h combines lane s with
   // lane s+h for s a multiple of 2h (the same order as a sequential tree, at
   // log2(C) dependent steps instead of C-1).
@@ -103,14 +114,19 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
     bool pa = (lane < C) ? (sp[lane] != 0) : false;
     mw::MW<1> c{{(lane < C) ? sf[lane] : 0.0}};
     bool pc = (lane < C) ? (spf[lane] != 0) : false;
+    mw::MW<1> c2{{(lane < C) ? sf2[lane] : 0.0}};
+    bool pc2 = (lane < C) ? (spf2[lane] != 0) : false;
     for (int h = 1; h < C; h <<= 1) {
       T o = mwk::shfl_down<A>(a, h);
       bool po = __shfl_down_sync(0xffffffffu, (int)pa, h) != 0;
       mw::MW<1> oc = mwk::shfl_down<mw::FP64>(c, h);
       bool poc = __shfl_down_sync(0xffffffffu, (int)pc, h) != 0;
+      mw::MW<1> oc2 = mwk::shfl_down<mw::FP64>(c2, h);
+      bool poc2 = __shfl_down_sync(0xffffffffu, (int)pc2, h) != 0;
       if ((lane % (2 * h)) == 0 && lane + h < C) {
         mwk::combine<A>(a, pa, o, po);
         mwk::combine<mw::FP64>(c, pc, oc, poc);
+        mwk::combine<mw::FP64>(c2, pc2, oc2, poc2);
       }
     }
     if (lane == 0) {
@@ -118,16 +134,22 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
       pres = pa;
       resf = c.w[0];
       presf = pc;
+      resf2 = c2.w[0];
+      presf2 = pc2;
     }
   }
   __syncthreads();
   pout = pres != 0;
   if (fp64) *fp64 = resf;
   if (pfp64) *pfp64 = presf != 0;
+  if (fp64_2) *fp64_2 = resf2;
+  if (pfp64_2) *pfp64_2 = presf2 != 0;
   return res;
 }
 
-template <class A>
+// PREC: Jacobi-preconditioned CG (z = w (x) r kept in q, rho = r^T z, FP64
+// stopping residual from the collapsed r), as k_init / k_update / k_pupdate.
+template <class A, bool PREC = false>
 __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   using T = typename A::T;
   const int64_t n = S.n;
@@ -189,16 +211,27 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   cc.cl.sync();                       // q = A x0 complete in global memory
   T acc = A::zero();
   bool pacc = false;
-  mw::MW<1> bb{{0.0}};
-  bool pbb = false;
+  mw::MW<1> bb{{0.0}}, rr{{0.0}};
+  bool pbb = false, prr = false;
   for (int64_t t = rank; t < ntiles_v; t += C) {
     const int64_t i = t * TPB + threadIdx.x;
     if (i < n) {
       const double bi = S.b[i];
       T ri = A::add(A::from(bi), mw::neg<A>(mwk::ld<A>(S.q, n, i)));
       mwk::st<A>(S.r, n, i, ri);
-      mwk::st<A>(S.p, n, i, ri);
-      T leaf = A::mul(ri, ri);
+      T leaf;
+      if constexpr (PREC) {
+        const T zi = A::dxmul(S.w[i], ri);
+        mwk::st<A>(S.p, n, i, zi);
+        leaf = A::mul(ri, zi);
+        const double c = A::collapse(ri);
+        mw::MW<1> lc{{mw::dmul(c, c)}};
+        if (prr) rr = mw::FP64::add(rr, lc);
+        else { rr = lc; prr = true; }
+      } else {
+        mwk::st<A>(S.p, n, i, ri);
+        leaf = A::mul(ri, ri);
+      }
       if (pacc) acc = A::add(acc, leaf);
       else { acc = leaf; pacc = true; }
       mw::MW<1> lb{{mw::dmul(bi, bi)}};
@@ -208,9 +241,10 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   }
   mwk::block_tree<A>(acc, pacc, 1);
   mwk::block_tree<mw::FP64>(bb, pbb, 1);
-  bool prho, pbn;
-  double bn2;
-  T rho = cluster_reduce<A>(cc, slots, buf, acc, pacc, prho, &bn2, &pbn, bb.w[0], pbb);
+  if constexpr (PREC) mwk::block_tree<mw::FP64>(rr, prr, 1);
+  bool prho, pbn, prrs = false;
+  double bn2, rrs = 0.0;
+  T rho = cluster_reduce<A>(cc, slots, buf, acc, pacc, prho, &bn2, &pbn, bb.w[0], pbb, &rrs, &prrs, rr.w[0], prr);
   buf ^= 1;
   // Scalar steps run on one thread per CTA (the FP64 pipe is shared by the
   // whole SM) and are broadcast through shared memory.  Every CTA's thread 0
@@ -229,7 +263,8 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
       bool rzero = true;
 #pragma unroll
       for (int k = 0; k < A::W; ++k) rzero = rzero && !mw::nonzero(rho.w[k]);
-      rr0 = __ddiv_rn(__dsqrt_rn(A::collapse(rho)), bnorm0);
+      rr0 = PREC ? __ddiv_rn(__dsqrt_rn(prrs ? rrs : 0.0), bnorm0)
+                 : __ddiv_rn(__dsqrt_rn(A::collapse(rho)), bnorm0);
       if (rzero) { rr0 = 0.0; fl = 2; }
       else if (S.maxit <= 0) { st0 = mwk::ST_MAXIT; fl = 2; }
     }
@@ -280,6 +315,8 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     const T mal = mw::neg<A>(al);
     acc = A::zero();
     pacc = false;
+    mw::MW<1> rq{{0.0}};
+    bool prq = false;
     for (int64_t t = rank; t < ntiles_v; t += C) {
       const int64_t i = t * TPB + threadIdx.x;
       if (i < n) {
@@ -289,19 +326,33 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
         T ri = A::muladd(mwk::ld<A>(S.r, n, i), mal, mwk::ld<A>(S.q, n, i));
         if (nm & mwk::NORM_R) A::normalize(ri);
         mwk::st<A>(S.r, n, i, ri);
-        T leaf = A::mul(ri, ri);
+        T leaf;
+        if constexpr (PREC) {
+          const T zi = A::dxmul(S.w[i], ri);      // z over q (this CTA's rows only)
+          mwk::st<A>(S.q, n, i, zi);
+          leaf = A::mul(ri, zi);
+          const double c = A::collapse(ri);
+          mw::MW<1> lc{{mw::dmul(c, c)}};
+          if (prq) rq = mw::FP64::add(rq, lc);
+          else { rq = lc; prq = true; }
+        } else {
+          leaf = A::mul(ri, ri);
+        }
         if (pacc) acc = A::add(acc, leaf);
         else { acc = leaf; pacc = true; }
       }
     }
     mwk::block_tree<A>(acc, pacc, 1);
-    bool prr;
-    T rho1 = cluster_reduce<A>(cc, slots, buf, acc, pacc, prr);
+    if constexpr (PREC) mwk::block_tree<mw::FP64>(rq, prq, 1);
+    bool prr, prqs = false;
+    double rqs = 0.0;
+    T rho1 = cluster_reduce<A>(cc, slots, buf, acc, pacc, prr, &rqs, &prqs, rq.w[0], prq);
     buf ^= 1;
     __syncthreads();
     if (threadIdx.x == 0) {
       if (!prr) rho1 = A::zero();
-      const double rr = __ddiv_rn(__dsqrt_rn(A::collapse(rho1)), bnorm);
+      const double rr = PREC ? __ddiv_rn(__dsqrt_rn(prqs ? rqs : 0.0), bnorm)
+                             : __ddiv_rn(__dsqrt_rn(A::collapse(rho1)), bnorm);
       if (S.hist && rank == 0) S.hist[iters - 1] = rr;
       int fl = 0;
       if (rr < S.tol) fl = 1;
@@ -325,11 +376,12 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     for (int k = 0; k < A::W; ++k) be.w[k] = s_sc[3 + k];
     if (!prr) rho1 = A::zero();
     rho = rho1;
-    // p = r + beta p on this CTA's rows (the update tiles).
+    // p = r + beta p (PREC: z + beta p) on this CTA's rows (the update tiles).
+    const double* __restrict__ src = PREC ? S.q : S.r;
     for (int64_t t = rank; t < ntiles_v; t += C) {
       const int64_t i = t * TPB + threadIdx.x;
       if (i < n) {
-        T pi = A::muladd(mwk::ld<A>(S.r, n, i), be, mwk::ld<A>(S.p, n, i));
+        T pi = A::muladd(mwk::ld<A>(src, n, i), be, mwk::ld<A>(S.p, n, i));
         if (nm & mwk::NORM_P) A::normalize(pi);
         mwk::st<A>(S.p, n, i, pi);
       }
@@ -341,6 +393,74 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     S.relres = relres;
   }
   cc.cl.sync();                       // x, outputs complete; slots free for the next system
+}
+
+template <bool PREC>
+__device__ __forceinline__ void solve_any(const ClusterCtx& cc, Slots* slots, Sys& S) {
+  switch (S.arith) {
+    case 0: solve_cluster<mw::FP64, PREC>(cc, slots, S); break;
+    case 1: solve_cluster<mw::DW, PREC>(cc, slots, S); break;
+    case 2: solve_cluster<mw::QDW, PREC>(cc, slots, S); break;
+    case 3: solve_cluster<mw::TW, PREC>(cc, slots, S); break;
+    case 4: solve_cluster<mw::QTW, PREC>(cc, slots, S); break;
+    case 5: solve_cluster<mw::QDW_NN, PREC>(cc, slots, S); break;
+    default: solve_cluster<mw::QTW_NN, PREC>(cc, slots, S); break;
+  }
+}
+
+// The persistent kernel: clusters take systems from the queue until it is
+// empty.  One instantiation per PREC (each compiled in its own translation
+// unit, batched.cu and batched_pcg.cu: a kernel holding every arithmetic's
+// solver is large).
+template <bool PREC>
+__global__ void __launch_bounds__(TPB, 1) k_batched(Sys* __restrict__ sys, int nsys, unsigned* queue) {
+  __shared__ Slots slots;
+  __shared__ int s_next;
+  cgx::cluster_group cl = cgx::this_cluster();
+  const ClusterCtx cc{cl, (int)cl.block_rank(), (int)cl.num_blocks()};
+  for (;;) {
+    if (cc.rank == 0 && threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
+    cl.sync();
+    const int sid = *cl.map_shared_rank(&s_next, 0);
+    cl.sync();                               // every CTA has read s_next before it is overwritten
+    if (sid >= nsys) break;
+    solve_any<PREC>(cc, &slots, sys[sid]);     // the host groups systems by PREC
+  }
+}
+
+constexpr size_t kPadSmem = 120 * 1024;     // dynamic shared memory that keeps one CTA per SM
+
+// Host: run k_batched<PREC> over n systems already on the device (queue
+// zeroed), clusters of `cluster` CTAs, as many clusters as fit at once (at
+// most n).  The translation unit that calls it holds that instantiation.
+template <bool PREC>
+cudaError_t run_group(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int cluster, size_t pad, int* nclusters) {
+  cudaError_t e = cudaFuncSetAttribute(k_batched<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPadSmem);
+  if (e == cudaSuccess && cluster > 8)
+    e = cudaFuncSetAttribute(k_batched<PREC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(TPB);
+  cfg.dynamicSmemBytes = pad;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (e == cudaSuccess) {
+    cfg.gridDim = dim3(cluster);
+    e = cudaOccupancyMaxActiveClusters(&nc, k_batched<PREC>, &cfg);
+  }
+  if (e == cudaSuccess) {
+    nc = nc < 1 ? 1 : (nc < n ? nc : n);
+    cfg.gridDim = dim3(nc * cluster);
+    e = cudaLaunchKernelEx(&cfg, k_batched<PREC>, dsys, n, queue);
+  }
+  if (nclusters) *nclusters = nc;
+  return e;
 }
 
 }  // namespace mwb

@@ -29,6 +29,11 @@ int small_cluster_size();
 cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* clusters_out);
 }  // namespace mwb_host
 
+namespace mwcg_precond {
+cudaError_t jacobi_weights(const int64_t* rp, const int32_t* col, const double* val, int64_t n, double* w,
+                           int* bad, cudaStream_t s);
+}  // namespace mwcg_precond
+
 namespace mwk {
 KernelTable table_fp64();
 KernelTable table_dw();
@@ -81,14 +86,15 @@ constexpr int kMaxG = 1024;
 constexpr int32_t kMaxIt = 1 << 30;
 
 // Dynamic shared memory of the last-block reductions: G slots of up to
-// (3 words + 1 FP64 + 2 int flags = 40 bytes).
-size_t red_smem(int G) { return (size_t)G * 40; }
+// 3 words + 2 FP64 + 3 one-byte flags (43 bytes, 44 KB at G = 1024, within
+// the 48 KB available without opting in).
+size_t red_smem(int G) { return (size_t)G * 44; }
 
 struct GraphCache {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   mwcg_plan plan{0, 0, 0};
-  bool pol = false;            // built with the policy-following loop kernels
+  int key = -1;                // kernel selection it was built with (LoopKernels::key)
 };
 
 int sm_count_of(int dev) {
@@ -127,6 +133,11 @@ struct mwcg_csr {
   std::vector<int64_t> rowlen;  // host copy of row lengths (plan selection)
   int32_t norm_every = 1;       // normalisation policy of the quasi arithmetics
   uint32_t norm_mask = mwk::NORM_R;
+  int prec = MWCG_PREC_NONE;    // preconditioner
+  double* w = nullptr;          // Jacobi weights, rebuilt after a value update
+  int* w_bad = nullptr;         // device flag of the weights kernel
+  bool w_valid = false;
+  bool w_undefined = false;     // a diagonal entry missing, not positive or not finite
 };
 
 namespace {
@@ -236,29 +247,43 @@ mwk::Work work_view(const mwcg_csr* A, unsigned long long cond, int has_cond) {
   W.has_cond = has_cond;
   W.V = A->plan.V;
   W.G = A->plan.G;
+  W.w = (A->prec == MWCG_PREC_JACOBI) ? A->w : nullptr;
   return W;
 }
 
 // The loop kernels: the default instantiations implement the default
 // normalisation policy {1, NORM_R} with no run-time tests; any other policy
-// runs the instantiations that read it from the DevState.
+// runs the instantiations that read it from the DevState.  A Jacobi
+// preconditioner selects the PCG init / update / p-update kernels.
 struct LoopKernels {
+  const void* init;
   const void* spmv;
   const void* update;
   const void* pupdate;
-  bool pol;
+  int key;                     // bit 0: policy kernels, bit 1: preconditioned
 };
 LoopKernels loop_kernels(const mwcg_csr* A, const mwk::KernelTable* kt) {
   const bool pol = !(A->norm_every == 1 && A->norm_mask == mwk::NORM_R);
-  if (pol) return {kt->spmv_pol, kt->update_pol, kt->pupdate_pol, true};
-  return {kt->spmv, kt->update, kt->pupdate, false};
+  const bool pc = A->prec == MWCG_PREC_JACOBI;
+  LoopKernels k;
+  k.key = (pol ? 1 : 0) | (pc ? 2 : 0);
+  k.init = pc ? kt->init_pcg : kt->init;
+  k.spmv = pol ? kt->spmv_pol : kt->spmv;
+  if (pc) {
+    k.update = pol ? kt->update_pcg_pol : kt->update_pcg;
+    k.pupdate = pol ? kt->pupdate_pcg_pol : kt->pupdate_pcg;
+  } else {
+    k.update = pol ? kt->update_pol : kt->update;
+    k.pupdate = pol ? kt->pupdate_pol : kt->pupdate;
+  }
+  return k;
 }
 
 // Build (or reuse) the graph of a whole solve in one arithmetic.
 int ensure_graph(mwcg_csr* A, int arith) {
   GraphCache& gc = A->graphs[arith];
   const LoopKernels lk = loop_kernels(A, table(arith));
-  if (gc.exec && gc.plan.V == A->plan.V && gc.plan.G == A->plan.G && gc.pol == lk.pol) return MWCG_OK;
+  if (gc.exec && gc.plan.V == A->plan.V && gc.plan.G == A->plan.G && gc.key == lk.key) return MWCG_OK;
   if (gc.exec) cudaGraphExecDestroy(gc.exec);
   if (gc.graph) cudaGraphDestroy(gc.graph);
   gc = GraphCache{};
@@ -279,7 +304,7 @@ int ensure_graph(mwcg_csr* A, int arith) {
   int rc;
   const int mode0 = 0, mode1 = 1;
   if ((rc = add_kernel(&n0, g, nullptr, 0, kt->spmv, G, smem, M, W, mode0)) ||
-      (rc = add_kernel(&n1, g, &n0, 1, kt->init, G, smem, M, W)) ||
+      (rc = add_kernel(&n1, g, &n0, 1, lk.init, G, smem, M, W)) ||
       (rc = add_kernel(&n2, g, &n1, 1, kt->zero_x, G, 0, M, W))) {
     cudaGraphDestroy(g);
     return rc;
@@ -310,13 +335,34 @@ int ensure_graph(mwcg_csr* A, int arith) {
   gc.graph = g;
   gc.exec = ex;
   gc.plan = A->plan;
-  gc.pol = lk.pol;
+  gc.key = lk.key;
   return MWCG_OK;
 }
 
 int ensure_ws(mwcg_csr* A) {
   if (A->ws || A->n == 0) return MWCG_OK;
   CK(cudaMalloc(&A->ws, sizeof(double) * 9 * (size_t)A->n));
+  return MWCG_OK;
+}
+
+// Jacobi weights for a preconditioned solve, built on first use after the
+// preconditioner was set or the values changed.  *undefined: a diagonal
+// entry is missing, not positive or not finite.
+int ensure_weights(mwcg_csr* A, cudaStream_t s, bool* undefined) {
+  *undefined = false;
+  if (A->prec != MWCG_PREC_JACOBI || A->n == 0) return MWCG_OK;
+  if (!A->w_valid) {
+    if (!A->w) CK(cudaMalloc(&A->w, sizeof(double) * (size_t)A->n));
+    if (!A->w_bad) CK(cudaMalloc(&A->w_bad, sizeof(int)));
+    CK(cudaMemsetAsync(A->w_bad, 0, sizeof(int), s));
+    CK(mwcg_precond::jacobi_weights(A->rp, A->col, A->val, A->n, A->w, A->w_bad, s));
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, A->w_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    A->w_undefined = bad != 0;
+    A->w_valid = true;
+  }
+  *undefined = A->w_undefined;
   return MWCG_OK;
 }
 
@@ -339,10 +385,10 @@ int run_eager(mwcg_csr* A, int arith, cudaStream_t s) {
   void* a_spmv0[] = {(void*)&M, (void*)&W, (void*)&mode0};
   void* a_spmv1[] = {(void*)&M, (void*)&W, (void*)&mode1};
   void* a_mw[] = {(void*)&M, (void*)&W};
-  CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
-  CK(cudaLaunchKernel(kt->init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
-  CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
   const LoopKernels lk = loop_kernels(A, kt);
+  CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
+  CK(cudaLaunchKernel(lk.init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
+  CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
   mwk::DevState* h = A->h_st;
   const int64_t batches = (int64_t)h->maxit / 16 + 2;
   for (int64_t bt = 0; bt < batches; ++bt) {
@@ -383,6 +429,7 @@ int run_cluster(mwcg_csr* A, const double* b, double* x, int arith, double tol, 
   q.hist = hist;
   q.norm_every = A->norm_every;
   q.norm_mask = A->norm_mask;
+  q.w = (A->prec == MWCG_PREC_JACOBI) ? A->w : nullptr;
   cudaError_t e = mwb_host::launch(&q, 1, s, A->plan.G, nullptr);
   if (e != cudaSuccess) return fail(MWCG_ERR_CUDA, "cluster solve: %s", cudaGetErrorString(e));
   if (iters_out) *iters_out = q.iters;
@@ -394,6 +441,13 @@ int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, in
               cudaStream_t s, int32_t* iters_out, double* relres_out) {
   int rc;
   if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
+  bool undefined = false;
+  if ((rc = ensure_weights(A, s, &undefined)) != MWCG_OK) return rc;
+  if (undefined) {                     // x0 untouched, no iteration
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return MWCG_BAD_PRECONDITIONER;
+  }
   const int64_t tiles = (A->n + mwk::TPB - 1) / mwk::TPB;
   const int small = mwb_host::small_cluster_size();
   if (!eager_mode() && A->plan.G == small && tiles <= small)
@@ -519,6 +573,8 @@ void mwcg_destroy_csr(mwcg_csr* A) {
   cudaFree(A->lam);
   cudaFree(A->hb);
   cudaFree(A->hx);
+  cudaFree(A->w);
+  cudaFree(A->w_bad);
   if (A->h_st) cudaFreeHost(A->h_st);
   delete A;
 }
@@ -535,6 +591,7 @@ int mwcg_update_values(mwcg_csr* A, const double* val, int on_device, void* stre
     if (!std::isfinite(hv[k])) return fail(MWCG_ERR_ARG, "val[%lld] is not finite", (long long)k);
   CK(cudaMemcpyAsync(A->val, hv.data(), sizeof(double) * A->nnz, cudaMemcpyHostToDevice, S(stream)));
   CK(cudaStreamSynchronize(S(stream)));
+  A->w_valid = false;                  // Jacobi weights follow the new diagonal
   return MWCG_OK;
 }
 
@@ -561,6 +618,20 @@ int mwcg_set_normalization(mwcg_csr* A, int32_t every, uint32_t mask) {
   if (mask & ~(uint32_t)mwk::NORM_ALL) return fail(MWCG_ERR_ARG, "unknown normalisation bits 0x%x", (unsigned)mask);
   A->norm_every = every;
   A->norm_mask = mask;
+  return MWCG_OK;
+}
+
+int mwcg_set_preconditioner(mwcg_csr* A, int kind) {
+  if (!A) return fail(MWCG_ERR_ARG, "null matrix handle");
+  if (kind != MWCG_PREC_NONE && kind != MWCG_PREC_JACOBI) return fail(MWCG_ERR_ARG, "unknown preconditioner %d", kind);
+  if (kind != A->prec) A->w_valid = false;
+  A->prec = kind;
+  return MWCG_OK;
+}
+
+int mwcg_get_preconditioner(const mwcg_csr* A, int* kind) {
+  if (!A || !kind) return fail(MWCG_ERR_ARG, "null argument");
+  *kind = A->prec;
   return MWCG_OK;
 }
 
@@ -628,7 +699,7 @@ int mwcg_adjoint(mwcg_csr* A, const double* x, const double* gx, int arith, doub
   if (!A->lam) CK(cudaMalloc(&A->lam, sizeof(double) * 3 * n));
   CK(cudaMemsetAsync(A->lam, 0, sizeof(double) * 3 * n, s));
   rc = run_solve(A, gx, A->lam, arith, tol, maxit, nullptr, s, iters_out, relres_out);
-  if (rc < 0) return rc;
+  if (rc < 0 || rc == MWCG_BAD_PRECONDITIONER) return rc;
   const mwk::KernelTable* kt = table(arith);
   const mwk::Csr M = csr_view(A);
   const int G = A->plan.G;
@@ -754,10 +825,10 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   void* a_spmv0[] = {(void*)&M, (void*)&W, (void*)&mode0};
   void* a_spmv1[] = {(void*)&M, (void*)&W, (void*)&mode1};
   void* a_mw[] = {(void*)&M, (void*)&W};
-  CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
-  CK(cudaLaunchKernel(kt->init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
-  CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
   const LoopKernels lk = loop_kernels(A, kt);
+  CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
+  CK(cudaLaunchKernel(lk.init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
+  CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
   std::vector<cudaEvent_t> ev(3 * (size_t)niters + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   int err = MWCG_OK;
@@ -811,10 +882,13 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
   std::vector<int> idx;
   std::vector<double> cost;
   for (int s = 0; s < nsys; ++s) {
-    if (A[s]->n == 0) {
+    bool undefined = false;
+    int rc = ensure_weights(A[s], S(stream), &undefined);
+    if (rc != MWCG_OK) return rc;
+    if (A[s]->n == 0 || undefined) {   // nothing to do / preconditioner undefined: x0 untouched
       if (iters_out) iters_out[s] = 0;
       if (relres_out) relres_out[s] = 0.0;
-      if (status_out) status_out[s] = MWCG_OK;
+      if (status_out) status_out[s] = undefined ? MWCG_BAD_PRECONDITIONER : MWCG_OK;
       continue;
     }
     mwb::Sys q{};
@@ -834,6 +908,7 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
     q.V = A[s]->plan.V;
     q.norm_every = A[s]->norm_every;
     q.norm_mask = A[s]->norm_mask;
+    q.w = (A[s]->prec == MWCG_PREC_JACOBI) ? A[s]->w : nullptr;
     double mac, add;
     op_costs(arith[s], mac, add);
     cost.push_back((double)A[s]->nnz * mac + (double)n * 10.0 * add);

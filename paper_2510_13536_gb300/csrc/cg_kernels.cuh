@@ -96,6 +96,7 @@ struct Work {
   int has_cond;
   int V;                    // lanes per row in the SpMV
   int G;                    // blocks
+  const double* w;          // Jacobi weights fl(1/a_ii) (preconditioned CG), else null
 };
 
 template <class A>
@@ -205,6 +206,81 @@ __device__ __forceinline__ bool grid_reduce(const Work& W, const typename A::T& 
   if (threadIdx.x == 0) {
     out = sv[0];
     pout = spf[0] != 0;
+  }
+  return true;
+}
+
+// As grid_reduce, for one multi-word value (partial slots 0-3) and NF = 1 or
+// 2 FP64 values (slot 4 + k, presence in slot 7 - k) under one election.
+// Needs G * (8 W + 8 NF + 1 + NF) <= G * 43 bytes of dynamic shared memory.
+template <class A, int NF>
+__device__ __forceinline__ bool grid_reduce_mix(const Work& W, const typename A::T& v, bool pv, const double* f,
+                                                const bool* pf, typename A::T& out, bool& pout, double* fout,
+                                                bool* pfout) {
+  using T = typename A::T;
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    double* dst = W.part + (size_t)blockIdx.x * 8;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) dst[k] = v.w[k];
+    dst[3] = pv ? 1.0 : 0.0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      dst[4 + k] = f[k];
+      dst[7 - k] = pf[k] ? 1.0 : 0.0;
+    }
+    __threadfence();
+    unsigned tk = atomicAdd(&W.st->counter, 1u);
+    am_last = (tk == (unsigned)(gridDim.x - 1));
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  extern __shared__ double dyn[];
+  const int G = gridDim.x;
+  T* sv = reinterpret_cast<T*>(dyn);
+  double* sf = reinterpret_cast<double*>(sv + G);          // [NF][G]
+  unsigned char* sp = reinterpret_cast<unsigned char*>(sf + NF * G);   // presence [1 + NF][G]
+  for (int bk = threadIdx.x; bk < G; bk += blockDim.x) {
+    const double* src = W.part + (size_t)bk * 8;
+    T tv;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) tv.w[k] = __ldcg(src + k);
+    sv[bk] = tv;
+    sp[bk] = __ldcg(src + 3) != 0.0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      sf[k * G + bk] = __ldcg(src + 4 + k);
+      sp[(1 + k) * G + bk] = __ldcg(src + 7 - k) != 0.0;
+    }
+  }
+  __syncthreads();
+  for (int h = 1; h < G; h <<= 1) {
+    for (int s2 = 2 * h * threadIdx.x; s2 + h < G; s2 += 2 * h * blockDim.x) {
+      T a = sv[s2];
+      bool pa = sp[s2] != 0;
+      combine<A>(a, pa, sv[s2 + h], sp[s2 + h] != 0);
+      sv[s2] = a;
+      sp[s2] = pa;
+#pragma unroll
+      for (int k = 0; k < NF; ++k) {
+        mw::MW<1> c{{sf[k * G + s2]}};
+        bool pc = sp[(1 + k) * G + s2] != 0;
+        combine<mw::FP64>(c, pc, mw::MW<1>{{sf[k * G + s2 + h]}}, sp[(1 + k) * G + s2 + h] != 0);
+        sf[k * G + s2] = c.w[0];
+        sp[(1 + k) * G + s2] = pc;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out = sv[0];
+    pout = sp[0] != 0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      fout[k] = sf[k * G];
+      pfout[k] = sp[(1 + k) * G] != 0;
+    }
   }
   return true;
 }
@@ -391,7 +467,12 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
 // ---------------------------------------------------------------------------
 // r0 = (b,0,..) + (-(A x0)), p0 = r0, rho0 = r0^T r0, ||b||^2 (FP64).
 // ---------------------------------------------------------------------------
-template <class A>
+// Initialisation (Algorithm 1 lines 1-2): r0 = (b, 0, ..) (+) -(A x0) with
+// A x0 in q, p0 = r0, rho0 = r0^T r0, ||b||_2 in FP64; the last block sets
+// the scalars and the stop flags.  PREC (Jacobi-preconditioned CG):
+// z0 = w (x) r0, p0 = z0, rho0 = r0^T z0, and the FP64 residual norm from
+// the collapsed r0 (the stopping residual stays FP64, Sec. IV-C).
+template <class A, bool PREC = false>
 __global__ void __launch_bounds__(TPB) k_init(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
@@ -400,77 +481,51 @@ __global__ void __launch_bounds__(TPB) k_init(Csr M, Work W) {
   const int64_t ntiles = (n + TPB - 1) / TPB;
   T acc = A::zero();
   bool pacc = false;
-  mw::MW<1> bb{{0.0}};
-  bool pbb = false;
+  constexpr int NF = PREC ? 2 : 1;
+  mw::MW<1> fa[NF];                       // [0] b^T b, [1] sum of collapse(r)^2
+  bool pf[NF];
+#pragma unroll
+  for (int k = 0; k < NF; ++k) { fa[k].w[0] = 0.0; pf[k] = false; }
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t i = t * TPB + threadIdx.x;
     if (i < n) {
       double bi = b[i];
       T ri = A::add(A::from(bi), mw::neg<A>(ld<A>(W.q, n, i)));
       st<A>(W.r, n, i, ri);
-      st<A>(W.p, n, i, ri);
-      T leaf = A::mul(ri, ri);
+      T leaf;
+      if constexpr (PREC) {
+        const T zi = A::dxmul(W.w[i], ri);
+        st<A>(W.p, n, i, zi);
+        leaf = A::mul(ri, zi);
+        const double c = A::collapse(ri);
+        mw::MW<1> lc{{mw::dmul(c, c)}};
+        if (pf[1]) fa[1] = mw::FP64::add(fa[1], lc);
+        else { fa[1] = lc; pf[1] = true; }
+      } else {
+        st<A>(W.p, n, i, ri);
+        leaf = A::mul(ri, ri);
+      }
       if (pacc) acc = A::add(acc, leaf);
       else { acc = leaf; pacc = true; }
       mw::MW<1> lb{{mw::dmul(bi, bi)}};
-      if (pbb) bb = mw::FP64::add(bb, lb);
-      else { bb = lb; pbb = true; }
+      if (pf[0]) fa[0] = mw::FP64::add(fa[0], lb);
+      else { fa[0] = lb; pf[0] = true; }
     }
   }
   block_tree<A>(acc, pacc, 1);
-  block_tree<mw::FP64>(bb, pbb, 1);
-  // Two grid reductions share one election: store both, then reduce both.
-  __shared__ bool am_last;
-  if (threadIdx.x == 0) {
-    double* dst = W.part + (size_t)blockIdx.x * 8;
 #pragma unroll
-    for (int k = 0; k < A::W; ++k) dst[k] = acc.w[k];
-    dst[3] = pacc ? 1.0 : 0.0;
-    dst[4] = bb.w[0];
-    dst[7] = pbb ? 1.0 : 0.0;
-    __threadfence();
-    unsigned tk = atomicAdd(&S->counter, 1u);
-    am_last = (tk == (unsigned)(gridDim.x - 1));
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  extern __shared__ double dyn[];
-  const int G = gridDim.x;
-  T* sv = reinterpret_cast<T*>(dyn);
-  double* sb = reinterpret_cast<double*>(sv + G);
-  int* spf = reinterpret_cast<int*>(sb + G);
-  int* spb = spf + G;
-  for (int bk = threadIdx.x; bk < G; bk += blockDim.x) {
-    const double* src = W.part + (size_t)bk * 8;
-    T tv;
+  for (int k = 0; k < NF; ++k) block_tree<mw::FP64>(fa[k], pf[k], 1);
+  double fv[NF], fo[NF];
+  bool pfo[NF];
 #pragma unroll
-    for (int k = 0; k < A::W; ++k) tv.w[k] = __ldcg(src + k);
-    sv[bk] = tv;
-    spf[bk] = __ldcg(src + 3) != 0.0;
-    sb[bk] = __ldcg(src + 4);
-    spb[bk] = __ldcg(src + 7) != 0.0;
-  }
-  __syncthreads();
-  for (int h = 1; h < G; h <<= 1) {
-    for (int s = 2 * h * threadIdx.x; s + h < G; s += 2 * h * blockDim.x) {
-      T a = sv[s];
-      bool pa = spf[s] != 0;
-      combine<A>(a, pa, sv[s + h], spf[s + h] != 0);
-      sv[s] = a;
-      spf[s] = pa;
-      mw::MW<1> c{{sb[s]}};
-      bool pc = spb[s] != 0;
-      combine<mw::FP64>(c, pc, mw::MW<1>{{sb[s + h]}}, spb[s + h] != 0);
-      sb[s] = c.w[0];
-      spb[s] = pc;
-    }
-    __syncthreads();
-  }
+  for (int k = 0; k < NF; ++k) fv[k] = fa[k].w[0];
+  T rho;
+  bool prho = false;
+  if (!grid_reduce_mix<A, NF>(W, acc, pacc, fv, pf, rho, prho, fo, pfo)) return;
   if (threadIdx.x == 0) {
     S->counter = 0;
-    T rho = spf[0] ? sv[0] : A::zero();
-    double bnorm = __dsqrt_rn(spb[0] ? sb[0] : 0.0);
+    if (!prho) rho = A::zero();
+    double bnorm = __dsqrt_rn(pfo[0] ? fo[0] : 0.0);
     S->bnorm = bnorm;
     S->iters = 0;
     S->status = ST_CONVERGED;
@@ -486,7 +541,8 @@ __global__ void __launch_bounds__(TPB) k_init(Csr M, Work W) {
       bool rzero = true;
 #pragma unroll
       for (int k = 0; k < A::W; ++k) rzero = rzero && !mw::nonzero(rho.w[k]);
-      S->relres = __ddiv_rn(__dsqrt_rn(A::collapse(rho)), bnorm);
+      if constexpr (PREC) S->relres = __ddiv_rn(__dsqrt_rn(pfo[NF - 1] ? fo[NF - 1] : 0.0), bnorm);
+      else S->relres = __ddiv_rn(__dsqrt_rn(A::collapse(rho)), bnorm);
       if (rzero) {
         S->relres = 0.0;
         S->done = 1;
@@ -509,10 +565,12 @@ __global__ void __launch_bounds__(TPB) k_zero_x(Csr M, Work W) {
 
 // One row per thread and tile: x += alpha p, r += (-alpha) q (normalised where
 // NX / NR say), and the r^T r leaf added into the thread's slot.
-template <class A, bool NX, bool NR>
+// PREC: also z = w (x) r, stored over q (dead once r is updated), the leaf
+// r_i z_i, and the FP64 leaf collapse(r_i)^2 added into (rr, prr).
+template <class A, bool NX, bool NR, bool PREC>
 __device__ __forceinline__ void update_rows(const Csr& M, const Work& W, double* __restrict__ x,
                                             const typename A::T& al, const typename A::T& mal,
-                                            typename A::T& acc, bool& pacc) {
+                                            typename A::T& acc, bool& pacc, mw::MW<1>& rr, bool& prr) {
   using T = typename A::T;
   const int64_t n = M.n;
   const int64_t ntiles = (n + TPB - 1) / TPB;
@@ -525,7 +583,18 @@ __device__ __forceinline__ void update_rows(const Csr& M, const Work& W, double*
       T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
       if constexpr (NR) A::normalize(ri);
       st<A>(W.r, n, i, ri);
-      T leaf = A::mul(ri, ri);
+      T leaf;
+      if constexpr (PREC) {
+        const T zi = A::dxmul(W.w[i], ri);
+        st<A>(W.q, n, i, zi);
+        leaf = A::mul(ri, zi);
+        const double c = A::collapse(ri);
+        mw::MW<1> lc{{mw::dmul(c, c)}};
+        if (prr) rr = mw::FP64::add(rr, lc);
+        else { rr = lc; prr = true; }
+      } else {
+        leaf = A::mul(ri, ri);
+      }
       if (pacc) acc = A::add(acc, leaf);
       else { acc = leaf; pacc = true; }
     }
@@ -535,8 +604,10 @@ __device__ __forceinline__ void update_rows(const Csr& M, const Work& W, double*
 // ---------------------------------------------------------------------------
 // x += alpha p; r += (-alpha) q; normalise r; rho' = r^T r; stop test; beta.
 // POL as for k_spmv: the default instantiation normalises r every iteration.
+// PREC (Jacobi-preconditioned CG): z = w (x) r into q, rho' = r^T z, and the
+// stopping residual from the FP64 sum of collapse(r_i)^2.
 // ---------------------------------------------------------------------------
-template <class A, bool POL = false>
+template <class A, bool POL = false, bool PREC = false>
 __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
@@ -554,17 +625,19 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   const uint32_t nm = POL ? norm_at(S->norm_every, S->norm_mask, S->iters) : (uint32_t)NORM_R;
   T acc = A::zero();
   bool pacc = false;
+  mw::MW<1> rr{{0.0}};
+  bool prr = false;
   if constexpr (A::ILP == 1) {
     // One loop copy per combination of the x / r normalisations (see
     // row_accumulate); the default instantiation has only {r}.
     if constexpr (!POL) {
-      update_rows<A, false, true>(M, W, x, al, mal, acc, pacc);
+      update_rows<A, false, true, PREC>(M, W, x, al, mal, acc, pacc, rr, prr);
     } else {
       switch (((nm & NORM_X) ? 1 : 0) | ((nm & NORM_R) ? 2 : 0)) {
-        case 0: update_rows<A, false, false>(M, W, x, al, mal, acc, pacc); break;
-        case 1: update_rows<A, true, false>(M, W, x, al, mal, acc, pacc); break;
-        case 2: update_rows<A, false, true>(M, W, x, al, mal, acc, pacc); break;
-        default: update_rows<A, true, true>(M, W, x, al, mal, acc, pacc); break;
+        case 0: update_rows<A, false, false, PREC>(M, W, x, al, mal, acc, pacc, rr, prr); break;
+        case 1: update_rows<A, true, false, PREC>(M, W, x, al, mal, acc, pacc, rr, prr); break;
+        case 2: update_rows<A, false, true, PREC>(M, W, x, al, mal, acc, pacc, rr, prr); break;
+        default: update_rows<A, true, true, PREC>(M, W, x, al, mal, acc, pacc, rr, prr); break;
       }
     }
   } else {
@@ -593,7 +666,12 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
           if (nm & NORM_X) A::normalize(xs[u]);
           rs[u] = A::muladd(rs[u], mal, qs[u]);
           if (nm & NORM_R) A::normalize(rs[u]);
-          leaf[u] = A::mul(rs[u], rs[u]);
+          if constexpr (PREC) {
+            qs[u] = A::dxmul(W.w[idx[u]], rs[u]);       // z, stored over q
+            leaf[u] = A::mul(rs[u], qs[u]);
+          } else {
+            leaf[u] = A::mul(rs[u], rs[u]);
+          }
         }
       }
 #pragma unroll
@@ -601,6 +679,7 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
         if (valid[u]) {
           st<A>(x, n, idx[u], xs[u]);
           st<A>(W.r, n, idx[u], rs[u]);
+          if constexpr (PREC) st<A>(W.q, n, idx[u], qs[u]);
         }
       }
 #pragma unroll
@@ -608,6 +687,12 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
         if (valid[u]) {
           if (pacc) acc = A::add(acc, leaf[u]);
           else { acc = leaf[u]; pacc = true; }
+          if constexpr (PREC) {
+            const double c = A::collapse(rs[u]);
+            mw::MW<1> lc{{mw::dmul(c, c)}};
+            if (prr) rr = mw::FP64::add(rr, lc);
+            else { rr = lc; prr = true; }
+          }
         }
       }
     }
@@ -615,11 +700,21 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   block_tree<A>(acc, pacc, 1);
   T tot;
   bool ptot = false;
-  if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  double rrt = 0.0;
+  if constexpr (PREC) {
+    block_tree<mw::FP64>(rr, prr, 1);
+    double fo[1];
+    bool pfo[1];
+    if (!grid_reduce_mix<A, 1>(W, acc, pacc, &rr.w[0], &prr, tot, ptot, fo, pfo)) return;
+    if (threadIdx.x == 0) rrt = pfo[0] ? fo[0] : 0.0;
+  } else {
+    if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  }
   if (threadIdx.x == 0) {
     S->counter = 0;
     if (!ptot) tot = A::zero();
-    const double relres = __ddiv_rn(__dsqrt_rn(A::collapse(tot)), S->bnorm);
+    const double relres = PREC ? __ddiv_rn(__dsqrt_rn(rrt), S->bnorm)
+                               : __ddiv_rn(__dsqrt_rn(A::collapse(tot)), S->bnorm);
     S->relres = relres;
     const int it = S->iters;
     if (S->hist) S->hist[it - 1] = relres;
@@ -646,8 +741,9 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_update(Csr M, Work W) {
   }
 }
 
-// p = r + beta p (POL: normalise p where the policy says so).
-template <class A, bool POL = false>
+// p = r + beta p (POL: normalise p where the policy says so; PREC: p = z +
+// beta p, z held in q).
+template <class A, bool POL = false, bool PREC = false>
 __global__ void __launch_bounds__(TPB, A::MINB) k_pupdate(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
@@ -657,34 +753,35 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_pupdate(Csr M, Work W) {
 #pragma unroll
   for (int k = 0; k < A::W; ++k) be.w[k] = S->beta[k];
   const int64_t stride = (int64_t)gridDim.x * TPB;
+  const double* __restrict__ src = PREC ? W.q : W.r;
   const bool np_ = POL && (norm_at(S->norm_every, S->norm_mask, S->iters) & NORM_P) != 0;
   if constexpr (A::ILP == 1) {
     if (np_) {                // separate loop copies, as in row_accumulate
       for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride) {
-        T pi = A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i));
+        T pi = A::muladd(ld<A>(src, n, i), be, ld<A>(W.p, n, i));
         A::normalize(pi);
         st<A>(W.p, n, i, pi);
       }
     } else {
       for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride)
-        st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), be, ld<A>(W.p, n, i)));
+        st<A>(W.p, n, i, A::muladd(ld<A>(src, n, i), be, ld<A>(W.p, n, i)));
     }
-    return;
-  }
-  for (int64_t i0 = (int64_t)blockIdx.x * TPB + threadIdx.x; i0 < n; i0 += (int64_t)A::ILP * stride) {
-    T rr[A::ILP], pp[A::ILP];
+  } else {
+    for (int64_t i0 = (int64_t)blockIdx.x * TPB + threadIdx.x; i0 < n; i0 += (int64_t)A::ILP * stride) {
+      T rr[A::ILP], pp[A::ILP];
 #pragma unroll
-    for (int u = 0; u < A::ILP; ++u) {
-      const int64_t i = i0 + u * stride;
-      if (i < n) { rr[u] = ld<A>(W.r, n, i); pp[u] = ld<A>(W.p, n, i); }
-    }
+      for (int u = 0; u < A::ILP; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < n) { rr[u] = ld<A>(src, n, i); pp[u] = ld<A>(W.p, n, i); }
+      }
 #pragma unroll
-    for (int u = 0; u < A::ILP; ++u) {
-      const int64_t i = i0 + u * stride;
-      if (i < n) {
-        T pi = A::muladd(rr[u], be, pp[u]);
-        if (np_) A::normalize(pi);
-        st<A>(W.p, n, i, pi);
+      for (int u = 0; u < A::ILP; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < n) {
+          T pi = A::muladd(rr[u], be, pp[u]);
+          if (np_) A::normalize(pi);
+          st<A>(W.p, n, i, pi);
+        }
       }
     }
   }
@@ -768,6 +865,11 @@ struct KernelTable {
   const void* spmv_pol;     // the three loop kernels under a non-default normalisation policy
   const void* update_pol;
   const void* pupdate_pol;
+  const void* init_pcg;     // Jacobi-preconditioned CG: init, update and p update,
+  const void* update_pcg;   // default policy / any policy
+  const void* pupdate_pcg;
+  const void* update_pcg_pol;
+  const void* pupdate_pcg_pol;
   const void* init;
   const void* zero_x;
   const void* update;
@@ -785,14 +887,21 @@ KernelTable make_table() {
   KernelTable t;
   t.words = A::W;
   t.spmv = (const void*)&k_spmv<AS>;
+  t.init_pcg = (const void*)&k_init<A, true>;
+  t.update_pcg = (const void*)&k_update<A, false, true>;
+  t.pupdate_pcg = (const void*)&k_pupdate<A, false, true>;
   if constexpr (A::NORMALISES) {
     t.spmv_pol = (const void*)&k_spmv<AS, true>;
     t.update_pol = (const void*)&k_update<A, true>;
     t.pupdate_pol = (const void*)&k_pupdate<A, true>;
+    t.update_pcg_pol = (const void*)&k_update<A, true, true>;
+    t.pupdate_pcg_pol = (const void*)&k_pupdate<A, true, true>;
   } else {                  // the policy cannot change these arithmetics' results
     t.spmv_pol = t.spmv;
     t.update_pol = t.update;
     t.pupdate_pol = t.pupdate;
+    t.update_pcg_pol = t.update_pcg;
+    t.pupdate_pcg_pol = t.pupdate_pcg;
   }
   t.init = (const void*)&k_init<A>;
   t.zero_x = (const void*)&k_zero_x<A::W>;

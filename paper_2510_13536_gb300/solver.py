@@ -104,6 +104,19 @@ class CSRMatrix:
             mask = sum(_capi.NORM[k] for k in set(mask))
         check(_capi.load().mwcg_set_normalization(self._h, int(every), int(mask)))
 
+    @property
+    def preconditioner(self) -> str:
+        """"none" (Algorithm 1) or "jacobi" (M^-1 = diag(fl(1/a_ii)), mwcg.h)."""
+        k = ctypes.c_int(0)
+        check(_capi.load().mwcg_get_preconditioner(self._h, ctypes.byref(k)))
+        return {v: n for n, v in _capi.PRECOND.items()}[k.value]
+
+    @preconditioner.setter
+    def preconditioner(self, kind: str):
+        if kind not in _capi.PRECOND:
+            raise ValueError(f"unknown preconditioner {kind!r}")
+        check(_capi.load().mwcg_set_preconditioner(self._h, _capi.PRECOND[kind]))
+
     def update_values(self, val) -> None:
         L = _capi.load()
         if isinstance(val, torch.Tensor) and val.is_cuda:
