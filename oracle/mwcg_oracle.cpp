@@ -228,6 +228,110 @@ struct QTW_NN : QTWbase {
   static void normalize(T&) {}
 };
 
+// ---- QQW, quasi quadruple-word.  The paper lists QQW (Sec. I, after Ozaki
+// and Imamura) but prints no algorithm and the cited work is not available.
+// Reading: the QTW algorithms (7, 8, 9, 10) continued one level down.  At
+// each level the level's own terms are combined by TwoSum / TwoProd and every
+// error of the level above is folded in by TwoSum; the lowest level (order
+// u^3) is summed plainly, left to right, with its products taken by FMA
+// together with the first errors, as QTWmul does at its lowest level.
+// (Parity unpinned against the cited work; accuracy pinned by the tests.)
+struct QQWbase {
+  static constexpr int W = 4;
+  using T = MW<4>;
+  static T zero() { return T{{0.0, 0.0, 0.0, 0.0}}; }
+  static T from(double a) { return T{{a, 0.0, 0.0, 0.0}}; }
+  static T add(const T& a, const T& b) {
+    T c;
+    double e1, e2, e3, e4, e5, e6;
+    two_sum(a.w[0], b.w[0], c.w[0], e1);
+    two_sum(a.w[1], b.w[1], c.w[1], e2);
+    two_sum(c.w[1], e1, c.w[1], e3);
+    two_sum(a.w[2], b.w[2], c.w[2], e4);
+    two_sum(c.w[2], e2, c.w[2], e5);
+    two_sum(c.w[2], e3, c.w[2], e6);
+    c.w[3] = fadd(fadd(fadd(fadd(a.w[3], b.w[3]), e4), e5), e6);
+    return c;
+  }
+  static T mul(const T& a, const T& b) {
+    T c;
+    double e1, t2, e2, t3, e3, e4, e5;
+    two_prod(a.w[0], b.w[0], c.w[0], e1);                       // order 1
+    two_prod(a.w[0], b.w[1], t2, e2);                           // order u
+    two_prod(a.w[1], b.w[0], t3, e3);
+    two_sum(t2, t3, c.w[1], e4);
+    two_sum(c.w[1], e1, c.w[1], e5);
+    double t4, e6, t5, e7, t6, e8, e9, e10, e11, e12, e13, e14;
+    two_prod(a.w[0], b.w[2], t4, e6);                           // order u^2
+    two_prod(a.w[1], b.w[1], t5, e7);
+    two_prod(a.w[2], b.w[0], t6, e8);
+    two_sum(t4, t5, c.w[2], e9);
+    two_sum(c.w[2], t6, c.w[2], e10);
+    two_sum(c.w[2], e2, c.w[2], e11);
+    two_sum(c.w[2], e3, c.w[2], e12);
+    two_sum(c.w[2], e4, c.w[2], e13);
+    two_sum(c.w[2], e5, c.w[2], e14);
+    double f1 = ffma(a.w[3], b.w[0], e6);                      // order u^3
+    double f2 = ffma(a.w[2], b.w[1], e7);
+    double f3 = ffma(a.w[1], b.w[2], e8);
+    double f4 = ffma(a.w[0], b.w[3], e9);
+    double s3 = fadd(fadd(fadd(f1, f2), f3), f4);
+    c.w[3] = fadd(fadd(fadd(fadd(fadd(s3, e10), e11), e12), e13), e14);
+    return c;
+  }
+  // FP64 x QQW, Algorithm 10 continued one level down.
+  static T dxmul(double a, const T& b) {
+    T c;
+    double e1, e2, e3, e4, e5, e6;
+    two_prod(a, b.w[0], c.w[0], e1);
+    two_prod(a, b.w[1], c.w[1], e2);
+    two_sum(c.w[1], e1, c.w[1], e3);
+    two_prod(a, b.w[2], c.w[2], e4);
+    two_sum(c.w[2], e2, c.w[2], e5);
+    two_sum(c.w[2], e3, c.w[2], e6);
+    c.w[3] = fadd(fadd(ffma(a, b.w[3], e4), e5), e6);
+    return c;
+  }
+  static T muladd(const T& acc, const T& a, const T& b) { return add(acc, mul(a, b)); }
+  static T dxmuladd(const T& acc, double a, const T& b) { return add(acc, dxmul(a, b)); }
+  // VecSum4: Algorithm 9 continued, TwoSum(c1,c2), TwoSum(c2,c3), TwoSum(c3,c4).
+  static void renorm(T& a) {
+    two_sum(a.w[0], a.w[1], a.w[0], a.w[1]);
+    two_sum(a.w[1], a.w[2], a.w[1], a.w[2]);
+    two_sum(a.w[2], a.w[3], a.w[2], a.w[3]);
+  }
+  static double collapse(const T& a) { return fadd(a.w[0], fadd(a.w[1], fadd(a.w[2], a.w[3]))); }
+};
+struct QQW : QQWbase {
+  static T div(const T& a, const T& b);
+  static void normalize(T& a) { renorm(a); }
+};
+struct QQW_NN : QQWbase {
+  static T div(const T& a, const T& b) { return QQW::div(a, b); }
+  static void normalize(T&) {}
+};
+
+// ---- QW, quadruple-word.  The paper cites Hida et al. for QW but prints no
+// algorithm.  Reading (parity unpinned against the cited work): every QQW
+// operation followed by the error-free VecSum and the renormalisation with
+// branches used for TW below, to four non-overlapping words -- QW relates to
+// QQW as DW relates to QDW (Sec. III).
+struct QW {
+  static constexpr int W = 4;
+  using T = MW<4>;
+  static T zero() { return QQWbase::zero(); }
+  static T from(double a) { return QQWbase::from(a); }
+  static T fix(T c);
+  static T add(const T& a, const T& b) { return fix(QQWbase::add(a, b)); }
+  static T mul(const T& a, const T& b) { return fix(QQWbase::mul(a, b)); }
+  static T dxmul(double a, const T& b) { return fix(QQWbase::dxmul(a, b)); }
+  static T muladd(const T& acc, const T& a, const T& b) { return add(acc, mul(a, b)); }
+  static T dxmuladd(const T& acc, double a, const T& b) { return add(acc, dxmul(a, b)); }
+  static T div(const T& a, const T& b);
+  static void normalize(T&) {}
+  static double collapse(const T& a) { return QQWbase::collapse(a); }
+};
+
 // ---- TW, triple-word arithmetic.  The paper uses the addition and "fast"
 // multiplication of Fabiano, Muller and Picot (2019) but does not print them
 // (Sec. III, TW paragraph).  What follows is this project's restatement of
@@ -384,6 +488,54 @@ MW<3> TW::div(const MW<3>& a, const MW<3>& b) {
   double z[3] = {q1, q2, q3};
   vecsum(z, 3);
   return renorm3(z, 3);
+}
+
+// QW normalisation: error-free VecSum of the four words, then the TW
+// renormalisation (running QuickTwoSum, a nonzero error closes an output
+// word) continued to four words.
+MW<4> QW::fix(MW<4> c) {
+  double z[4] = {c.w[0], c.w[1], c.w[2], c.w[3]};
+  TW::vecsum(z, 4);
+  double r[4] = {0.0, 0.0, 0.0, 0.0};
+  int j = 0;
+  double eps = z[0];
+  for (int i = 0; i + 1 < 4; ++i) {
+    double hi, lo;
+    quick_two_sum(eps, z[i + 1], hi, lo);
+    r[j] = hi;
+    if (lo != 0.0) {
+      if (j >= 3) return MW<4>{{r[0], r[1], r[2], r[3]}};
+      ++j;
+      eps = lo;
+    } else {
+      eps = hi;
+    }
+  }
+  r[j] = eps;
+  return MW<4>{{r[0], r[1], r[2], r[3]}};
+}
+MW<4> QQW::div(const MW<4>& a, const MW<4>& b) {
+  double q[4];
+  MW<4> r = a;
+  for (int k = 0; k < 4; ++k) {
+    q[k] = fdiv(r.w[0], b.w[0]);
+    if (k < 3) {
+      r = add(r, neg<QQW>(dxmul(q[k], b)));
+      renorm(r);
+    }
+  }
+  MW<4> c{{q[0], q[1], q[2], q[3]}};
+  renorm(c);
+  return c;
+}
+MW<4> QW::div(const MW<4>& a, const MW<4>& b) {
+  double q[4];
+  MW<4> r = a;
+  for (int k = 0; k < 4; ++k) {
+    q[k] = fdiv(r.w[0], b.w[0]);
+    if (k < 3) r = add(r, neg<QW>(dxmul(q[k], b)));
+  }
+  return fix(MW<4>{{q[0], q[1], q[2], q[3]}});
 }
 
 // ---------------------------------------------------------------------------
@@ -752,7 +904,8 @@ void grad_values(int64_t n, const int64_t* rp, const int32_t* col, const double*
       g[k] = -A::collapse(A::mul(load<A>(lam, n, i), load<A>(x, n, col[k])));
 }
 
-// Arithmetic dispatch: 0 FP64, 1 DW, 2 QDW, 3 TW, 4 QTW, 5 QDW-NN, 6 QTW-NN.
+// Arithmetic dispatch: 0 FP64, 1 DW, 2 QDW, 3 TW, 4 QTW, 5 QDW-NN, 6 QTW-NN,
+// 7 QW, 8 QQW, 9 QQW-NN.
 template <template <class> class F, class... Args>
 int dispatch(int arith, Args... args) {
   switch (arith) {
@@ -763,6 +916,9 @@ int dispatch(int arith, Args... args) {
     case 4: return F<QTW>::run(args...);
     case 5: return F<QDW_NN>::run(args...);
     case 6: return F<QTW_NN>::run(args...);
+    case 7: return F<QW>::run(args...);
+    case 8: return F<QQW>::run(args...);
+    case 9: return F<QQW_NN>::run(args...);
   }
   return -1;
 }
@@ -939,8 +1095,8 @@ int orc_grad_values(int arith, int64_t n, const int64_t* rp, const int32_t* col,
   return dispatch<OpGrad>(arith, n, rp, col, lam, x, g);
 }
 int orc_words(int arith) {
-  static const int w[7] = {1, 2, 2, 3, 3, 2, 3};
-  return (arith >= 0 && arith < 7) ? w[arith] : -1;
+  static const int w[10] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4};
+  return (arith >= 0 && arith < 10) ? w[arith] : -1;
 }
 
 }  // extern "C"
