@@ -53,7 +53,7 @@ SPMV_OPS = {  # arith: (per nnz, per row)
 }
 SPMV_OPS["qdw_nn"] = SPMV_OPS["qdw"]
 SPMV_OPS["qtw_nn"] = SPMV_OPS["qtw"]
-WORDS = {"fp64": 1, "dw": 2, "qdw": 2, "qtw": 3, "tw": 3, "qdw_nn": 2, "qtw_nn": 3}
+WORDS = {"fp64": 1, "dw": 2, "qdw": 2, "qtw": 3, "tw": 3, "qdw_nn": 2, "qtw_nn": 3, "qw": 4, "qqw": 4, "qqw_nn": 4}
 
 
 def _dist():
@@ -349,6 +349,24 @@ def run_pcg(torch, mw, P, cpu):
     return out
 
 
+def run_words(torch, mw, P, cpu):
+    """The precision ladder: every arithmetic on the exact-solution Poisson
+    system (128^3, x* = +-1, b = A x* exact), each to a tolerance near its
+    precision; iterations, time and the forward error measured in the words."""
+    A, b, xs = P.exact_solution_system("norm_poisson")
+    M = mw.CSRMatrix.from_csr(A)
+    db = torch.as_tensor(b, device="cuda")
+    out = {"workload": P.NORM_SYSTEMS["norm_poisson"], "plan": list(M.plan), "runs": []}
+    for ar, tol in (("fp64", 1e-14), ("dw", 1e-26), ("qdw", 1e-26), ("tw", 1e-38), ("qtw", 1e-38),
+                    ("qw", 1e-50), ("qqw", 1e-50)):
+        mw.solve(M, db, ar, tol, 2)
+        r, ms = _timed(torch, lambda: mw.solve(M, db, ar, tol, 20000))
+        out["runs"].append({"arith": ar, "tol": tol, "iters": r.iters, "status": r.status, "relres": r.relres,
+                            "time_s": ms / 1e3, "ms_per_iter": ms / max(r.iters, 1),
+                            "forward_error": _forward_error(r.x.cpu().numpy(), xs)})
+    return out
+
+
 def run_c4(torch, mw, P, cpu):
     specs = P.batch_specs(256, P.SEED_BASE + 4)
     systems = [P.build_batch_system(s) for s in specs]
@@ -463,6 +481,8 @@ def run_workloads(args):
             res = run_norm(torch, mw, P, not args.no_cpu)
         elif w == "pcg":
             res = run_pcg(torch, mw, P, not args.no_cpu)
+        elif w == "words":
+            res = run_words(torch, mw, P, not args.no_cpu)
         else:
             raise SystemExit(f"unknown workload {w}")
         res["wall_s"] = time.perf_counter() - t0
@@ -683,7 +703,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mwcg", choices=["mwcg", "reference"])
-    ap.add_argument("--arith", default="qtw", choices=["qtw", "dw", "qdw", "tw", "fp64", "qdw_nn", "qtw_nn"])
+    ap.add_argument("--arith", default="qtw", choices=["qtw", "dw", "qdw", "tw", "fp64", "qdw_nn", "qtw_nn", "qw", "qqw",
+                                                       "qqw_nn"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no DW, profile, e2e or CPU legs); used for ncu captures")
@@ -691,7 +712,7 @@ def main():
     ap.add_argument("--kernels-only", type=int, default=0, metavar="N",
                     help="run N iterations with each kernel launched on its own (mwcg_profile_kernels) and print "
                          "their mean durations; used for ncu captures")
-    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm", "pcg"],
+    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm", "pcg", "words"],
                     help="measure another configuration instead of the headline (one JSON line each)")
     ap.add_argument("--fd", type=int, default=32, help="finite-difference entries checked in c5")
     ap.add_argument("--plan", default=None, help="override the summation plan V,T,G (ncu / tuning runs)")

@@ -37,7 +37,11 @@ extern "C" {
 #endif
 
 /* Arithmetics (Sec. III).  *_NN: quasi arithmetic without the per-iteration
- * normalisation of r (Sec. V-B3, "CG-QDW-NN", "CG-QTW-NN"). */
+ * normalisation of r (Sec. V-B3, "CG-QDW-NN", "CG-QTW-NN").  QW and QQW
+ * (four words, about 212 bits) are listed in Sec. I without algorithms; here
+ * QQW continues QTW's Algorithms 7-10 one level down (VecSum4 normalises it)
+ * and QW is every QQW operation followed by a renormalisation to four
+ * non-overlapping words. */
 typedef enum {
   MWCG_FP64 = 0,
   MWCG_DW = 1,
@@ -45,7 +49,10 @@ typedef enum {
   MWCG_TW = 3,
   MWCG_QTW = 4,
   MWCG_QDW_NN = 5,
-  MWCG_QTW_NN = 6
+  MWCG_QTW_NN = 6,
+  MWCG_QW = 7,
+  MWCG_QQW = 8,
+  MWCG_QQW_NN = 9
 } mwcg_arith;
 
 /* Solver status (>= 0) and error codes (< 0). */
@@ -80,7 +87,7 @@ typedef struct {
 
 typedef struct mwcg_csr mwcg_csr;
 
-/* Number of FP64 words of an arithmetic (1, 2 or 3), or -1 if unknown. */
+/* Number of FP64 words of an arithmetic (1 to 4), or -1 if unknown. */
 int mwcg_words(int arith);
 
 /* Message of the last error on this thread ("" if none).  Owned by the
@@ -238,8 +245,8 @@ int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, 
  * latency-critical pipeline; code that runs under a fixed device-memory
  * budget or a pooled allocator may also be forbidden hidden allocations.
  * Here the block partials and the ticket counter live in a fixed array
- * compiled into the library (MWCG_DOT_NOALLOC_MAX_G blocks of 8 doubles plus
- * one counter block, about 66 KB, held by every GPU that loads the library
+ * compiled into the library (MWCG_DOT_NOALLOC_MAX_G blocks of 12 doubles plus
+ * one counter block, about 99 KB, held by every GPU that loads the library
  * until the process exits).  The function calls no cudaMalloc, cudaFree or
  * allocating library routine.
  *   arith, n, u, v, G  as in mwcg_dot (u, v device double[w*n]); G in

@@ -13,9 +13,15 @@ namespace mwb {
 
 constexpr int kCluster = 8;                 // CTAs per worker cluster (portable maximum)
 
-// Defined in batched_pcg.cu (run_group<true>).
-cudaError_t run_group_pcg(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int cluster, size_t pad,
-                          int* nclusters);
+// Defined in batched_k<PREC><GRP>.cu: run_group<PREC, GRP>, one kernel each.
+using RunGroup = cudaError_t (*)(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
+cudaError_t run_group_00(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
+cudaError_t run_group_01(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
+cudaError_t run_group_02(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
+cudaError_t run_group_10(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
+cudaError_t run_group_11(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
+cudaError_t run_group_12(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
+const void* kernel_00();
 
 }  // namespace mwb
 
@@ -36,9 +42,9 @@ int small_cluster_size() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return mwb::kCluster;
   if (g_small_cluster[dev]) return g_small_cluster[dev];
   int best = mwb::kCluster;
-  if (cudaFuncSetAttribute(mwb::k_batched<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-      cudaFuncSetAttribute(mwb::k_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mwb::kPadSmem) ==
-          cudaSuccess) {
+  const void* kern = mwb::kernel_00();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mwb::kPadSmem) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -51,7 +57,7 @@ int small_cluster_size() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, mwb::k_batched<false>, &cfg) == cudaSuccess && n >= 1) best = 16;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) best = 16;
   }
   cudaGetLastError();
   g_small_cluster[dev] = best;
@@ -59,43 +65,45 @@ int small_cluster_size() {
 }
 
 // Launch the persistent kernel over `nsys` prepared systems (host array, in
-// queue order) with clusters of `cluster` CTAs.  Systems without and with a
-// Jacobi preconditioner run as two consecutive launches (one kernel
-// instantiation each), each in queue order.  Returns a cudaError_t; outputs
-// are copied back into hsys.
+// queue order) with clusters of `cluster` CTAs.  Systems are grouped by
+// (preconditioned or not, word group); the groups run as consecutive
+// launches, one kernel instantiation each, every group in queue order.  A
+// system's result depends only on its own plan, not on the grouping.
+// Returns a cudaError_t; outputs are copied back into hsys.
 cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* clusters_out) {
   // MWCG_BATCH_PAD=0 drops the shared-memory pad that keeps one CTA per SM
   // (clusters may then share SMs); for tuning runs.
   const char* pad_env = std::getenv("MWCG_BATCH_PAD");
   const size_t pad = (pad_env && pad_env[0] == '0') ? 0 : mwb::kPadSmem;
-  std::vector<mwb::Sys> grp[2];
-  std::vector<int> where[2];
+  constexpr int NG = 6;
+  static const mwb::RunGroup run[NG] = {mwb::run_group_00, mwb::run_group_01, mwb::run_group_02,
+                                        mwb::run_group_10, mwb::run_group_11, mwb::run_group_12};
+  std::vector<mwb::Sys> grp[NG];
+  std::vector<int> where[NG];
   for (int i = 0; i < nsys; ++i) {
-    const int g = hsys[i].w ? 1 : 0;
+    const int g = (hsys[i].w ? 3 : 0) + mwb::word_group(hsys[i].arith);
     grp[g].push_back(hsys[i]);
     where[g].push_back(i);
   }
   mwb::Sys* dsys = nullptr;
   unsigned* queue = nullptr;
   cudaError_t e = cudaMalloc(&dsys, sizeof(mwb::Sys) * nsys);
-  if (e == cudaSuccess) e = cudaMalloc(&queue, 2 * sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMalloc(&queue, NG * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, NG * sizeof(unsigned), s);
   int nclusters = 0, off = 0;
-  for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
+  for (int g = 0; g < NG && e == cudaSuccess; ++g) {
     const int n = (int)grp[g].size();
     if (n == 0) continue;
     e = cudaMemcpyAsync(dsys + off, grp[g].data(), sizeof(mwb::Sys) * n, cudaMemcpyHostToDevice, s);
     int nc = 0;
-    if (e == cudaSuccess)
-      e = g ? mwb::run_group_pcg(dsys + off, n, queue + g, s, cluster, pad, &nc)
-            : mwb::run_group<false>(dsys + off, n, queue + g, s, cluster, pad, &nc);
+    if (e == cudaSuccess) e = run[g](dsys + off, n, queue + g, s, cluster, pad, &nc);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grp[g].data(), dsys + off, sizeof(mwb::Sys) * n, cudaMemcpyDeviceToHost, s);
     nclusters = std::max(nclusters, nc);
     off += n;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess)
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < NG; ++g)
       for (size_t k = 0; k < grp[g].size(); ++k) hsys[where[g][k]] = grp[g][k];
   cudaFree(dsys);
   cudaFree(queue);

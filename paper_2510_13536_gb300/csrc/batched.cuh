@@ -53,10 +53,11 @@ struct ClusterCtx {
   int C;
 };
 
-// Partial slots in shared memory: [2 buffers][8 doubles] (3 words, presence,
-// FP64 value 1, FP64 value 2, presence 2, presence 1).
+// Partial slots in shared memory: [2 buffers][mwk::PART doubles] in the
+// layout of the grid reductions (words, presence, two FP64 values and their
+// presences).
 struct Slots {
-  double v[2][8];
+  double v[2][mwk::PART];
 };
 
 // Reduce per-CTA values across the cluster: every CTA returns the same result.
@@ -73,11 +74,11 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < A::W; ++k) slots->v[buf][k] = v.w[k];
-    slots->v[buf][3] = pv ? 1.0 : 0.0;
-    slots->v[buf][4] = fv;
-    slots->v[buf][7] = pf ? 1.0 : 0.0;
-    slots->v[buf][5] = fv2;
-    slots->v[buf][6] = pf2 ? 1.0 : 0.0;
+    slots->v[buf][mwk::PRES] = pv ? 1.0 : 0.0;
+    slots->v[buf][mwk::FV] = fv;
+    slots->v[buf][mwk::FP] = pf ? 1.0 : 0.0;
+    slots->v[buf][mwk::FV + 1] = fv2;
+    slots->v[buf][mwk::FP + 1] = pf2 ? 1.0 : 0.0;
   }
   cc.cl.sync();
   __shared__ T sv[32];
@@ -93,11 +94,11 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
 #pragma unroll
     for (int k = 0; k < A::W; ++k) t.w[k] = rs->v[buf][k];
     sv[threadIdx.x] = t;
-    sp[threadIdx.x] = rs->v[buf][3] != 0.0;
-    sf[threadIdx.x] = rs->v[buf][4];
-    spf[threadIdx.x] = rs->v[buf][7] != 0.0;
-    sf2[threadIdx.x] = rs->v[buf][5];
-    spf2[threadIdx.x] = rs->v[buf][6] != 0.0;
+    sp[threadIdx.x] = rs->v[buf][mwk::PRES] != 0.0;
+    sf[threadIdx.x] = rs->v[buf][mwk::FV];
+    spf[threadIdx.x] = rs->v[buf][mwk::FP] != 0.0;
+    sf2[threadIdx.x] = rs->v[buf][mwk::FV + 1];
+    spf2[threadIdx.x] = rs->v[buf][mwk::FP + 1] != 0.0;
   }
   __syncthreads();
   __shared__ T res;
@@ -249,7 +250,10 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   // Scalar steps run on one thread per CTA (the FP64 pipe is shared by the
   // whole SM) and are broadcast through shared memory.  Every CTA's thread 0
   // computes them from the same inputs, so all CTAs agree.
-  __shared__ double s_sc[8];
+  // Broadcast scalars: [0] ||b|| then the relative residual, alpha at
+  // [SA, SA + W), beta at [SB, SB + W), the iteration's residual at SR.
+  constexpr int SA = 1, SB = SA + 4, SR = SB + 4;
+  __shared__ double s_sc[SR + 1];
   __shared__ int s_flag[2];
   if (threadIdx.x == 0) {
     if (!prho) rho = A::zero();
@@ -269,14 +273,14 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
       else if (S.maxit <= 0) { st0 = mwk::ST_MAXIT; fl = 2; }
     }
     s_sc[0] = bnorm0;
-    s_sc[1] = rr0;
+    s_sc[SR] = rr0;
     s_flag[0] = fl;
     s_flag[1] = st0;
   }
   __syncthreads();
   const double bnorm = s_sc[0];
   int iters = 0, status = s_flag[1];
-  double relres = s_sc[1];
+  double relres = s_sc[SR];
   bool done = s_flag[0] != 0;
   if (s_flag[0] == 1) {
     for (int64_t i = (int64_t)rank * TPB + threadIdx.x; i < (int64_t)A::W * n; i += (int64_t)C * TPB) S.x[i] = 0.0;
@@ -304,14 +308,14 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
       if (!brk) {
         const T a1 = A::div(rho, pq);
 #pragma unroll
-        for (int k = 0; k < A::W; ++k) s_sc[k] = a1.w[k];
+        for (int k = 0; k < A::W; ++k) s_sc[SA + k] = a1.w[k];
       }
     }
     __syncthreads();
     if (s_flag[0]) { status = mwk::ST_BREAKDOWN; break; }
     T al;
 #pragma unroll
-    for (int k = 0; k < A::W; ++k) al.w[k] = s_sc[k];
+    for (int k = 0; k < A::W; ++k) al.w[k] = s_sc[SA + k];
     const T mal = mw::neg<A>(al);
     acc = A::zero();
     pacc = false;
@@ -361,19 +365,19 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
       else {
         const T be = A::div(rho1, rho);
 #pragma unroll
-        for (int k = 0; k < A::W; ++k) s_sc[3 + k] = be.w[k];
+        for (int k = 0; k < A::W; ++k) s_sc[SB + k] = be.w[k];
       }
-      s_sc[6] = rr;
+      s_sc[SR] = rr;
       s_flag[0] = fl;
     }
     __syncthreads();
-    relres = s_sc[6];
+    relres = s_sc[SR];
     if (s_flag[0] == 1) { status = mwk::ST_CONVERGED; break; }
     if (s_flag[0] == 2) { status = mwk::ST_BREAKDOWN; break; }
     if (s_flag[0] == 3) { status = mwk::ST_MAXIT; break; }
     T be;
 #pragma unroll
-    for (int k = 0; k < A::W; ++k) be.w[k] = s_sc[3 + k];
+    for (int k = 0; k < A::W; ++k) be.w[k] = s_sc[SB + k];
     if (!prr) rho1 = A::zero();
     rho = rho1;
     // p = r + beta p (PREC: z + beta p) on this CTA's rows (the update tiles).
@@ -395,24 +399,21 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   cc.cl.sync();                       // x, outputs complete; slots free for the next system
 }
 
-template <bool PREC>
-__device__ __forceinline__ void solve_any(const ClusterCtx& cc, Slots* slots, Sys& S) {
-  switch (S.arith) {
-    case 0: solve_cluster<mw::FP64, PREC>(cc, slots, S); break;
-    case 1: solve_cluster<mw::DW, PREC>(cc, slots, S); break;
-    case 2: solve_cluster<mw::QDW, PREC>(cc, slots, S); break;
-    case 3: solve_cluster<mw::TW, PREC>(cc, slots, S); break;
-    case 4: solve_cluster<mw::QTW, PREC>(cc, slots, S); break;
-    case 5: solve_cluster<mw::QDW_NN, PREC>(cc, slots, S); break;
-    default: solve_cluster<mw::QTW_NN, PREC>(cc, slots, S); break;
-  }
+// Word groups of the persistent kernel: GRP 0 = FP64, DW, QDW, QDW-NN;
+// GRP 1 = TW, QTW, QTW-NN; GRP 2 = QW, QQW, QQW-NN (the last needs the
+// four-word arithmetics of mw_device4.cuh, included by its translation units).
+inline int word_group(int arith) {
+  return (arith == 3 || arith == 4 || arith == 6) ? 1 : (arith >= 7) ? 2 : 0;
 }
 
+template <bool PREC, int GRP>
+__device__ __forceinline__ void solve_any(const ClusterCtx& cc, Slots* slots, Sys& S);
+
 // The persistent kernel: clusters take systems from the queue until it is
-// empty.  One instantiation per PREC (each compiled in its own translation
-// unit, batched.cu and batched_pcg.cu: a kernel holding every arithmetic's
-// solver is large).
-template <bool PREC>
+// empty.  One instantiation per (PREC, word group), each compiled in its own
+// translation unit (batched_k*.cu): a kernel holding every arithmetic's
+// solver takes minutes to compile.
+template <bool PREC, int GRP>
 __global__ void __launch_bounds__(TPB, 1) k_batched(Sys* __restrict__ sys, int nsys, unsigned* queue) {
   __shared__ Slots slots;
   __shared__ int s_next;
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(TPB, 1) k_batched(Sys* __restrict__ sys, int n
     const int sid = *cl.map_shared_rank(&s_next, 0);
     cl.sync();                               // every CTA has read s_next before it is overwritten
     if (sid >= nsys) break;
-    solve_any<PREC>(cc, &slots, sys[sid]);     // the host groups systems by PREC
+    solve_any<PREC, GRP>(cc, &slots, sys[sid]);     // the host groups systems by (PREC, GRP)
   }
 }
 
@@ -433,11 +434,11 @@ constexpr size_t kPadSmem = 120 * 1024;     // dynamic shared memory that keeps 
 // Host: run k_batched<PREC> over n systems already on the device (queue
 // zeroed), clusters of `cluster` CTAs, as many clusters as fit at once (at
 // most n).  The translation unit that calls it holds that instantiation.
-template <bool PREC>
+template <bool PREC, int GRP>
 cudaError_t run_group(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int cluster, size_t pad, int* nclusters) {
-  cudaError_t e = cudaFuncSetAttribute(k_batched<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPadSmem);
-  if (e == cudaSuccess && cluster > 8)
-    e = cudaFuncSetAttribute(k_batched<PREC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const void* kern = (const void*)&k_batched<PREC, GRP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPadSmem);
+  if (e == cudaSuccess && cluster > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -452,12 +453,12 @@ cudaError_t run_group(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int clu
   int nc = 0;
   if (e == cudaSuccess) {
     cfg.gridDim = dim3(cluster);
-    e = cudaOccupancyMaxActiveClusters(&nc, k_batched<PREC>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&nc, kern, &cfg);
   }
   if (e == cudaSuccess) {
     nc = nc < 1 ? 1 : (nc < n ? nc : n);
     cfg.gridDim = dim3(nc * cluster);
-    e = cudaLaunchKernelEx(&cfg, k_batched<PREC>, dsys, n, queue);
+    e = cudaLaunchKernelEx(&cfg, k_batched<PREC, GRP>, dsys, n, queue);
   }
   if (nclusters) *nclusters = nc;
   return e;

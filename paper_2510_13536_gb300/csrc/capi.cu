@@ -42,6 +42,9 @@ KernelTable table_qdw_nn();
 KernelTable table_tw();
 KernelTable table_qtw();
 KernelTable table_qtw_nn();
+KernelTable table_qw();
+KernelTable table_qqw();
+KernelTable table_qqw_nn();
 }  // namespace mwk
 
 namespace {
@@ -66,8 +69,19 @@ int fail(int code, const char* fmt, ...) {
                   cudaGetErrorString(e_));                                                        \
   } while (0)
 
+constexpr int kNArith = 10;   // MWCG_FP64 .. MWCG_QQW_NN
+constexpr int kMaxG = 1024;
+
+// Dynamic shared memory of the last-block reductions: G slots of up to w
+// words + 2 FP64 + 3 one-byte flags (8 w + 19 bytes, rounded up: 44 KB at
+// G = 1024 for w = 3, 52 KB for w = 4, which is above the 48 KB available
+// without opting in, so every reduction kernel opts in once, to the largest
+// size: the attribute is a cap, and a lower one would refuse launches that
+// need the default 48 KB).
+size_t red_smem(int G, int w) { return (size_t)G * (8 * w + 20); }
+
 const mwk::KernelTable* table(int arith) {
-  static mwk::KernelTable t[7];
+  static mwk::KernelTable t[kNArith];
   static std::once_flag once;
   std::call_once(once, [] {
     t[0] = mwk::table_fp64();
@@ -77,18 +91,22 @@ const mwk::KernelTable* table(int arith) {
     t[4] = mwk::table_qtw();
     t[5] = mwk::table_qdw_nn();
     t[6] = mwk::table_qtw_nn();
+    t[7] = mwk::table_qw();
+    t[8] = mwk::table_qqw();
+    t[9] = mwk::table_qqw_nn();
+    for (auto& k : t)
+      for (const void* f : {k.spmv, k.spmv_pol, k.init, k.init_pcg, k.update, k.update_pol, k.update_pcg,
+                            k.update_pcg_pol, k.dot})
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
+    cudaGetLastError();
   });
-  if (arith < 0 || arith > 6) return nullptr;
+  if (arith < 0 || arith >= kNArith) return nullptr;
   return &t[arith];
 }
 
-constexpr int kMaxG = 1024;
 constexpr int32_t kMaxIt = 1 << 30;
 
-// Dynamic shared memory of the last-block reductions: G slots of up to
-// 3 words + 2 FP64 + 3 one-byte flags (43 bytes, 44 KB at G = 1024, within
-// the 48 KB available without opting in).
-size_t red_smem(int G) { return (size_t)G * 44; }
+
 
 struct GraphCache {
   cudaGraph_t graph = nullptr;
@@ -129,7 +147,7 @@ struct mwcg_csr {
   double* lam = nullptr;       // adjoint solution, lazily allocated
   double* hb = nullptr;        // staging for host-buffer solves, lazily allocated
   double* hx = nullptr;
-  GraphCache graphs[7];
+  GraphCache graphs[kNArith];
   std::vector<int64_t> rowlen;  // host copy of row lengths (plan selection)
   int32_t norm_every = 1;       // normalisation policy of the quasi arithmetics
   uint32_t norm_mask = mwk::NORM_R;
@@ -158,6 +176,8 @@ void op_costs(int arith, double& mac, double& add) {
     case MWCG_DW: mac = 17; add = 11; break;
     case MWCG_QDW: case MWCG_QDW_NN: mac = 11; add = 8; break;
     case MWCG_TW: mac = 80; add = 45; break;
+    case MWCG_QW: mac = 110; add = 60; break;
+    case MWCG_QQW: case MWCG_QQW_NN: mac = 70; add = 40; break;
     default: mac = 33; add = 21; break;
   }
 }
@@ -239,8 +259,8 @@ mwk::Work work_view(const mwcg_csr* A, unsigned long long cond, int has_cond) {
   const int64_t n = A->n;
   mwk::Work W;
   W.r = A->ws;
-  W.p = A->ws + 3 * n;
-  W.q = A->ws + 6 * n;
+  W.p = A->ws + 4 * n;
+  W.q = A->ws + 8 * n;
   W.part = A->part;
   W.st = A->st;
   W.cond = cond;
@@ -289,7 +309,7 @@ int ensure_graph(mwcg_csr* A, int arith) {
   gc = GraphCache{};
   const mwk::KernelTable* kt = table(arith);
   const int G = A->plan.G;
-  const size_t smem = red_smem(G);
+  const size_t smem = red_smem(G, kt->words);
   cudaGraph_t g;
   CK(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle h;
@@ -341,7 +361,7 @@ int ensure_graph(mwcg_csr* A, int arith) {
 
 int ensure_ws(mwcg_csr* A) {
   if (A->ws || A->n == 0) return MWCG_OK;
-  CK(cudaMalloc(&A->ws, sizeof(double) * 9 * (size_t)A->n));
+  CK(cudaMalloc(&A->ws, sizeof(double) * 12 * (size_t)A->n));   // r, p, q: up to four words each
   return MWCG_OK;
 }
 
@@ -380,7 +400,7 @@ int run_eager(mwcg_csr* A, int arith, cudaStream_t s) {
   mwk::Csr M = csr_view(A);
   mwk::Work W = work_view(A, 0, 0);
   const int G = A->plan.G;
-  const size_t smem = red_smem(G);
+  const size_t smem = red_smem(G, kt->words);
   int mode0 = 0, mode1 = 1;
   void* a_spmv0[] = {(void*)&M, (void*)&W, (void*)&mode0};
   void* a_spmv1[] = {(void*)&M, (void*)&W, (void*)&mode1};
@@ -420,8 +440,8 @@ int run_cluster(mwcg_csr* A, const double* b, double* x, int arith, double tol, 
   q.b = b;
   q.x = x;
   q.r = A->ws;
-  q.p = A->ws + 3 * n;
-  q.q = A->ws + 6 * n;
+  q.p = A->ws + 4 * n;
+  q.q = A->ws + 8 * n;
   q.tol = tol;
   q.maxit = maxit;
   q.arith = arith;
@@ -491,8 +511,8 @@ int check_solve_args(const mwcg_csr* A, const void* b, const void* x, int arith,
 extern "C" {
 
 int mwcg_words(int arith) {
-  static const int w[7] = {1, 2, 2, 3, 3, 2, 3};
-  return (arith >= 0 && arith < 7) ? w[arith] : -1;
+  static const int w[kNArith] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4};
+  return (arith >= 0 && arith < kNArith) ? w[arith] : -1;
 }
 
 const char* mwcg_last_error(void) { return g_err.c_str(); }
@@ -541,7 +561,7 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
   if ((e = cudaMalloc(&A->rp, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
       (nnz && (e = cudaMalloc(&A->col, sizeof(int32_t) * nnz)) != cudaSuccess) ||
       (nnz && (e = cudaMalloc(&A->val, sizeof(double) * nnz)) != cudaSuccess) ||
-      (e = cudaMalloc(&A->part, sizeof(double) * 8 * kMaxG)) != cudaSuccess ||
+      (e = cudaMalloc(&A->part, sizeof(double) * mwk::PART * kMaxG)) != cudaSuccess ||
       (e = cudaMalloc(&A->st, sizeof(mwk::DevState))) != cudaSuccess ||
       (e = cudaMallocHost(&A->h_st, sizeof(mwk::DevState))) != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? MWCG_ERR_NOMEM : MWCG_ERR_CUDA, "allocation: %s",
@@ -673,7 +693,7 @@ int mwcg_solve_host(mwcg_csr* A, const double* b_host, double* x_host, int arith
   const size_t n = (size_t)A->n;
   const int w = mwcg_words(arith);
   if (!A->hb) CK(cudaMalloc(&A->hb, sizeof(double) * n));
-  if (!A->hx) CK(cudaMalloc(&A->hx, sizeof(double) * 3 * n));
+  if (!A->hx) CK(cudaMalloc(&A->hx, sizeof(double) * 4 * n));
   cudaStream_t s = S(stream);
   CK(cudaMemcpyAsync(A->hb, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(A->hx, x_host, sizeof(double) * w * n, cudaMemcpyHostToDevice, s));
@@ -696,8 +716,8 @@ int mwcg_adjoint(mwcg_csr* A, const double* x, const double* gx, int arith, doub
   }
   cudaStream_t s = S(stream);
   const size_t n = (size_t)A->n;
-  if (!A->lam) CK(cudaMalloc(&A->lam, sizeof(double) * 3 * n));
-  CK(cudaMemsetAsync(A->lam, 0, sizeof(double) * 3 * n, s));
+  if (!A->lam) CK(cudaMalloc(&A->lam, sizeof(double) * 4 * n));
+  CK(cudaMemsetAsync(A->lam, 0, sizeof(double) * 4 * n, s));
   rc = run_solve(A, gx, A->lam, arith, tol, maxit, nullptr, s, iters_out, relres_out);
   if (rc < 0 || rc == MWCG_BAD_PRECONDITIONER) return rc;
   const mwk::KernelTable* kt = table(arith);
@@ -733,7 +753,8 @@ int mwcg_spmv(mwcg_csr* A, int arith, const double* p, double* q, void* stream) 
   W.q = q;
   int mode = 0;
   void* args[] = {(void*)&M, (void*)&W, (void*)&mode};
-  CK(cudaLaunchKernel(table(arith)->spmv, dim3(A->plan.G), dim3(mwk::TPB), args, red_smem(A->plan.G), s));
+  CK(cudaLaunchKernel(table(arith)->spmv, dim3(A->plan.G), dim3(mwk::TPB), args,
+                      red_smem(A->plan.G, table(arith)->words), s));
   CK(cudaStreamSynchronize(s));
   return MWCG_OK;
 }
@@ -751,7 +772,7 @@ int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, 
   double* part = nullptr;
   mwk::DevState* st = nullptr;
   double* dout = nullptr;
-  cudaError_t e = cudaMalloc(&part, sizeof(double) * 8 * G);
+  cudaError_t e = cudaMalloc(&part, sizeof(double) * mwk::PART * G);
   if (e == cudaSuccess) e = cudaMalloc(&st, sizeof(mwk::DevState));
   if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double) * 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(mwk::DevState), s);
@@ -762,7 +783,7 @@ int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, 
     W.V = 1;
     W.G = G;
     void* args[] = {(void*)&u, (void*)&v, (void*)&n, (void*)&W, (void*)&dout};
-    e = cudaLaunchKernel(table(arith)->dot, dim3(G), dim3(mwk::TPB), args, red_smem(G), s);
+    e = cudaLaunchKernel(table(arith)->dot, dim3(G), dim3(mwk::TPB), args, red_smem(G, table(arith)->words), s);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(double) * w, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -788,10 +809,10 @@ int mwcg_word_op(int op, int arith, int64_t n, const double* a, const double* b,
 
 int mwcg_collapse(const double* xw, int32_t w, int64_t n, double* x64, void* stream) {
   g_err.clear();
-  if (w < 1 || w > 3 || n < 0) return fail(MWCG_ERR_ARG, "bad argument");
+  if (w < 1 || w > 4 || n < 0) return fail(MWCG_ERR_ARG, "bad argument");
   if (n == 0) return MWCG_OK;
   if (!xw || !x64) return fail(MWCG_ERR_ARG, "null pointer");
-  const int arith = (w == 1) ? MWCG_FP64 : (w == 2) ? MWCG_DW : MWCG_QTW;
+  const int arith = (w == 1) ? MWCG_FP64 : (w == 2) ? MWCG_DW : (w == 3) ? MWCG_QTW : MWCG_QQW;
   const int grid = (int)std::min<int64_t>((n + mwk::TPB - 1) / mwk::TPB, 4096);
   void* args[] = {(void*)&xw, (void*)&n, (void*)&x64};
   CK(cudaLaunchKernel(table(arith)->collapse, dim3(grid), dim3(mwk::TPB), args, 0, S(stream)));
@@ -820,7 +841,7 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   mwk::Csr M = csr_view(A);
   mwk::Work W = work_view(A, 0, 0);
   const int G = A->plan.G;
-  const size_t smem = red_smem(G);
+  const size_t smem = red_smem(G, kt->words);
   int mode0 = 0, mode1 = 1;
   void* a_spmv0[] = {(void*)&M, (void*)&W, (void*)&mode0};
   void* a_spmv1[] = {(void*)&M, (void*)&W, (void*)&mode1};
@@ -900,8 +921,8 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
     q.b = b[s];
     q.x = x[s];
     q.r = A[s]->ws;
-    q.p = A[s]->ws + 3 * n;
-    q.q = A[s]->ws + 6 * n;
+    q.p = A[s]->ws + 4 * n;
+    q.q = A[s]->ws + 8 * n;
     q.tol = tol[s];
     q.maxit = maxit[s];
     q.arith = arith[s];

@@ -32,6 +32,10 @@
 namespace mwk {
 
 constexpr int TPB = 256;                  // threads per block of every kernel
+// Block partials of the grid reductions: PART doubles per block -- the
+// multi-word value in [0, W), its presence at PRES, FP64 value k at FV + k
+// with its presence at FP + k.
+constexpr int PART = 12, PRES = 4, FV = 5, FP = 7;
 // Tiles interleaved per thread (A::ILP; never changes the summation order).
 // Measured on GB300: the multi-word kernels are fastest with 1; FP64, which is
 // memory bound, needs several rows' loads in flight per thread.
@@ -48,9 +52,9 @@ struct DevState {
   double tol;
   int32_t maxit;
   int32_t pad0;
-  double rho[3];
-  double alpha[3];
-  double beta[3];
+  double rho[4];             // multi-word scalars, up to four words
+  double alpha[4];
+  double beta[4];
   double bnorm;
   double relres;
   int32_t iters;
@@ -168,10 +172,10 @@ __device__ __forceinline__ bool grid_reduce(const Work& W, const typename A::T& 
                                             bool& pout) {
   __shared__ bool am_last;
   if (threadIdx.x == 0) {
-    double* dst = W.part + (size_t)blockIdx.x * 8 + OFF;
+    double* dst = W.part + (size_t)blockIdx.x * PART + OFF;
 #pragma unroll
     for (int k = 0; k < A::W; ++k) dst[k] = v.w[k];
-    dst[3] = pv ? 1.0 : 0.0;
+    dst[PRES] = pv ? 1.0 : 0.0;
     __threadfence();
     unsigned t = atomicAdd(&W.st->counter, 1u);
     am_last = (t == (unsigned)(gridDim.x - 1));
@@ -185,12 +189,12 @@ __device__ __forceinline__ bool grid_reduce(const Work& W, const typename A::T& 
   int* spf = reinterpret_cast<int*>(sv + gridDim.x);
   const int G = gridDim.x;
   for (int b = threadIdx.x; b < G; b += blockDim.x) {
-    const double* src = W.part + (size_t)b * 8 + OFF;
+    const double* src = W.part + (size_t)b * PART + OFF;
     typename A::T t;
 #pragma unroll
     for (int k = 0; k < A::W; ++k) t.w[k] = __ldcg(src + k);
     sv[b] = t;
-    spf[b] = __ldcg(src + 3) != 0.0 ? 1 : 0;
+    spf[b] = __ldcg(src + PRES) != 0.0 ? 1 : 0;
   }
   __syncthreads();
   for (int h = 1; h < G; h <<= 1) {
@@ -210,9 +214,9 @@ __device__ __forceinline__ bool grid_reduce(const Work& W, const typename A::T& 
   return true;
 }
 
-// As grid_reduce, for one multi-word value (partial slots 0-3) and NF = 1 or
-// 2 FP64 values (slot 4 + k, presence in slot 7 - k) under one election.
-// Needs G * (8 W + 8 NF + 1 + NF) <= G * 43 bytes of dynamic shared memory.
+// As grid_reduce, for one multi-word value and NF = 1 or 2 FP64 values under
+// one election.  Needs G * (8 W + 8 NF + 1 + NF) <= G * 51 bytes of dynamic
+// shared memory.
 template <class A, int NF>
 __device__ __forceinline__ bool grid_reduce_mix(const Work& W, const typename A::T& v, bool pv, const double* f,
                                                 const bool* pf, typename A::T& out, bool& pout, double* fout,
@@ -220,14 +224,14 @@ __device__ __forceinline__ bool grid_reduce_mix(const Work& W, const typename A:
   using T = typename A::T;
   __shared__ bool am_last;
   if (threadIdx.x == 0) {
-    double* dst = W.part + (size_t)blockIdx.x * 8;
+    double* dst = W.part + (size_t)blockIdx.x * PART;
 #pragma unroll
     for (int k = 0; k < A::W; ++k) dst[k] = v.w[k];
-    dst[3] = pv ? 1.0 : 0.0;
+    dst[PRES] = pv ? 1.0 : 0.0;
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-      dst[4 + k] = f[k];
-      dst[7 - k] = pf[k] ? 1.0 : 0.0;
+      dst[FV + k] = f[k];
+      dst[FP + k] = pf[k] ? 1.0 : 0.0;
     }
     __threadfence();
     unsigned tk = atomicAdd(&W.st->counter, 1u);
@@ -242,16 +246,16 @@ __device__ __forceinline__ bool grid_reduce_mix(const Work& W, const typename A:
   double* sf = reinterpret_cast<double*>(sv + G);          // [NF][G]
   unsigned char* sp = reinterpret_cast<unsigned char*>(sf + NF * G);   // presence [1 + NF][G]
   for (int bk = threadIdx.x; bk < G; bk += blockDim.x) {
-    const double* src = W.part + (size_t)bk * 8;
+    const double* src = W.part + (size_t)bk * PART;
     T tv;
 #pragma unroll
     for (int k = 0; k < A::W; ++k) tv.w[k] = __ldcg(src + k);
     sv[bk] = tv;
-    sp[bk] = __ldcg(src + 3) != 0.0;
+    sp[bk] = __ldcg(src + PRES) != 0.0;
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-      sf[k * G + bk] = __ldcg(src + 4 + k);
-      sp[(1 + k) * G + bk] = __ldcg(src + 7 - k) != 0.0;
+      sf[k * G + bk] = __ldcg(src + FV + k);
+      sp[(1 + k) * G + bk] = __ldcg(src + FP + k) != 0.0;
     }
   }
   __syncthreads();

@@ -25,6 +25,9 @@ KernelTable table_qdw_nn();
 KernelTable table_tw();
 KernelTable table_qtw();
 KernelTable table_qtw_nn();
+KernelTable table_qw();
+KernelTable table_qqw();
+KernelTable table_qqw_nn();
 }  // namespace mwk
 
 namespace mwcg_detail {
@@ -33,11 +36,11 @@ int set_error(int code, const char* msg);
 
 namespace {
 
-// Capacity: block partials for up to kNoallocMaxG blocks (8 doubles each)
-// followed by one DevState (ticket counter).  About 66 KB, held by every GPU
-// that loads the library until the process exits.
+// Capacity: block partials for up to kNoallocMaxG blocks (mwk::PART = 12
+// doubles each) followed by one DevState (ticket counter).  About 99 KB, held
+// by every GPU that loads the library until the process exits.
 constexpr int kNoallocMaxG = MWCG_DOT_NOALLOC_MAX_G;
-constexpr size_t kPartDoubles = (size_t)kNoallocMaxG * 8;
+constexpr size_t kPartDoubles = (size_t)kNoallocMaxG * mwk::PART;
 constexpr size_t kStateDoubles = (sizeof(mwk::DevState) + sizeof(double) - 1) / sizeof(double);
 
 __device__ __align__(256) double g_dot_scratch[kPartDoubles + kStateDoubles];
@@ -47,7 +50,7 @@ std::mutex g_mu;
 double* g_scratch_dev[kMaxDevices] = {};    // device address of g_dot_scratch, per device
 
 const mwk::KernelTable& table_of(int arith) {
-  static mwk::KernelTable t[7];
+  static mwk::KernelTable t[10];
   static std::once_flag once;
   std::call_once(once, [] {
     t[0] = mwk::table_fp64();
@@ -57,6 +60,9 @@ const mwk::KernelTable& table_of(int arith) {
     t[4] = mwk::table_qtw();
     t[5] = mwk::table_qdw_nn();
     t[6] = mwk::table_qtw_nn();
+    t[7] = mwk::table_qw();
+    t[8] = mwk::table_qqw();
+    t[9] = mwk::table_qqw_nn();
   });
   return t[arith];
 }
@@ -91,7 +97,7 @@ int scratch_on_current_device(double** out) {
 extern "C" int mwcg_dot_noalloc(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream,
                                 double* out) {
   mwcg_detail::set_error(MWCG_OK, "");
-  if (arith < 0 || arith > 6) return mwcg_detail::set_error(MWCG_ERR_ARG, "mwcg_dot_noalloc: unknown arithmetic");
+  if (arith < 0 || arith > 9) return mwcg_detail::set_error(MWCG_ERR_ARG, "mwcg_dot_noalloc: unknown arithmetic");
   if (n < 0) return mwcg_detail::set_error(MWCG_ERR_ARG, "mwcg_dot_noalloc: n < 0");
   if (G < 1 || G > kNoallocMaxG) {
     char buf[160];

@@ -12,7 +12,7 @@ import pytest
 from paper_2510_13536_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
-ARITHS = ["fp64", "dw", "qdw", "tw", "qtw", "qdw_nn", "qtw_nn"]
+ARITHS = ["fp64", "dw", "qdw", "tw", "qtw", "qdw_nn", "qtw_nn", "qw", "qqw", "qqw_nn"]
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +47,7 @@ def _batch():
         else:
             A = P.diffusion_2d(int(rng.integers(4, 40)), seed=int(k))
         b = P.rhs_uniform(A.n, 100 + k)
-        systems.append((A, b, ARITHS[k % 7], 1e-11, 3000))
+        systems.append((A, b, ARITHS[k % len(ARITHS)], 1e-11, 3000))
     systems.append((P.laplacian_2d(10), np.zeros(100), "qtw", 1e-12, 100))            # b = 0
     systems.append((P.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0)), np.zeros(0), "dw",
                     1e-12, 100))                                                   # empty system

@@ -55,7 +55,7 @@ def _check(mw, orc, M, A, b, arith, norm, tol, maxit, tag):
     assert same_bits(r.history.cpu().numpy(), ho), (tag, arith, norm)
 
 
-@pytest.mark.parametrize("arith", ["qdw", "qtw"])
+@pytest.mark.parametrize("arith", ["qdw", "qtw", "qqw"])
 def test_graph_path_every_policy(mw, orc, arith):
     """3-D Laplacian 24^3 (54 tiles: the CUDA-graph path) in plan V=2 so that the
     lane-tree combines of NORM_SUM are exercised."""
@@ -77,7 +77,7 @@ def test_power_law_auto_plan(mw, orc, arith):
         _check(mw, orc, M, A, b, arith, norm, 1e-30, 150, "power-law")
 
 
-@pytest.mark.parametrize("arith", ["qdw", "qtw"])
+@pytest.mark.parametrize("arith", ["qdw", "qtw", "qqw"])
 def test_single_cluster_path(mw, orc, arith):
     """A 2-D Laplacian small enough for the one-cluster launch."""
     A = P.laplacian_2d(40)

@@ -15,8 +15,9 @@ from paper_2510_13536_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
 
-ARITHS = ["fp64", "dw", "qdw", "tw", "qtw", "qdw_nn", "qtw_nn"]
-W = {"fp64": 1, "dw": 2, "qdw": 2, "tw": 3, "qtw": 3, "qdw_nn": 2, "qtw_nn": 3}
+ARITHS = ["fp64", "dw", "qdw", "tw", "qtw", "qdw_nn", "qtw_nn", "qw", "qqw", "qqw_nn"]
+W = {"fp64": 1, "dw": 2, "qdw": 2, "tw": 3, "qtw": 3, "qdw_nn": 2, "qtw_nn": 3, "qw": 4, "qqw": 4, "qqw_nn": 4}
+SCALE = np.array([1.0, 1e-17, 1e-34, 1e-51])
 
 
 @pytest.fixture(scope="module")
@@ -106,20 +107,20 @@ def test_spmv_bit_exact_all_lane_splits(mw, orc, arith):
     w = W[arith]
     for A in _matrices():
         M = mw.CSRMatrix.from_csr(A)
-        p = rng.standard_normal((w, A.n)) * np.array([1.0, 1e-17, 1e-34][:w])[:, None]
+        p = rng.standard_normal((w, A.n)) * SCALE[:w, None]
         for V in (1, 2, 4, 8, 16, 32):
             M.plan = (V, 256, 5)
             q = host(mw.spmv(M, arith, dev(p)))
             assert same_bits(q, orc.spmv(arith, A, p, V)), (A.name, V)
 
 
-@pytest.mark.parametrize("arith", ["fp64", "dw", "qtw", "tw"])
+@pytest.mark.parametrize("arith", ["fp64", "dw", "qtw", "tw", "qqw", "qw"])
 def test_dot_bit_exact(mw, orc, arith):
     rng = np.random.default_rng(8)
     w = W[arith]
     for n in (1, 7, 255, 256, 257, 5000, 65536 + 3):
-        u = rng.standard_normal((w, n)) * np.array([1.0, 1e-17, 1e-34][:w])[:, None]
-        v = rng.standard_normal((w, n)) * np.array([1.0, 1e-17, 1e-34][:w])[:, None]
+        u = rng.standard_normal((w, n)) * SCALE[:w, None]
+        v = rng.standard_normal((w, n)) * SCALE[:w, None]
         for G in (1, 3, 152, 1024):
             d = mw.dot(arith, dev(u), dev(v), G)
             assert same_bits(d, orc.dot(arith, u, v, 256, G)), (n, G)

@@ -12,8 +12,8 @@ from paper_2510_13536_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
 
-ARITHS = ["fp64", "dw", "qdw", "tw", "qtw", "qdw_nn", "qtw_nn"]
-W = {"fp64": 1, "dw": 2, "qdw": 2, "tw": 3, "qtw": 3, "qdw_nn": 2, "qtw_nn": 3}
+ARITHS = ["fp64", "dw", "qdw", "tw", "qtw", "qdw_nn", "qtw_nn", "qw", "qqw", "qqw_nn"]
+W = {"fp64": 1, "dw": 2, "qdw": 2, "tw": 3, "qtw": 3, "qdw_nn": 2, "qtw_nn": 3, "qw": 4, "qqw": 4, "qqw_nn": 4}
 R, X, PP, Q, SUM = 1, 2, 4, 8, 16
 
 
@@ -69,7 +69,7 @@ def test_graph_path_all_arithmetics(mw, orc, arith):
         _check(mw, orc, M, A, b, arith, tol, maxit, A.name)
 
 
-@pytest.mark.parametrize("arith", ["qdw", "qtw"])
+@pytest.mark.parametrize("arith", ["qdw", "qtw", "qqw"])
 def test_with_normalisation_policies(mw, orc, arith):
     A = P.laplacian_3d(24, 1e-3)
     b = P.rhs_uniform(A.n, 33)
@@ -80,7 +80,7 @@ def test_with_normalisation_policies(mw, orc, arith):
         _check(mw, orc, M, A, b, arith, 1e-30, 150, "policy", norm=norm)
 
 
-@pytest.mark.parametrize("arith", ["fp64", "dw", "qtw", "tw"])
+@pytest.mark.parametrize("arith", ["fp64", "dw", "qtw", "tw", "qqw", "qw"])
 def test_single_cluster_path(mw, orc, arith):
     A = P.diffusion_2d(40, 5)
     b = P.rhs_uniform(A.n, 34)
@@ -88,7 +88,7 @@ def test_single_cluster_path(mw, orc, arith):
     M.preconditioner = "jacobi"
     _check(mw, orc, M, A, b, arith, 1e-30, 400, "cluster")
     M.plan = (4, 256, M.plan[2])
-    x0 = np.random.default_rng(3).standard_normal((W[arith], A.n)) * np.array([1.0, 1e-17, 1e-34][:W[arith]])[:, None]
+    x0 = np.random.default_rng(3).standard_normal((W[arith], A.n)) * np.array([1.0, 1e-17, 1e-34, 1e-51][:W[arith]])[:, None]
     _check(mw, orc, M, A, b, arith, 1e-30, 400, "cluster V=4 x0", x0=x0)
 
 
@@ -136,7 +136,7 @@ def test_undefined_preconditioner(mw, orc):
             B.col[k0] = 6 if B.col[k0 - 1] != 6 else 8
         M = mw.CSRMatrix.from_csr(B)
         M.preconditioner = "jacobi"
-        x0 = np.full((3, A.n), 0.25)
+        x0 = np.full((3, A.n), 0.25)      # three words: QTW
         r = mw.solve(M, dev(b), "qtw", 1e-20, 100, x0=dev(x0))
         xo, ito, rro, sto = orc.cg("qtw", B, b, x0=x0, tol=1e-20, maxit=100, plan=M.plan, precond="jacobi")
         assert (r.status, r.iters, sto, ito) == (3, 0, 3, 0), bad
@@ -149,6 +149,7 @@ def test_undefined_preconditioner(mw, orc):
 def test_batched_mixed_preconditioning(mw, orc):
     import torch
     systems = [(P.diffusion_2d(35, 1), "qtw", "jacobi"), (P.laplacian_3d(14, 1e-3), "qdw", "none"),
+               (P.diffusion_2d(30, 7), "qqw", "jacobi"), (P.laplacian_2d(22), "qw", "none"),
                (P.power_law_laplacian(2000, seed=9, mean_deg=10, max_deg=120), "dw", "jacobi"),
                (P.diffusion_2d(20, 2), "fp64", "jacobi"), (P.laplacian_2d(25), "tw", "none"),
                (P.diffusion_2d(28, 4), "qtw_nn", "jacobi")]
@@ -173,7 +174,7 @@ def test_batched_mixed_preconditioning(mw, orc):
     assert res[-1].status == 3
 
 
-@pytest.mark.parametrize("arith", ["qtw", "dw"])
+@pytest.mark.parametrize("arith", ["qtw", "dw", "qqw"])
 def test_adjoint_gradients(mw, orc, arith):
     import torch
     A = P.diffusion_2d(50, 10)
