@@ -66,6 +66,8 @@ def lib():
         L.orc_cg_norm.restype = i32
         L.orc_pcg_jacobi.argtypes = [i32, i64, P, P, P, P, P, d, i32, i32, i32, i32, i32, ctypes.c_uint32, P, P, P]
         L.orc_pcg_jacobi.restype = i32
+        L.orc_bicgstab.argtypes = [i32, i64, P, P, P, P, P, d, i32, i32, i32, i32, P, P, P]
+        L.orc_bicgstab.restype = i32
         L.orc_grad_values.argtypes = [i32, i64, P, P, P, P, P]
         L.orc_grad_values.restype = i32
         L.orc_words.argtypes = [i32]
@@ -229,6 +231,27 @@ def cg(arith, A, b, x0=None, tol=1e-12, maxit=1000, plan=None, history=False, no
         st = lib().orc_cg_norm(k, A.n, _p(rp), _p(col), _p(val), _p(b), _p(x), float(tol), int(maxit),
                                int(V), int(T), int(G), int(every), int(mask), ctypes.byref(it),
                                ctypes.byref(rr), _p(hist) if history else None)
+    if st < 0:
+        raise ValueError(arith)
+    if history:
+        return x, it.value, rr.value, st, hist[: it.value]
+    return x, it.value, rr.value, st
+
+
+def bicgstab(arith, A, b, x0=None, tol=1e-12, maxit=1000, plan=None, history=False):
+    """BiCGStab in the given arithmetic (nonsymmetric A); as cg()."""
+    k = arith_id(arith)
+    w = WORDS[k]
+    rp, col, val = _csr(A)
+    b = _a(b)
+    x = np.zeros((w, A.n)) if x0 is None else _a(x0).reshape(w, A.n).copy()
+    V, T, G = plan if plan is not None else (0, 0, 0)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    hist = np.full(max(maxit, 1), np.nan) if history else None
+    st = lib().orc_bicgstab(k, A.n, _p(rp), _p(col), _p(val), _p(b), _p(x), float(tol), int(maxit),
+                            int(V), int(T), int(G), ctypes.byref(it), ctypes.byref(rr),
+                            _p(hist) if history else None)
     if st < 0:
         raise ValueError(arith)
     if history:

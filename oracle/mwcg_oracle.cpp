@@ -893,6 +893,129 @@ CGResult pcg_jacobi(int64_t n, const int64_t* rp, const int32_t* col, const doub
   }
 }
 
+// ---------------------------------------------------------------------------
+// BiCGStab (an extension: Sec. VI names other iterative methods as future
+// work), for nonsymmetric A, every vector and scalar in arithmetic A.  The
+// textbook recurrence (van der Vorst), shadow residual rh = r0:
+//   rho = rh^T r; [i > 1: beta = (rho / rho_prev) * (alpha / omega);
+//   p = r + beta (p - omega v), i.e. p = r (+) beta*(p (+) (-omega)*v)]
+//   v = A p; alpha = rho / rh^T v; s = r (+) (-alpha)*v;
+//   if ||s|| / ||b|| < tol: x = x (+) alpha*p, stop;
+//   t = A s; omega = t^T s / t^T t;
+//   x = (x (+) alpha*p) (+) omega*s; r = s (+) (-omega)*t; stop test on ||r||.
+// Readings:
+//  * The stopping residuals are FP64 (Sec. IV-C): sqrt(sum fl(c_i c_i)) /
+//    ||b|| with c_i = collapse(.), FP64 dots in the plan's vector order.
+//  * The quasi arithmetics normalise both residual AXPYs, s and r, every
+//    iteration (the analogue of Sec. IV-D's r).
+//  * Dots: rh^T v, t^T s and t^T t are fused with their SpMV (SpMV tiles of
+//    T/V rows, leaves rh_i*v_i, t_i*s_i, t_i*t_i); rho = rh^T r (leaves
+//    rh_i*r_i) with the x / r update (vector tiles of T rows).
+//  * Breakdown (status 2): collapse(rho), collapse(rh^T v) or collapse(t^T t)
+//    zero or not finite, omega's collapse zero, or a non-finite residual.
+//  * r0 = 0 (every word of rho0 = r0^T r0 zero): x0, zero iterations.  ||b|| =
+//    0: x = 0.  maxit <= 0: x0, status 1, relres = ||r0|| / ||b||.
+// ---------------------------------------------------------------------------
+template <class A>
+double fp64_norm_rel(const std::vector<double>& v, int64_t n, int64_t Rv, int G, bool plain, double bn) {
+  using T = typename A::T;
+  std::vector<double> c(n);
+  for (int64_t i = 0; i < n; ++i) c[i] = A::collapse(load<A>(v.data(), n, i));
+  return fdiv(fsqrt(dot<FP64>(c.data(), c.data(), n, Rv, G, plain).w[0]), bn);
+}
+
+template <class A>
+bool bad_scalar(const typename A::T& t) {
+  double c = A::collapse(t);
+  return c == 0.0 || !std::isfinite(c);
+}
+
+template <class A>
+CGResult bicgstab(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                  const double* b, double* x, double tol, int maxit, Plan plan, double* hist) {
+  using T = typename A::T;
+  const int W = A::W;
+  const bool plain = plan.V <= 0;
+  const int V = plain ? 1 : plan.V;
+  const int64_t Rs = plain ? 1 : std::max(1, plan.T / V);
+  const int64_t Rv = plain ? 1 : plan.T;
+  const int G = plain ? 1 : plan.G;
+  CGResult res{ST_CONVERGED, 0, 0.0};
+  double bn = fsqrt(bnorm2(b, n, Rv, G, plain));
+  if (bn == 0.0) {
+    for (int64_t i = 0; i < W * n; ++i) x[i] = 0.0;
+    return res;
+  }
+  std::vector<double> r(W * n), rh(W * n), p(W * n), v(W * n), s(W * n), t(W * n);
+  spmv<A>(rp, col, val, x, v.data(), n, V);
+  for (int64_t i = 0; i < n; ++i)
+    store<A>(r.data(), n, i, A::add(A::from(b[i]), neg<A>(load<A>(v.data(), n, i))));
+  rh = r;
+  T rho = dot<A>(rh.data(), r.data(), n, Rv, G, plain);
+  bool rzero = true;
+  for (int k = 0; k < W; ++k) rzero = rzero && (rho.w[k] == 0.0);
+  if (rzero) return res;
+  res.relres = fp64_norm_rel<A>(r, n, Rv, G, plain, bn);
+  if (maxit <= 0) { res.status = ST_MAXIT; return res; }
+  T rho_prev = A::zero(), alpha = A::zero(), omega = A::zero();
+  for (;;) {
+    if (bad_scalar<A>(rho)) { res.status = ST_BREAKDOWN; return res; }
+    if (res.iters == 0) {
+      p = r;
+    } else {
+      T beta = A::mul(A::div(rho, rho_prev), A::div(alpha, omega));
+      T momega = neg<A>(omega);
+      for (int64_t i = 0; i < n; ++i) {
+        T tmp = A::muladd(load<A>(p.data(), n, i), momega, load<A>(v.data(), n, i));
+        store<A>(p.data(), n, i, A::muladd(load<A>(r.data(), n, i), beta, tmp));
+      }
+    }
+    spmv<A>(rp, col, val, p.data(), v.data(), n, V);
+    T rv = dot<A>(rh.data(), v.data(), n, Rs, G, plain);
+    res.iters += 1;
+    if (bad_scalar<A>(rv)) { res.status = ST_BREAKDOWN; return res; }
+    alpha = A::div(rho, rv);
+    T malpha = neg<A>(alpha);
+    for (int64_t i = 0; i < n; ++i) {
+      T si = A::muladd(load<A>(r.data(), n, i), malpha, load<A>(v.data(), n, i));
+      A::normalize(si);
+      store<A>(s.data(), n, i, si);
+    }
+    double rs_ = fp64_norm_rel<A>(s, n, Rv, G, plain, bn);
+    if (rs_ < tol) {
+      for (int64_t i = 0; i < n; ++i)
+        store<A>(x, n, i, A::muladd(load<A>(x, n, i), alpha, load<A>(p.data(), n, i)));
+      res.relres = rs_;
+      if (hist) hist[res.iters - 1] = rs_;
+      res.status = ST_CONVERGED;
+      return res;
+    }
+    spmv<A>(rp, col, val, s.data(), t.data(), n, V);
+    T ts = dot<A>(t.data(), s.data(), n, Rs, G, plain);
+    T tt = dot<A>(t.data(), t.data(), n, Rs, G, plain);
+    if (bad_scalar<A>(tt)) { res.status = ST_BREAKDOWN; return res; }
+    omega = A::div(ts, tt);
+    T momega = neg<A>(omega);
+    for (int64_t i = 0; i < n; ++i) {
+      T xi = A::muladd(A::muladd(load<A>(x, n, i), alpha, load<A>(p.data(), n, i)), omega,
+                       load<A>(s.data(), n, i));
+      store<A>(x, n, i, xi);
+      T ri = A::muladd(load<A>(s.data(), n, i), momega, load<A>(t.data(), n, i));
+      A::normalize(ri);
+      store<A>(r.data(), n, i, ri);
+    }
+    T rho1 = dot<A>(rh.data(), r.data(), n, Rv, G, plain);
+    double relres = fp64_norm_rel<A>(r, n, Rv, G, plain, bn);
+    res.relres = relres;
+    if (hist) hist[res.iters - 1] = relres;
+    if (relres < tol) { res.status = ST_CONVERGED; return res; }
+    if (!std::isfinite(relres) || A::collapse(omega) == 0.0) { res.status = ST_BREAKDOWN; return res; }
+    if (res.iters >= maxit) { res.status = ST_MAXIT; return res; }
+    rho_prev = rho;
+    rho = rho1;
+  }
+}
+
 // Gradient of L = w^T x through A x = b (values only, sparsity kept):
 // dL/dval_k = -lambda_row(k) * x_col(k), lambda the adjoint solution, formed
 // as the arithmetic's product lambda_i * x_j and collapsed to FP64.
@@ -1010,6 +1133,16 @@ template <class A> struct OpPCG {
     return r.status;
   }
 };
+template <class A> struct OpBiCG {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                 int* iters, double* relres, double* hist) {
+    CGResult r = bicgstab<A>(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist);
+    *iters = r.iters;
+    *relres = r.relres;
+    return r.status;
+  }
+};
 template <class A> struct OpGrad {
   static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* lam,
                  const double* x, double* g) {
@@ -1089,6 +1222,12 @@ int orc_pcg_jacobi(int arith, int64_t n, const int64_t* rp, const int32_t* col, 
                    int every, unsigned mask, int* iters, double* relres, double* hist) {
   return dispatch<OpPCG>(arith, n, rp, col, val, b, x, tol, maxit, V, T, G, every, mask, iters,
                          relres, hist);
+}
+// BiCGStab (nonsymmetric A), mirrored order when V > 0.
+int orc_bicgstab(int arith, int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                 int* iters, double* relres, double* hist) {
+  return dispatch<OpBiCG>(arith, n, rp, col, val, b, x, tol, maxit, V, T, G, iters, relres, hist);
 }
 int orc_grad_values(int arith, int64_t n, const int64_t* rp, const int32_t* col,
                     const double* lam, const double* x, double* g) {

@@ -243,6 +243,27 @@ def diffusion_2d(m: int, seed: int, sigma: float = 1.0, dyadic: bool = False) ->
     return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), f"diffusion2d_{m}")
 
 
+def convection_diffusion_2d(m: int, beta: float = 1.0, shift: float = 0.0) -> CSR:
+    """Nonsymmetric 2-D convection-diffusion on an m x m grid: the 5-point
+    Laplacian plus first-order upwind convection with velocity (1, 1), scaled
+    so that each row gains ``beta`` on the diagonal and on its west and south
+    couplings (``beta`` = mesh Peclet number).  Row (y, x): diagonal
+    4 + 2 beta + shift, west -1 - beta, south -1 - beta, east and north -1,
+    couplings across the Dirichlet boundary dropped.  A nonsingular M-matrix;
+    dyadic beta keeps every entry, and A x for x of +-1, exact."""
+    n = m * m
+    idx = np.arange(n).reshape(m, m)
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [np.full(n, 4.0 + 2.0 * beta + shift)]
+    for (dy, dx), w in (((0, -1), -1.0 - beta), ((-1, 0), -1.0 - beta), ((0, 1), -1.0), ((1, 0), -1.0)):
+        ys, xs = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+        ok = (ys + dy >= 0) & (ys + dy < m) & (xs + dx >= 0) & (xs + dx < m)
+        rows.append(idx[ok])
+        cols.append(idx[(ys + dy)[ok], (xs + dx)[ok]])
+        vals.append(np.full(int(ok.sum()), w))
+    return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals),
+                     f"convdiff2d_{m}_{beta:g}")
+
+
 def random_spd_small(n: int, seed: int, density: float = 0.3, shift_exp: int = -6) -> CSR:
     """Small SPD matrix with dyadic entries (tests with a dense exact solve).
 

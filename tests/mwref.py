@@ -148,3 +148,44 @@ def pcg_exact(M, b, w, iters: int):
         p = [z[i] + beta * p[i] for i in range(n)]
         rho = rho1
     return xs, rrs
+
+
+def bicgstab_exact(M, b, iters: int):
+    """Textbook BiCGStab (x0 = 0, shadow residual r0) in exact rationals.
+    Returns the iterates x_1..x_k (stops early when s or r becomes zero)."""
+    n = len(M)
+
+    def matvec(v):
+        return [sum(M[i][j] * v[j] for j in range(n) if M[i][j] != 0) for i in range(n)]
+
+    def dot(u, v):
+        return sum(u[i] * v[i] for i in range(n))
+
+    x = [Fraction(0)] * n
+    r = [Fraction(float(v)) for v in b]
+    rh = r[:]
+    rho = dot(rh, r)
+    p = v = None
+    rho_prev = alpha = omega = None
+    xs = []
+    for k in range(iters):
+        if k == 0:
+            p = r[:]
+        else:
+            beta = (rho / rho_prev) * (alpha / omega)
+            p = [r[i] + beta * (p[i] - omega * v[i]) for i in range(n)]
+        v = matvec(p)
+        alpha = rho / dot(rh, v)
+        s = [r[i] - alpha * v[i] for i in range(n)]
+        if all(e == 0 for e in s):
+            xs.append([x[i] + alpha * p[i] for i in range(n)])
+            break
+        t = matvec(s)
+        omega = dot(t, s) / dot(t, t)
+        x = [x[i] + alpha * p[i] + omega * s[i] for i in range(n)]
+        r = [s[i] - omega * t[i] for i in range(n)]
+        xs.append(x[:])
+        rho_prev, rho = rho, dot(rh, r)
+        if all(e == 0 for e in r):
+            break
+    return xs
