@@ -367,6 +367,26 @@ def run_words(torch, mw, P, cpu):
     return out
 
 
+def run_bicg(torch, mw, P, cpu):
+    """BiCGStab on nonsymmetric upwind convection-diffusion systems (512^2,
+    mesh Peclet 1 and 8), every arithmetic from FP64 to QQW, to 1e-14."""
+    out = {}
+    for beta in (1.0, 8.0):
+        A = P.convection_diffusion_2d(512, beta)
+        b = P.rhs_uniform(A.n, P.SEED_BASE + 8)
+        M = mw.CSRMatrix.from_csr(A)
+        db = torch.as_tensor(b, device="cuda")
+        res = {"workload": f"2-D upwind convection-diffusion 512^2 (n = {A.n}), mesh Peclet {beta:g}, b = 2U-1, "
+                           "tol 1e-14, maxit 20000", "plan": list(M.plan), "runs": []}
+        for ar in ("fp64", "dw", "qdw", "qtw", "qqw"):
+            mw.solve_bicgstab(M, db, ar, 1e-14, 2)
+            r, ms = _timed(torch, lambda: mw.solve_bicgstab(M, db, ar, 1e-14, 20000))
+            res["runs"].append({"arith": ar, "iters": r.iters, "status": r.status, "relres": r.relres,
+                                "time_s": ms / 1e3, "ms_per_iter": ms / max(r.iters, 1)})
+        out[f"peclet_{beta:g}"] = res
+    return out
+
+
 def run_c4(torch, mw, P, cpu):
     specs = P.batch_specs(256, P.SEED_BASE + 4)
     systems = [P.build_batch_system(s) for s in specs]
@@ -483,6 +503,8 @@ def run_workloads(args):
             res = run_pcg(torch, mw, P, not args.no_cpu)
         elif w == "words":
             res = run_words(torch, mw, P, not args.no_cpu)
+        elif w == "bicg":
+            res = run_bicg(torch, mw, P, not args.no_cpu)
         else:
             raise SystemExit(f"unknown workload {w}")
         res["wall_s"] = time.perf_counter() - t0
@@ -712,7 +734,7 @@ def main():
     ap.add_argument("--kernels-only", type=int, default=0, metavar="N",
                     help="run N iterations with each kernel launched on its own (mwcg_profile_kernels) and print "
                          "their mean durations; used for ncu captures")
-    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm", "pcg", "words"],
+    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm", "pcg", "words", "bicg"],
                     help="measure another configuration instead of the headline (one JSON line each)")
     ap.add_argument("--fd", type=int, default=32, help="finite-difference entries checked in c5")
     ap.add_argument("--plan", default=None, help="override the summation plan V,T,G (ncu / tuning runs)")

@@ -169,6 +169,27 @@ int mwcg_get_normalization(const mwcg_csr* A, int32_t* every, uint32_t* mask);
 int mwcg_set_preconditioner(mwcg_csr* A, int kind);
 int mwcg_get_preconditioner(const mwcg_csr* A, int* kind);
 
+/* Solve A x = b by BiCGStab in the given arithmetic, for nonsymmetric A (an
+ * extension: the paper's solver is CG, and Sec. VI names other iterative
+ * methods as future work).  The textbook recurrence (van der Vorst) with
+ * shadow residual rh = r0:
+ *   rho = rh^T r; p = r (first pass) or r (+) beta*(p (+) (-omega)*v);
+ *   v = A p; alpha = rho / rh^T v; s = r (+) (-alpha)*v;
+ *   stop with x (+)= alpha*p if ||s|| / ||b|| < tol; t = A s;
+ *   omega = t^T s / t^T t; x = (x (+) alpha*p) (+) omega*s; r = s (+) (-omega)*t;
+ *   beta = (rho' / rho) * (alpha / omega).
+ * Every vector and scalar is in the arithmetic; the quasi arithmetics
+ * normalise both residual AXPYs (s and r) every iteration; the stopping
+ * residuals are FP64, sqrt(sum_i collapse(.)^2) / ||b||_2 (Sec. IV-C).
+ * Arguments, x0, hist (optional device double[maxit], the FP64 relative
+ * residual after each iteration) and the results are as for
+ * mwcg_solve_history.  Returns MWCG_OK, MWCG_NOT_CONVERGED, MWCG_BREAKDOWN
+ * (collapse of rho, rh^T v or t^T t zero or not finite, omega's collapse zero,
+ * or a non-finite residual) or an error.  The handle's preconditioner and
+ * normalisation policy apply to CG only; BiCGStab has no batched form. */
+int mwcg_solve_bicgstab(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
+                        void* stream, int32_t* iters_out, double* relres_out);
+
 /* Solve A x = b by CG in the given arithmetic (Algorithm 1).
  *   b        device double[n];
  *   x        device double[w*n] (w = mwcg_words(arith)): x0 on entry, the

@@ -25,7 +25,7 @@ EXPORTS = [
     "mwcg_solve_history", "mwcg_solve_batched", "mwcg_adjoint", "mwcg_spmv", "mwcg_dot",
     "mwcg_word_op", "mwcg_collapse", "mwcg_profile_kernels", "mwcg_batched_cluster_size",
     "mwcg_dot_noalloc", "mwcg_probe_peak", "mwcg_set_normalization", "mwcg_get_normalization",
-    "mwcg_set_preconditioner", "mwcg_get_preconditioner",
+    "mwcg_set_preconditioner", "mwcg_get_preconditioner", "mwcg_solve_bicgstab",
 ]
 
 # Normalisation places of the quasi arithmetics' policy (MWCG_NORM_* in mwcg.h).
@@ -75,6 +75,7 @@ def load(path: str | None = None):
         "mwcg_solve": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, pi32, pd]),
         "mwcg_solve_host": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, pi32, pd]),
         "mwcg_solve_history": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, P, pi32, pd]),
+        "mwcg_solve_bicgstab": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, P, pi32, pd]),
         "mwcg_solve_batched": (ctypes.c_int, [i32, P, P, P, P, P, P, P, P, P, P]),
         "mwcg_adjoint": (ctypes.c_int, [P, P, P, ctypes.c_int, d, i32, P, P, P, pi32, pd]),
         "mwcg_spmv": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),

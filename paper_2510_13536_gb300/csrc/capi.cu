@@ -21,6 +21,7 @@
 
 #include "mwcg.h"
 #include "cg_kernels.cuh"
+#include "bicg_kernels.cuh"
 #include "batched.cuh"
 
 namespace mwb_host {
@@ -45,6 +46,16 @@ KernelTable table_qtw_nn();
 KernelTable table_qw();
 KernelTable table_qqw();
 KernelTable table_qqw_nn();
+BiTable bitable_fp64();
+BiTable bitable_dw();
+BiTable bitable_qdw();
+BiTable bitable_tw();
+BiTable bitable_qtw();
+BiTable bitable_qdw_nn();
+BiTable bitable_qtw_nn();
+BiTable bitable_qw();
+BiTable bitable_qqw();
+BiTable bitable_qqw_nn();
 }  // namespace mwk
 
 namespace {
@@ -104,6 +115,29 @@ const mwk::KernelTable* table(int arith) {
   return &t[arith];
 }
 
+const mwk::BiTable* bitable(int arith) {
+  static mwk::BiTable t[kNArith];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    t[0] = mwk::bitable_fp64();
+    t[1] = mwk::bitable_dw();
+    t[2] = mwk::bitable_qdw();
+    t[3] = mwk::bitable_tw();
+    t[4] = mwk::bitable_qtw();
+    t[5] = mwk::bitable_qdw_nn();
+    t[6] = mwk::bitable_qtw_nn();
+    t[7] = mwk::bitable_qw();
+    t[8] = mwk::bitable_qqw();
+    t[9] = mwk::bitable_qqw_nn();
+    for (auto& k : t)
+      for (const void* f : {k.init, k.spmv_v, k.s, k.spmv_t, k.xr})
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
+    cudaGetLastError();
+  });
+  if (arith < 0 || arith >= kNArith) return nullptr;
+  return &t[arith];
+}
+
 constexpr int32_t kMaxIt = 1 << 30;
 
 
@@ -148,6 +182,8 @@ struct mwcg_csr {
   double* hb = nullptr;        // staging for host-buffer solves, lazily allocated
   double* hx = nullptr;
   GraphCache graphs[kNArith];
+  GraphCache bigraphs[kNArith];  // BiCGStab
+  double* bws = nullptr;         // BiCGStab: rh, s, t (four words each), lazily allocated
   std::vector<int64_t> rowlen;  // host copy of row lengths (plan selection)
   int32_t norm_every = 1;       // normalisation policy of the quasi arithmetics
   uint32_t norm_mask = mwk::NORM_R;
@@ -161,11 +197,13 @@ struct mwcg_csr {
 namespace {
 
 void free_graphs(mwcg_csr* A) {
-  for (auto& g : A->graphs) {
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (g.graph) cudaGraphDestroy(g.graph);
-    g = GraphCache{};
-  }
+  for (GraphCache* set : {A->graphs, A->bigraphs})
+    for (int k = 0; k < kNArith; ++k) {
+      GraphCache& g = set[k];
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+      g = GraphCache{};
+    }
 }
 
 // FP64 operations per SpMV multiply-add and per add, by arithmetic (Sec. III
@@ -497,6 +535,133 @@ int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, in
   return h->status;
 }
 
+// ---------------------------------------------------------------------------
+// BiCGStab: one CUDA graph per (matrix, arithmetic) -- the x0 SpMV, init and
+// zero_x nodes, then a conditional WHILE node over the five loop kernels.
+// Small systems run the same graph (there is no single-cluster BiCGStab).
+// ---------------------------------------------------------------------------
+mwk::BiWork biwork_view(const mwcg_csr* A, unsigned long long cond, int has_cond) {
+  const int64_t n = A->n;
+  mwk::BiWork B;
+  B.w = work_view(A, cond, has_cond);
+  B.w.w = nullptr;
+  B.rh = A->bws;
+  B.s = A->bws + 4 * n;
+  B.t = A->bws + 8 * n;
+  return B;
+}
+
+int ensure_bigraph(mwcg_csr* A, int arith) {
+  GraphCache& gc = A->bigraphs[arith];
+  if (gc.exec && gc.plan.V == A->plan.V && gc.plan.G == A->plan.G) return MWCG_OK;
+  if (gc.exec) cudaGraphExecDestroy(gc.exec);
+  if (gc.graph) cudaGraphDestroy(gc.graph);
+  gc = GraphCache{};
+  const mwk::KernelTable* kt = table(arith);
+  const mwk::BiTable* bt = bitable(arith);
+  const int G = A->plan.G;
+  const size_t smem = red_smem(G, kt->words);
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(MWCG_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
+  }
+  const mwk::Csr M = csr_view(A);
+  const mwk::Work W = work_view(A, (unsigned long long)h, 1);
+  const mwk::BiWork B = biwork_view(A, (unsigned long long)h, 1);
+  cudaGraphNode_t n0, n1, n2, nw, b[5];
+  int rc;
+  const int mode0 = 0;
+  if ((rc = add_kernel(&n0, g, nullptr, 0, kt->spmv, G, smem, M, W, mode0)) ||
+      (rc = add_kernel(&n1, g, &n0, 1, bt->init, G, smem, M, B)) ||
+      (rc = add_kernel(&n2, g, &n1, 1, kt->zero_x, G, 0, M, W))) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  e = cudaGraphAddNode(&nw, g, &n2, nullptr, 1, &cp);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(MWCG_ERR_CUDA, "cudaGraphAddNode(while): %s", cudaGetErrorString(e));
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const void* fns[5] = {bt->p, bt->spmv_v, bt->s, bt->spmv_t, bt->xr};
+  const size_t sm[5] = {0, smem, smem, smem, smem};
+  for (int k = 0; k < 5; ++k) {
+    if ((rc = add_kernel(&b[k], body, k ? &b[k - 1] : nullptr, k ? 1 : 0, fns[k], G, sm[k], M, B))) {
+      cudaGraphDestroy(g);
+      return rc;
+    }
+  }
+  cudaGraphExec_t ex;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(MWCG_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  gc.graph = g;
+  gc.exec = ex;
+  gc.plan = A->plan;
+  return MWCG_OK;
+}
+
+int run_bicg(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
+             cudaStream_t s, int32_t* iters_out, double* relres_out) {
+  int rc;
+  if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
+  if (!A->bws) CK(cudaMalloc(&A->bws, sizeof(double) * 12 * (size_t)A->n));
+  const bool eager = eager_mode();
+  if (!eager && (rc = ensure_bigraph(A, arith)) != MWCG_OK) return rc;
+  mwk::DevState* h = A->h_st;
+  std::memset(h, 0, sizeof *h);
+  h->b = b;
+  h->x = x;
+  h->hist = hist;
+  h->tol = tol;
+  h->maxit = maxit;
+  CK(cudaMemcpyAsync(A->st, h, sizeof *h, cudaMemcpyHostToDevice, s));
+  if (eager) {
+    const mwk::KernelTable* kt = table(arith);
+    const mwk::BiTable* bt = bitable(arith);
+    mwk::Csr M = csr_view(A);
+    mwk::Work W = work_view(A, 0, 0);
+    mwk::BiWork B = biwork_view(A, 0, 0);
+    const int G = A->plan.G;
+    const size_t smem = red_smem(G, kt->words);
+    int mode0 = 0;
+    void* a_spmv0[] = {(void*)&M, (void*)&W, (void*)&mode0};
+    void* a_w[] = {(void*)&M, (void*)&W};
+    void* a_b[] = {(void*)&M, (void*)&B};
+    CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
+    CK(cudaLaunchKernel(bt->init, dim3(G), dim3(mwk::TPB), a_b, smem, s));
+    CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_w, 0, s));
+    const void* fns[5] = {bt->p, bt->spmv_v, bt->s, bt->spmv_t, bt->xr};
+    const int64_t batches = (int64_t)maxit / 16 + 2;
+    for (int64_t bt_ = 0; bt_ < batches; ++bt_) {
+      CK(cudaMemcpyAsync(h, A->st, sizeof *h, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h->done) break;
+      for (int i = 0; i < 16; ++i)
+        for (int k = 0; k < 5; ++k) CK(cudaLaunchKernel(fns[k], dim3(G), dim3(mwk::TPB), a_b, k ? smem : 0, s));
+    }
+  } else {
+    CK(cudaGraphLaunch(A->bigraphs[arith].exec, s));
+  }
+  CK(cudaMemcpyAsync(h, A->st, sizeof *h, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (iters_out) *iters_out = h->iters;
+  if (relres_out) *relres_out = h->relres;
+  if (h->status == mwk::ST_GUARD) return fail(MWCG_ERR_GUARD, "device loop guard tripped");
+  return h->status;
+}
+
 int check_solve_args(const mwcg_csr* A, const void* b, const void* x, int arith, double tol, int32_t maxit) {
   if (!A) return fail(MWCG_ERR_ARG, "null matrix handle");
   if (!table(arith)) return fail(MWCG_ERR_ARG, "unknown arithmetic %d", arith);
@@ -595,6 +760,7 @@ void mwcg_destroy_csr(mwcg_csr* A) {
   cudaFree(A->hx);
   cudaFree(A->w);
   cudaFree(A->w_bad);
+  cudaFree(A->bws);
   if (A->h_st) cudaFreeHost(A->h_st);
   delete A;
 }
@@ -660,6 +826,19 @@ int mwcg_get_normalization(const mwcg_csr* A, int32_t* every, uint32_t* mask) {
   *every = A->norm_every;
   *mask = A->norm_mask;
   return MWCG_OK;
+}
+
+int mwcg_solve_bicgstab(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
+                        void* stream, int32_t* iters_out, double* relres_out) {
+  g_err.clear();
+  int rc = check_solve_args(A, b, x, arith, tol, maxit);
+  if (rc != MWCG_OK) return rc;
+  if (A->n == 0) {
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return MWCG_OK;
+  }
+  return run_bicg(A, b, x, arith, tol, maxit, hist, S(stream), iters_out, relres_out);
 }
 
 int mwcg_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, void* stream,

@@ -65,6 +65,9 @@ struct DevState {
   uint32_t guard;           // loop passes seen by block 0 of k_spmv (hang guard)
   int32_t norm_every;       // normalisation policy (quasi arithmetics): every k iterations, 0 never
   uint32_t norm_mask;       // NORM_* places
+  double omega[4];          // BiCGStab: omega
+  int32_t early;            // BiCGStab: ||s|| met the tolerance (x += alpha p ends the solve)
+  int32_t pad1;
 };
 
 // Normalisation places (an extension of Sec. IV-D, which normalises r after

@@ -172,6 +172,25 @@ def solve(A: CSRMatrix, b: torch.Tensor, arith="qtw", tol: float = 1e-14, maxit:
     return SolveResult(x, it.value, rr.value, st, hist)
 
 
+def solve_bicgstab(A: CSRMatrix, b: torch.Tensor, arith="qtw", tol: float = 1e-14, maxit: int = 20000,
+                   x0: torch.Tensor | None = None, history: bool = False) -> SolveResult:
+    """BiCGStab on A x = b (A may be nonsymmetric) in the given arithmetic (device tensors)."""
+    a = arith_id(arith)
+    w = WORDS[a]
+    x = torch.zeros((w, A.n), dtype=torch.float64, device=b.device) if x0 is None else \
+        x0.to(torch.float64).reshape(w, A.n).clone().contiguous()
+    it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
+    hist = None
+    if history:
+        hist = torch.full((max(int(maxit), 1),), float("nan"), dtype=torch.float64, device=b.device)
+    st = check(_capi.load().mwcg_solve_bicgstab(A.handle, _ptr(b), _ptr(x), a, float(tol), int(maxit),
+                                                _ptr(hist) if history else None, _stream(), ctypes.byref(it),
+                                                ctypes.byref(rr)))
+    if history:
+        hist = hist[: it.value]
+    return SolveResult(x, it.value, rr.value, st, hist)
+
+
 def solve_host(A: CSRMatrix, b: np.ndarray, arith="qtw", tol: float = 1e-14, maxit: int = 20000,
                x0: np.ndarray | None = None):
     """CG with host (numpy) buffers; the copies are part of the call.  Returns (x, iters, relres, status)."""
