@@ -14,13 +14,13 @@ namespace mwb {
 constexpr int kCluster = 8;                 // CTAs per worker cluster (portable maximum)
 
 // Defined in batched_k<PREC><GRP>.cu: run_group<PREC, GRP>, one kernel each.
-using RunGroup = cudaError_t (*)(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
-cudaError_t run_group_00(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
-cudaError_t run_group_01(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
-cudaError_t run_group_02(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
-cudaError_t run_group_10(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
-cudaError_t run_group_11(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
-cudaError_t run_group_12(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*);
+using RunGroup = cudaError_t (*)(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
+cudaError_t run_group_00(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
+cudaError_t run_group_01(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
+cudaError_t run_group_02(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
+cudaError_t run_group_10(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
+cudaError_t run_group_11(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
+cudaError_t run_group_12(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
 const void* kernel_00();
 
 }  // namespace mwb
@@ -66,10 +66,15 @@ int small_cluster_size() {
 
 // Launch the persistent kernel over `nsys` prepared systems (host array, in
 // queue order) with clusters of `cluster` CTAs.  Systems are grouped by
-// (preconditioned or not, word group); the groups run as consecutive
-// launches, one kernel instantiation each, every group in queue order.  A
-// system's result depends only on its own plan, not on the grouping.
-// Returns a cudaError_t; outputs are copied back into hsys.
+// (preconditioned or not, word group), one kernel instantiation per group,
+// every group in queue order.  The groups run concurrently on streams forked
+// from `s` and joined back into it: their kernels share no data and never
+// wait on one another, so a later group's clusters take SMs as an earlier
+// group's clusters finish.  (Splitting the clusters between the groups in
+// proportion to their estimated work was measured slower: the estimate cannot
+// know the iteration counts.)  A system's result depends only on its own
+// plan, not on the grouping.  Returns a cudaError_t; outputs are copied back
+// into hsys.
 cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* clusters_out) {
   // MWCG_BATCH_PAD=0 drops the shared-memory pad that keeps one CTA per SM
   // (clusters may then share SMs); for tuning runs.
@@ -87,21 +92,44 @@ cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* c
   }
   mwb::Sys* dsys = nullptr;
   unsigned* queue = nullptr;
+  cudaStream_t gs[NG] = {};
+  cudaEvent_t ev[NG + 1] = {};
   cudaError_t e = cudaMalloc(&dsys, sizeof(mwb::Sys) * nsys);
   if (e == cudaSuccess) e = cudaMalloc(&queue, NG * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, NG * sizeof(unsigned), s);
-  int nclusters = 0, off = 0;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[NG], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[NG], s);                 // fork point
+  int nclusters = 0, off = 0, ngroups = 0;
+  for (int g = 0; g < NG; ++g) ngroups += grp[g].empty() ? 0 : 1;
   for (int g = 0; g < NG && e == cudaSuccess; ++g) {
     const int n = (int)grp[g].size();
     if (n == 0) continue;
-    e = cudaMemcpyAsync(dsys + off, grp[g].data(), sizeof(mwb::Sys) * n, cudaMemcpyHostToDevice, s);
+    if (ngroups == 1) {                       // one group (e.g. a single system): the caller's stream
+      gs[g] = s;
+    } else {
+      e = cudaStreamCreateWithFlags(&gs[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(gs[g], ev[NG], 0);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[g], cudaEventDisableTiming);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dsys + off, grp[g].data(), sizeof(mwb::Sys) * n, cudaMemcpyHostToDevice, gs[g]);
     int nc = 0;
-    if (e == cudaSuccess) e = run[g](dsys + off, n, queue + g, s, cluster, pad, &nc);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(grp[g].data(), dsys + off, sizeof(mwb::Sys) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = run[g](dsys + off, n, queue + g, gs[g], cluster, pad, &nc, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(grp[g].data(), dsys + off, sizeof(mwb::Sys) * n, cudaMemcpyDeviceToHost, gs[g]);
+    if (e == cudaSuccess && gs[g] != s) {
+      e = cudaEventRecord(ev[g], gs[g]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[g], 0);       // join
+    }
     nclusters = std::max(nclusters, nc);
     off += n;
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = es;
+  for (int g = 0; g <= NG; ++g) {
+    if (g < NG && gs[g] && gs[g] != s) cudaStreamDestroy(gs[g]);
+    if (ev[g]) cudaEventDestroy(ev[g]);
+  }
   if (e == cudaSuccess)
     for (int g = 0; g < NG; ++g)
       for (size_t k = 0; k < grp[g].size(); ++k) hsys[where[g][k]] = grp[g][k];

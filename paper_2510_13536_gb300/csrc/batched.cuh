@@ -61,9 +61,10 @@ struct Slots {
 };
 
 // Reduce per-CTA values across the cluster: every CTA returns the same result.
-// Up to two FP64 values ride along (fv/pf into fp64/pfp64, fv2/pf2 into
-// fp64_2/pfp64_2), reduced by the same tree.
-template <class A>
+// NF = 0, 1 or 2 FP64 values ride along (fv/pf into fp64/pfp64, fv2/pf2
+// into fp64_2/pfp64_2), reduced by the same tree; NF is a compile-time
+// count so that the reductions of the loop carry only what they need.
+template <class A, int NF = 0>
 __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Slots* slots, int buf,
                                                         const typename A::T& v, bool pv, bool& pout,
                                                         double* fp64 = nullptr, bool* pfp64 = nullptr,
@@ -75,10 +76,14 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
 #pragma unroll
     for (int k = 0; k < A::W; ++k) slots->v[buf][k] = v.w[k];
     slots->v[buf][mwk::PRES] = pv ? 1.0 : 0.0;
-    slots->v[buf][mwk::FV] = fv;
-    slots->v[buf][mwk::FP] = pf ? 1.0 : 0.0;
-    slots->v[buf][mwk::FV + 1] = fv2;
-    slots->v[buf][mwk::FP + 1] = pf2 ? 1.0 : 0.0;
+    if (NF >= 1) {
+      slots->v[buf][mwk::FV] = fv;
+      slots->v[buf][mwk::FP] = pf ? 1.0 : 0.0;
+    }
+    if (NF >= 2) {
+      slots->v[buf][mwk::FV + 1] = fv2;
+      slots->v[buf][mwk::FP + 1] = pf2 ? 1.0 : 0.0;
+    }
   }
   cc.cl.sync();
   __shared__ T sv[32];
@@ -95,10 +100,14 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
     for (int k = 0; k < A::W; ++k) t.w[k] = rs->v[buf][k];
     sv[threadIdx.x] = t;
     sp[threadIdx.x] = rs->v[buf][mwk::PRES] != 0.0;
-    sf[threadIdx.x] = rs->v[buf][mwk::FV];
-    spf[threadIdx.x] = rs->v[buf][mwk::FP] != 0.0;
-    sf2[threadIdx.x] = rs->v[buf][mwk::FV + 1];
-    spf2[threadIdx.x] = rs->v[buf][mwk::FP + 1] != 0.0;
+    if (NF >= 1) {
+      sf[threadIdx.x] = rs->v[buf][mwk::FV];
+      spf[threadIdx.x] = rs->v[buf][mwk::FP] != 0.0;
+    }
+    if (NF >= 2) {
+      sf2[threadIdx.x] = rs->v[buf][mwk::FV + 1];
+      spf2[threadIdx.x] = rs->v[buf][mwk::FP + 1] != 0.0;
+    }
   }
   __syncthreads();
   __shared__ T res;
@@ -113,21 +122,27 @@ __device__ __forceinline__ typename A::T cluster_reduce(const ClusterCtx& cc, Sl
     const int C = cc.C;
     T a = (lane < C) ? sv[lane] : A::zero();
     bool pa = (lane < C) ? (sp[lane] != 0) : false;
-    mw::MW<1> c{{(lane < C) ? sf[lane] : 0.0}};
-    bool pc = (lane < C) ? (spf[lane] != 0) : false;
-    mw::MW<1> c2{{(lane < C) ? sf2[lane] : 0.0}};
-    bool pc2 = (lane < C) ? (spf2[lane] != 0) : false;
+    mw::MW<1> c{{(NF >= 1 && lane < C) ? sf[lane] : 0.0}};
+    bool pc = (NF >= 1 && lane < C) ? (spf[lane] != 0) : false;
+    mw::MW<1> c2{{(NF >= 2 && lane < C) ? sf2[lane] : 0.0}};
+    bool pc2 = (NF >= 2 && lane < C) ? (spf2[lane] != 0) : false;
     for (int h = 1; h < C; h <<= 1) {
       T o = mwk::shfl_down<A>(a, h);
       bool po = __shfl_down_sync(0xffffffffu, (int)pa, h) != 0;
-      mw::MW<1> oc = mwk::shfl_down<mw::FP64>(c, h);
-      bool poc = __shfl_down_sync(0xffffffffu, (int)pc, h) != 0;
-      mw::MW<1> oc2 = mwk::shfl_down<mw::FP64>(c2, h);
-      bool poc2 = __shfl_down_sync(0xffffffffu, (int)pc2, h) != 0;
+      mw::MW<1> oc{{0.0}}, oc2{{0.0}};
+      bool poc = false, poc2 = false;
+      if (NF >= 1) {
+        oc = mwk::shfl_down<mw::FP64>(c, h);
+        poc = __shfl_down_sync(0xffffffffu, (int)pc, h) != 0;
+      }
+      if (NF >= 2) {
+        oc2 = mwk::shfl_down<mw::FP64>(c2, h);
+        poc2 = __shfl_down_sync(0xffffffffu, (int)pc2, h) != 0;
+      }
       if ((lane % (2 * h)) == 0 && lane + h < C) {
         mwk::combine<A>(a, pa, o, po);
-        mwk::combine<mw::FP64>(c, pc, oc, poc);
-        mwk::combine<mw::FP64>(c2, pc2, oc2, poc2);
+        if (NF >= 1) mwk::combine<mw::FP64>(c, pc, oc, poc);
+        if (NF >= 2) mwk::combine<mw::FP64>(c2, pc2, oc2, poc2);
       }
     }
     if (lane == 0) {
@@ -245,7 +260,8 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
   if constexpr (PREC) mwk::block_tree<mw::FP64>(rr, prr, 1);
   bool prho, pbn, prrs = false;
   double bn2, rrs = 0.0;
-  T rho = cluster_reduce<A>(cc, slots, buf, acc, pacc, prho, &bn2, &pbn, bb.w[0], pbb, &rrs, &prrs, rr.w[0], prr);
+  T rho = cluster_reduce<A, PREC ? 2 : 1>(cc, slots, buf, acc, pacc, prho, &bn2, &pbn, bb.w[0], pbb, &rrs, &prrs,
+                                          rr.w[0], prr);
   buf ^= 1;
   // Scalar steps run on one thread per CTA (the FP64 pipe is shared by the
   // whole SM) and are broadcast through shared memory.  Every CTA's thread 0
@@ -350,7 +366,7 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
     if constexpr (PREC) mwk::block_tree<mw::FP64>(rq, prq, 1);
     bool prr, prqs = false;
     double rqs = 0.0;
-    T rho1 = cluster_reduce<A>(cc, slots, buf, acc, pacc, prr, &rqs, &prqs, rq.w[0], prq);
+    T rho1 = cluster_reduce<A, PREC ? 1 : 0>(cc, slots, buf, acc, pacc, prr, &rqs, &prqs, rq.w[0], prq);
     buf ^= 1;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -431,11 +447,13 @@ __global__ void __launch_bounds__(TPB, 1) k_batched(Sys* __restrict__ sys, int n
 
 constexpr size_t kPadSmem = 120 * 1024;     // dynamic shared memory that keeps one CTA per SM
 
-// Host: run k_batched<PREC> over n systems already on the device (queue
-// zeroed), clusters of `cluster` CTAs, as many clusters as fit at once (at
-// most n).  The translation unit that calls it holds that instantiation.
+// Host: run k_batched<PREC, GRP> over n systems already on the device (queue
+// zeroed), clusters of `cluster` CTAs: as many clusters as fit at once, at
+// most n and, if max_clusters > 0, at most max_clusters.  The translation
+// unit that calls it holds that instantiation.
 template <bool PREC, int GRP>
-cudaError_t run_group(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int cluster, size_t pad, int* nclusters) {
+cudaError_t run_group(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int cluster, size_t pad, int* nclusters,
+                      int max_clusters) {
   const void* kern = (const void*)&k_batched<PREC, GRP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPadSmem);
   if (e == cudaSuccess && cluster > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -456,6 +474,7 @@ cudaError_t run_group(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int clu
     e = cudaOccupancyMaxActiveClusters(&nc, kern, &cfg);
   }
   if (e == cudaSuccess) {
+    if (max_clusters > 0 && nc > max_clusters) nc = max_clusters;
     nc = nc < 1 ? 1 : (nc < n ? nc : n);
     cfg.gridDim = dim3(nc * cluster);
     e = cudaLaunchKernelEx(&cfg, k_batched<PREC, GRP>, dsys, n, queue);

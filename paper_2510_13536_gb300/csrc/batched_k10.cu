@@ -16,8 +16,8 @@ __device__ __forceinline__ void solve_any<true, 0>(const ClusterCtx& cc, Slots* 
 }
 
 cudaError_t run_group_10(Sys* dsys, int n, unsigned* queue, cudaStream_t s, int cluster, size_t pad,
-                          int* nclusters) {
-  return run_group<true, 0>(dsys, n, queue, s, cluster, pad, nclusters);
+                          int* nclusters, int max_clusters) {
+  return run_group<true, 0>(dsys, n, queue, s, cluster, pad, nclusters, max_clusters);
 }
 
 }  // namespace mwb
