@@ -174,7 +174,7 @@ struct mwcg_csr {
   int32_t* col = nullptr;
   double* val = nullptr;
   mwcg_plan plan{1, 256, 1};
-  double* ws = nullptr;        // r, p, q: 3 vectors of up to 3 words
+  double* ws = nullptr;        // r, p, q: 3 vectors of up to 4 words
   double* part = nullptr;      // kMaxG * 8
   mwk::DevState* st = nullptr;
   mwk::DevState* h_st = nullptr;   // pinned mirror
