@@ -26,6 +26,9 @@
  *  - A matrix handle owns its device copy of the matrix and the solver
  *    workspace.  One solve at a time per handle (the workspace is shared);
  *    distinct handles may be used concurrently.
+ *  - The reduction kernels opt in to more than 48 KB of dynamic shared memory
+ *    (needed only by four-word arithmetics with plans of more than 945
+ *    blocks) on the device that is current at the library's first call.
  */
 #ifndef MWCG_H
 #define MWCG_H
