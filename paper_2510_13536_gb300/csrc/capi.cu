@@ -91,34 +91,7 @@ constexpr int kMaxG = 1024;
 // need the default 48 KB).
 size_t red_smem(int G, int w) { return (size_t)G * (8 * w + 20); }
 
-const mwk::KernelTable* table_raw(int arith);
-const mwk::BiTable* bitable(int arith);
-
-// The reduction kernels' dynamic shared-memory cap is a per-device function
-// attribute: set it once on each device the library runs on (before its
-// first launch there).
-void opt_in_smem() {
-  static std::mutex mu;
-  static bool done[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-  std::lock_guard<std::mutex> lock(mu);
-  if (done[dev]) return;
-  done[dev] = true;
-  const int cap = (int)red_smem(kMaxG, 4);
-  for (int a = 0; a < kNArith; ++a) {
-    const mwk::KernelTable& k = *table_raw(a);
-    for (const void* f : {k.spmv, k.spmv_pol, k.init, k.init_pcg, k.update, k.update_pol, k.update_pcg,
-                          k.update_pcg_pol, k.dot})
-      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    const mwk::BiTable& b = *bitable(a);
-    for (const void* f : {b.init, b.spmv_v, b.s, b.spmv_t, b.xr})
-      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  }
-  cudaGetLastError();
-}
-
-const mwk::KernelTable* table_raw(int arith) {
+const mwk::KernelTable* table(int arith) {
   static mwk::KernelTable t[kNArith];
   static std::once_flag once;
   std::call_once(once, [] {
@@ -132,17 +105,14 @@ const mwk::KernelTable* table_raw(int arith) {
     t[7] = mwk::table_qw();
     t[8] = mwk::table_qqw();
     t[9] = mwk::table_qqw_nn();
+    for (auto& k : t)
+      for (const void* f : {k.spmv, k.spmv_pol, k.init, k.init_pcg, k.update, k.update_pol, k.update_pcg,
+                            k.update_pcg_pol, k.dot})
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
+    cudaGetLastError();
   });
   if (arith < 0 || arith >= kNArith) return nullptr;
   return &t[arith];
-}
-
-// The kernel table of an arithmetic, with the shared-memory opt-in done on
-// the current device.
-const mwk::KernelTable* table(int arith) {
-  const mwk::KernelTable* t = table_raw(arith);
-  if (t) opt_in_smem();
-  return t;
 }
 
 const mwk::BiTable* bitable(int arith) {
@@ -159,6 +129,10 @@ const mwk::BiTable* bitable(int arith) {
     t[7] = mwk::bitable_qw();
     t[8] = mwk::bitable_qqw();
     t[9] = mwk::bitable_qqw_nn();
+    for (auto& k : t)
+      for (const void* f : {k.init, k.spmv_v, k.s, k.spmv_t, k.xr})
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
+    cudaGetLastError();
   });
   if (arith < 0 || arith >= kNArith) return nullptr;
   return &t[arith];
