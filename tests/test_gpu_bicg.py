@@ -119,3 +119,17 @@ def test_special_cases(mw, orc):
         xo, ito, rro, sto = orc.bicgstab(ar, A, b, tol=1e-10, maxit=0, plan=M.plan)
         assert (r.iters, r.status) == (ito, sto) == (0, 1) and r.relres == rro
         _check(mw, orc, M, A, b, ar, 1e-300, 3, "maxit")
+
+
+def test_empty_system(mw):
+    import torch
+    E = P.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    M = mw.CSRMatrix.from_csr(E)
+    for ar in ("fp64", "qtw", "qqw"):
+        b = torch.zeros(0, dtype=torch.float64, device="cuda")
+        r = mw.solve_bicgstab(M, b, ar, 1e-10, 10)
+        assert (r.iters, r.status, r.relres) == (0, 0, 0.0) and r.x.numel() == 0
+        M.preconditioner = "jacobi"
+        r = mw.solve(M, b, ar, 1e-10, 10)
+        assert (r.iters, r.status, r.relres) == (0, 0, 0.0)
+        M.preconditioner = "none"
