@@ -147,8 +147,8 @@ def _kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(arith):
-    """DRAM bytes per k_spmv launch from the committed ncu summary, or None when
+def _profile_fields(arith):
+    """The key/value lines of the committed ncu summary of k_spmv, or None when
     the summary is missing or the kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"k_spmv_{arith}_c2.md")
     try:
@@ -157,11 +157,32 @@ def _profiled_traffic(arith):
             if line.startswith("- ") and ":" in line:
                 k, v = line[2:].split(":", 1)
                 kv[k.strip()] = v.strip().strip("`")
-        if kv.get("kernel_source_digest") != _kernel_source_digest():
-            return None
-        return float(kv["dram_bytes_per_launch"])
-    except Exception:
+        return kv if kv.get("kernel_source_digest") == _kernel_source_digest() else None
+    except OSError:
         return None
+
+
+def _profiled_traffic(arith):
+    """DRAM bytes per k_spmv launch from the committed ncu summary (or None)."""
+    kv = _profile_fields(arith)
+    try:
+        return float(kv["dram_bytes_per_launch"]) if kv else None
+    except (KeyError, ValueError):
+        return None
+
+
+def _profiled_fp64_pipe(arith):
+    """Fraction of cycles the FP64 pipe was active in that capture (or None)."""
+    kv = _profile_fields(arith)
+    if not kv:
+        return None
+    for k, v in kv.items():
+        if k.startswith("FP64 pipe active"):
+            try:
+                return float(v.split("%")[0].strip()) / 100.0
+            except ValueError:
+                return None
+    return None
 
 
 def _golden_plan():
@@ -709,7 +730,10 @@ def run_gpu(args):
                      "alg_bytes_per_launch": spmv_bytes,
                      "hbm_frac_of_measured": spmv_bytes / (spmv_ms * 1e-3) / 6691.8e9,
                      "peak_source": "2 FP64 op/clk/SM x 152 SMs x 2070 MHz (derived; probe below measures it)",
-                     "probe_measured_now": probe},
+                     "probe_measured_now": probe,
+                     # frac counts the paper's operations, part of which the integer pipe
+                     # executes; the FP64 pipe's own busy fraction comes from ncu.
+                     "fp64_pipe_active_ncu": _profiled_fp64_pipe(arith)},
         "cpu_baseline": cpu,
     }
     if rk == 0:
