@@ -12,6 +12,13 @@
 // residual) and Sec. IV-D (normalise r once per iteration, after its AXPY),
 // and, as an extension, other normalisation frequencies and placements.
 // Where the paper is silent the reading taken is stated at the function.
+// Extensions for the directions Sec. VI names: Jacobi-preconditioned CG,
+// BiCGStab and the four-word arithmetics QW / QQW (listed in Sec. I).
+//
+// Parity unpinned against a cited source: TW (Fabiano et al.), QW (Hida et
+// al.) and QQW (Ozaki and Imamura) -- the paper prints none of their
+// sequences, so these are this project's restatements; their accuracy is
+// pinned in exact rationals by the tests.
 //
 // Build: plain C++17, -O2 -ffp-contract=off, no fast-math.  Every FP64
 // operation is an explicit call below (fadd/fsub/fmul/ffma/fdiv/fsqrt), so
