@@ -13,10 +13,11 @@
 // and, as an extension, other normalisation frequencies and placements.
 // Where the paper is silent the reading taken is stated at the function.
 // Extensions for the directions Sec. VI names: Jacobi-preconditioned CG,
-// BiCGStab and the four-word arithmetics QW / QQW (listed in Sec. I).
+// BiCGStab, the four-word arithmetics QW / QQW (listed in Sec. I) and QQF,
+// four FP32 words (Sec. II, Sec. VI), with its power-of-two-scaled CG.
 //
 // Parity unpinned against a cited source: TW (Fabiano et al.), QW (Hida et
-// al.) and QQW (Ozaki and Imamura) -- the paper prints none of their
+// al.), QQW (Ozaki and Imamura) and QQF -- the paper prints none of their
 // sequences, so these are this project's restatements; their accuracy is
 // pinned in exact rationals by the tests.
 //
@@ -546,6 +547,161 @@ MW<4> QW::div(const MW<4>& a, const MW<4>& b) {
 }
 
 // ---------------------------------------------------------------------------
+// QQF: multi-word arithmetic on four FP32 words (an extension).  Sec. II notes
+// multi-word arithmetic built from FP32 words as a stand-in for FP64 where the
+// hardware lacks it, and Sec. VI names processors with little FP64 throughput
+// as a direction.  Reading (parity unpinned against a cited source; accuracy
+// pinned by the tests): QQW's sequences above with every FP64 word and
+// operation replaced by an FP32 one, about 4 x 24 bits, between FP64 and DW.
+//  * An FP64 input (a matrix entry, b_i) enters as its exact three-word split
+//    (split3), and FP64 x QQF is the full QQF product with that split.
+//  * Division takes four FP32 quotient digits, as QQW's does.
+//  * collapse sums the words, lowest first, in FP64.
+// FP32 operations are plain float arithmetic (the build forbids contraction).
+// ---------------------------------------------------------------------------
+template <int W> struct MWF { float w[W]; };
+
+inline void two_sum_f(float a, float b, float& x, float& y) {   // Algorithm 2 in FP32
+  float s = a + b;
+  float z = s - a;
+  y = (a - (s - z)) + (b - z);
+  x = s;
+}
+inline void two_prod_f(float a, float b, float& x, float& y) {  // Algorithm 4 in FP32
+  float p = a * b;
+  y = std::fma(a, b, -p);
+  x = p;
+}
+inline float f32_of_bits(uint32_t u) {
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+// Exact split of an FP64 value into three FP32 words by significand bits
+// (24 + 23 + 6): a0 is the value truncated to 24 significant bits, a1 the
+// next 23 bits, a2 the last 6 -- all FP32 numbers when 2^-97 <= |a| < 2^128
+// (biased FP64 exponent 926..1150).  An integer m < 2^23 times 2^k is formed
+// as the FP32 number with exponent k + 23 and fraction m minus the one with
+// fraction 0 (an exact subtraction).  Any other value (zeros, subnormals,
+// |a| < 2^-97, |a| >= 2^128) takes a0 = fl32(a), a1 = fl32(a - a0),
+// a2 = fl32((a - a0) - a1), the differences in FP64.
+inline void split3(double a, float& a0, float& a1, float& a2) {
+  uint64_t u;
+  std::memcpy(&u, &a, 8);
+  const uint32_t sg = (uint32_t)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FF);
+  const uint64_t fr = u & 0xFFFFFFFFFFFFFULL;
+  if (e >= 926 && e <= 1150) {
+    a0 = f32_of_bits(sg | ((uint32_t)(e - 896) << 23) | (uint32_t)(fr >> 29));
+    const uint32_t e1 = (uint32_t)(e - 919) << 23, e2 = (uint32_t)(e - 925) << 23;
+    a1 = f32_of_bits(sg | e1 | (uint32_t)((fr >> 6) & 0x7FFFFFu)) - f32_of_bits(sg | e1);
+    a2 = f32_of_bits(sg | e2 | (uint32_t)(fr & 63u)) - f32_of_bits(sg | e2);
+    return;
+  }
+  a0 = (float)a;
+  const double d = a - (double)a0;
+  a1 = (float)d;
+  a2 = (float)(d - (double)a1);
+}
+
+struct QQF {
+  static constexpr int W = 4;
+  using T = MWF<4>;
+  static T zero() { return T{{0.0f, 0.0f, 0.0f, 0.0f}}; }
+  static T from(double a) {
+    T c;
+    split3(a, c.w[0], c.w[1], c.w[2]);
+    c.w[3] = 0.0f;
+    return c;
+  }
+  static T add(const T& a, const T& b) {
+    T c;
+    float e1, e2, e3, e4, e5, e6;
+    two_sum_f(a.w[0], b.w[0], c.w[0], e1);
+    two_sum_f(a.w[1], b.w[1], c.w[1], e2);
+    two_sum_f(c.w[1], e1, c.w[1], e3);
+    two_sum_f(a.w[2], b.w[2], c.w[2], e4);
+    two_sum_f(c.w[2], e2, c.w[2], e5);
+    two_sum_f(c.w[2], e3, c.w[2], e6);
+    c.w[3] = (((a.w[3] + b.w[3]) + e4) + e5) + e6;
+    return c;
+  }
+  static T mul(const T& a, const T& b) {
+    T c;
+    float e1, t2, e2, t3, e3, e4, e5;
+    two_prod_f(a.w[0], b.w[0], c.w[0], e1);                     // order 1
+    two_prod_f(a.w[0], b.w[1], t2, e2);                         // order u
+    two_prod_f(a.w[1], b.w[0], t3, e3);
+    two_sum_f(t2, t3, c.w[1], e4);
+    two_sum_f(c.w[1], e1, c.w[1], e5);
+    float t4, e6, t5, e7, t6, e8, e9, e10, e11, e12, e13, e14;
+    two_prod_f(a.w[0], b.w[2], t4, e6);                         // order u^2
+    two_prod_f(a.w[1], b.w[1], t5, e7);
+    two_prod_f(a.w[2], b.w[0], t6, e8);
+    two_sum_f(t4, t5, c.w[2], e9);
+    two_sum_f(c.w[2], t6, c.w[2], e10);
+    two_sum_f(c.w[2], e2, c.w[2], e11);
+    two_sum_f(c.w[2], e3, c.w[2], e12);
+    two_sum_f(c.w[2], e4, c.w[2], e13);
+    two_sum_f(c.w[2], e5, c.w[2], e14);
+    const float f1 = std::fma(a.w[3], b.w[0], e6);              // order u^3
+    const float f2 = std::fma(a.w[2], b.w[1], e7);
+    const float f3 = std::fma(a.w[1], b.w[2], e8);
+    const float f4 = std::fma(a.w[0], b.w[3], e9);
+    const float s3 = ((f1 + f2) + f3) + f4;
+    c.w[3] = ((((s3 + e10) + e11) + e12) + e13) + e14;
+    return c;
+  }
+  // One FP32 word times QQF (QQW's Algorithm-10 continuation in FP32); the
+  // quotient digits of the division are single words.
+  static T smul(float a, const T& b) {
+    T c;
+    float e1, e2, e3, e4, e5, e6;
+    two_prod_f(a, b.w[0], c.w[0], e1);
+    two_prod_f(a, b.w[1], c.w[1], e2);
+    two_sum_f(c.w[1], e1, c.w[1], e3);
+    two_prod_f(a, b.w[2], c.w[2], e4);
+    two_sum_f(c.w[2], e2, c.w[2], e5);
+    two_sum_f(c.w[2], e3, c.w[2], e6);
+    c.w[3] = (std::fma(a, b.w[3], e4) + e5) + e6;
+    return c;
+  }
+  static T dxmul(double a, const T& b) { return mul(from(a), b); }
+  static T muladd(const T& acc, const T& a, const T& b) { return add(acc, mul(a, b)); }
+  static T dxmuladd(const T& acc, double a, const T& b) { return add(acc, dxmul(a, b)); }
+  static void renorm(T& a) {                                     // VecSum4 in FP32
+    two_sum_f(a.w[0], a.w[1], a.w[0], a.w[1]);
+    two_sum_f(a.w[1], a.w[2], a.w[1], a.w[2]);
+    two_sum_f(a.w[2], a.w[3], a.w[2], a.w[3]);
+  }
+  static void normalize(T& a) { renorm(a); }
+  static T div(const T& a, const T& b);
+  static double collapse(const T& a) {
+    return fadd((double)a.w[0], fadd((double)a.w[1], fadd((double)a.w[2], (double)a.w[3])));
+  }
+};
+MWF<4> QQF::div(const MWF<4>& a, const MWF<4>& b) {
+  float q[4];
+  MWF<4> r = a;
+  for (int k = 0; k < 4; ++k) {
+    q[k] = r.w[0] / b.w[0];
+    if (k < 3) {
+      r = add(r, neg<QQF>(smul(q[k], b)));
+      renorm(r);
+    }
+  }
+  MWF<4> c{{q[0], q[1], q[2], q[3]}};
+  renorm(c);
+  return c;
+}
+// Every word times 2^k, each correctly rounded (exact unless it underflows).
+inline MWF<4> scale_words(const MWF<4>& a, int k) {
+  MWF<4> c;
+  for (int j = 0; j < 4; ++j) c.w[j] = (float)std::ldexp((double)a.w[j], k);
+  return c;
+}
+
+// ---------------------------------------------------------------------------
 // SoA vectors: word k of element i at v[k*n + i].
 // ---------------------------------------------------------------------------
 template <class A> inline typename A::T load(const double* v, int64_t n, int64_t i) {
@@ -802,6 +958,113 @@ CGResult cg(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
 }
 
 // ---------------------------------------------------------------------------
+// Algorithm 1 in QQF, with power-of-two scaling of r and p (an extension; the
+// reading of how FP32 words carry a CG whose residual shrinks far below its
+// start).  FP32's exponent stops at 2^-126 (2^-149 subnormal), so the lower
+// words of a residual near 1e-14 |b|, and of the squares in r^T r, would
+// underflow.  r and p are therefore held as r = 2^E r~, p = 2^E p~ with one
+// integer exponent E for both, chosen so that r~ has a root mean square near
+// one; x is held unscaled.  With rho~ = r~^T r~ and pi~ = p~^T (A p~):
+//   alpha = rho / pi = rho~ / pi~            (both carry 2^{2E})
+//   x    += alpha p = (alpha~ 2^E) p~
+//   r~'   = 2^{-s} (r~ - alpha~ q~),  E' = E + s,  q~ = A p~
+//   beta  = rho' / rho = 2^{2s} beta~,  beta~ = rho~' / rho~
+//   p~'   = r~' + (beta~ 2^s) p~
+//   ||r|| = 2^E sqrt(rho~)
+// The shift s of an iteration is fixed before it, from rho~ of the r~ it
+// updates: s = floor((ilogb(rho~) - ilogb(n)) / 2), i.e. floor(log2) of the
+// root mean square, clamped to [-100, 100] and so that |E + s| <= 1000.
+// Readings:
+//  * E0 the same function of ||b||_2^2 (an FP64 dot, as in cg()), and
+//    r~0 = split3(b_i 2^{-E0}) (+) 2^{-E0} (-(A x0)); b_i 2^{-E0} and each
+//    scaled word are correctly rounded (exact unless they underflow).
+//  * Scaling a word is one correctly rounded multiplication by 2^k.
+//  * r~ is normalised after its AXPY (Sec. IV-D), then scaled by 2^{-s}.
+//  * The FP64 relative residual is 2^E sqrt(collapse(rho~)) / ||b||_2.
+//  * The normalisation policy is fixed at the default (r every iteration);
+//    everything else (stop tests, breakdown, zero b, zero r0, maxit) as cg().
+// x must lie within FP32's range: its words are FP32 numbers, unscaled.
+// ---------------------------------------------------------------------------
+inline int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
+inline int scale_exp(double c, int64_t n) {
+  if (!(c > 0.0) || !std::isfinite(c)) return 0;
+  return floor_half(std::ilogb(c) - std::ilogb((double)n));
+}
+inline int clamp_shift(int t, int E) {
+  const int lo = std::max(-100, -1000 - E), hi = std::min(100, 1000 - E);
+  return std::min(hi, std::max(lo, t));
+}
+
+CGResult cg_qqf(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                const double* b, double* x, double tol, int maxit, Plan plan, double* hist) {
+  using A = QQF;
+  using T = A::T;
+  const int W = A::W;
+  const bool plain = plan.V <= 0;
+  const int V = plain ? 1 : plan.V;
+  const int64_t Rs = plain ? 1 : std::max(1, plan.T / V);
+  const int64_t Rv = plain ? 1 : plan.T;
+  const int G = plain ? 1 : plan.G;
+  CGResult res{ST_CONVERGED, 0, 0.0};
+
+  const double bb = bnorm2(b, n, Rv, G, plain);
+  const double bn = fsqrt(bb);
+  if (bn == 0.0) {
+    for (int64_t i = 0; i < W * n; ++i) x[i] = 0.0;
+    return res;
+  }
+  int E = scale_exp(bb, n);
+  std::vector<double> r(W * n), p(W * n), q(W * n);
+  spmv<A>(rp, col, val, x, q.data(), n, V);                   // A x0, unscaled
+  for (int64_t i = 0; i < n; ++i) {
+    T bi = A::from(std::ldexp(b[i], -E));
+    T ri = A::add(bi, scale_words(neg<A>(load<A>(q.data(), n, i)), -E));
+    store<A>(r.data(), n, i, ri);
+  }
+  p = r;
+  T rho = dot<A>(r.data(), r.data(), n, Rv, G, plain);
+  bool rzero = true;
+  for (int k = 0; k < W; ++k) rzero = rzero && (rho.w[k] == 0.0f);
+  double relres = fdiv(std::ldexp(fsqrt(A::collapse(rho)), E), bn);
+  res.relres = relres;
+  if (rzero) { res.relres = 0.0; return res; }
+  if (maxit <= 0) { res.status = ST_MAXIT; return res; }
+  int s = clamp_shift(scale_exp(A::collapse(rho), n), E);
+
+  for (;;) {
+    spmv<A>(rp, col, val, p.data(), q.data(), n, V);
+    T pq = dot<A>(p.data(), q.data(), n, Rs, G, plain);
+    res.iters += 1;
+    double pqc = A::collapse(pq);
+    if (!(pqc > 0.0) || !std::isfinite(pqc)) { res.status = ST_BREAKDOWN; return res; }
+    T alpha = A::div(rho, pq);
+    T cx = scale_words(alpha, E);
+    T malpha = neg<A>(alpha);
+    for (int64_t i = 0; i < n; ++i) {
+      T xi = A::muladd(load<A>(x, n, i), cx, load<A>(p.data(), n, i));
+      store<A>(x, n, i, xi);
+      T ri = A::muladd(load<A>(r.data(), n, i), malpha, load<A>(q.data(), n, i));
+      A::normalize(ri);
+      store<A>(r.data(), n, i, scale_words(ri, -s));
+    }
+    E += s;
+    T rho1 = dot<A>(r.data(), r.data(), n, Rv, G, plain);
+    relres = fdiv(std::ldexp(fsqrt(A::collapse(rho1)), E), bn);
+    res.relres = relres;
+    if (hist) hist[res.iters - 1] = relres;
+    if (relres < tol) { res.status = ST_CONVERGED; return res; }
+    if (!std::isfinite(relres)) { res.status = ST_BREAKDOWN; return res; }
+    if (res.iters >= maxit) { res.status = ST_MAXIT; return res; }
+    T beta = A::div(rho1, rho);
+    T cp = scale_words(beta, s);
+    for (int64_t i = 0; i < n; ++i)
+      store<A>(p.data(), n, i, A::muladd(load<A>(r.data(), n, i), cp, load<A>(p.data(), n, i)));
+    rho = rho1;
+    s = clamp_shift(scale_exp(A::collapse(rho1), n), E);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Jacobi-preconditioned CG (an extension: Sec. VI names preconditioning as
 // future work).  The textbook PCG recurrence with M^-1 = diag(w),
 // w_i = fl(1 / a_ii) in FP64, the preconditioner being FP64 like A:
@@ -1035,7 +1298,8 @@ void grad_values(int64_t n, const int64_t* rp, const int32_t* col, const double*
 }
 
 // Arithmetic dispatch: 0 FP64, 1 DW, 2 QDW, 3 TW, 4 QTW, 5 QDW-NN, 6 QTW-NN,
-// 7 QW, 8 QQW, 9 QQW-NN.
+// 7 QW, 8 QQW, 9 QQW-NN, 10 QQF (four FP32 words; the arrays hold FP32 values
+// as FP64).
 template <template <class> class F, class... Args>
 int dispatch(int arith, Args... args) {
   switch (arith) {
@@ -1049,6 +1313,7 @@ int dispatch(int arith, Args... args) {
     case 7: return F<QW>::run(args...);
     case 8: return F<QQW>::run(args...);
     case 9: return F<QQW_NN>::run(args...);
+    case 10: return F<QQF>::run(args...);
   }
   return -1;
 }
@@ -1158,6 +1423,32 @@ template <class A> struct OpGrad {
   }
 };
 
+// QQF runs Algorithm 1 with the scaling of cg_qqf(); the policy, the
+// preconditioned solver, BiCGStab and the adjoint's gradient are not defined
+// for it (status -2).
+template <> struct OpCG<QQF> {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                 int* iters, double* relres, double* hist) {
+    CGResult r = cg_qqf(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist);
+    *iters = r.iters;
+    *relres = r.relres;
+    return r.status;
+  }
+};
+template <> struct OpCGNorm<QQF> {
+  template <class... Args> static int run(Args...) { return -2; }
+};
+template <> struct OpPCG<QQF> {
+  template <class... Args> static int run(Args...) { return -2; }
+};
+template <> struct OpBiCG<QQF> {
+  template <class... Args> static int run(Args...) { return -2; }
+};
+template <> struct OpGrad<QQF> {
+  template <class... Args> static int run(Args...) { return -2; }
+};
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1241,8 +1532,8 @@ int orc_grad_values(int arith, int64_t n, const int64_t* rp, const int32_t* col,
   return dispatch<OpGrad>(arith, n, rp, col, lam, x, g);
 }
 int orc_words(int arith) {
-  static const int w[10] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4};
-  return (arith >= 0 && arith < 10) ? w[arith] : -1;
+  static const int w[11] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4, 4};
+  return (arith >= 0 && arith < 11) ? w[arith] : -1;
 }
 
 }  // extern "C"
