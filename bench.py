@@ -53,7 +53,16 @@ SPMV_OPS = {  # arith: (per nnz, per row)
 }
 SPMV_OPS["qdw_nn"] = SPMV_OPS["qdw"]
 SPMV_OPS["qtw_nn"] = SPMV_OPS["qtw"]
-WORDS = {"fp64": 1, "dw": 2, "qdw": 2, "qtw": 3, "tw": 3, "qdw_nn": 2, "qtw_nn": 3, "qw": 4, "qqw": 4, "qqw_nn": 4}
+WORDS = {"fp64": 1, "dw": 2, "qdw": 2, "qtw": 3, "tw": 3, "qdw_nn": 2, "qtw_nn": 3, "qw": 4, "qqw": 4, "qqw_nn": 4,
+         "qqf": 4}
+# FP32 pipe: 128 lanes per SM (FMA = 1 operation).
+FP32_PEAK_OPS = 128 * SMS * SM_MAX_MHZ * 1e6
+# FP32 operations of the QQF SpMV + p^T q kernel: per stored entry the FP64 x
+# QQF product (the full QQF product with the split: 6 TwoProd x 2 + 8 TwoSum
+# x 6 + 4 FMA + 8 adds = 72, plus the split's 2 exact subtractions) and the
+# QQF add (6 TwoSum x 6 + 4 = 40), less the add saved on each row's first
+# product; per row the dot leaf (product 72 + add 40).
+QQF_SPMV_OPS = (72 + 2 + 40, 72 + 40 - 40)
 
 
 def _dist():
@@ -388,6 +397,65 @@ def run_words(torch, mw, P, cpu):
     return out
 
 
+def run_qqf(torch, mw, P, cpu):
+    """FP32-word arithmetic (QQF) against the FP64-word ones on the 128^3
+    Poisson system to 1e-14 (time, iterations, per-kernel rooflines) and on
+    its exact-solution twin to 1e-24 (forward error)."""
+    import ctypes
+    from paper_2510_13536_gb300 import _capi
+    A, b, tol, maxit = P.workload("c2")
+    M = mw.CSRMatrix.from_csr(A)
+    db = torch.as_tensor(b, device="cuda")
+    n, nnz = A.n, A.nnz
+    out = {"workload": "c2: " + P.WORKLOADS["c2"], "plan": list(M.plan), "runs": []}
+    for ar in ("fp64", "dw", "qdw", "qtw", "qqf"):
+        mw.solve(M, db, ar, tol, 2)
+        r, ms = _timed(torch, lambda: mw.solve(M, db, ar, tol, maxit), reps=3)
+        out["runs"].append({"arith": ar, "iters": r.iters, "status": r.status, "relres": r.relres,
+                            "time_s": ms / 1e3, "ms_per_iter": ms / max(r.iters, 1)})
+    # Per-kernel durations (CUDA events around each launch) and their rooflines.
+    s = torch.cuda.current_stream()
+    kms = (ctypes.c_double * 3)()
+    xx = torch.zeros((2, n), dtype=torch.float64, device="cuda")
+    _capi.check(_capi.load().mwcg_profile_kernels(M.handle, ctypes.c_void_p(db.data_ptr()),
+                                                  ctypes.c_void_p(xx.data_ptr()), mw.arith_id("qqf"), 30,
+                                                  ctypes.c_void_p(s.cuda_stream), kms))
+    hbm = _measured_hbm_gbs() * 1e9
+    by = {"spmv_dot": 12 * nnz + 8 * (n + 1) + 2 * 16 * n,    # CSR + p gathered once + q written
+          "update_dot": 6 * 16 * n,                         # x, r read and written; p, q read
+          "p_update": 3 * 16 * n}                           # r read; p read and written
+    ops = QQF_SPMV_OPS[0] * nnz + QQF_SPMV_OPS[1] * n
+    kern = {}
+    for k, name in enumerate(("spmv_dot", "update_dot", "p_update")):
+        t = kms[k] * 1e-3
+        kern[name] = {"ms": kms[k], "alg_bytes": by[name], "hbm_gbs": by[name] / t / 1e9,
+                      "hbm_frac_of_measured": by[name] / t / hbm}
+    kern["spmv_dot"]["fp32_ops"] = ops
+    kern["spmv_dot"]["fp32_frac_of_peak"] = ops / (kms[0] * 1e-3) / FP32_PEAK_OPS
+    out["qqf_kernels"] = kern
+    # Forward error on the exact-solution twin (x* = +-1, b = A x* exact).
+    Ae, be, xs = P.exact_solution_system("norm_poisson")
+    Me = mw.CSRMatrix.from_csr(Ae)
+    dbe = torch.as_tensor(be, device="cuda")
+    fe = []
+    for ar, tl in (("dw", 1e-24), ("qdw", 1e-24), ("qqf", 1e-24), ("fp64", 1e-14)):
+        mw.solve(Me, dbe, ar, tl, 2)
+        r, ms = _timed(torch, lambda: mw.solve(Me, dbe, ar, tl, 20000))
+        x = r.x.double().cpu().numpy()
+        fe.append({"arith": ar, "tol": tl, "iters": r.iters, "status": r.status, "time_s": ms / 1e3,
+                   "forward_error": _forward_error(x, xs)})
+    out["exact_solution_twin"] = {"workload": P.NORM_SYSTEMS["norm_poisson"], "runs": fe}
+    return out
+
+
+def _measured_hbm_gbs():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
 def run_bicg(torch, mw, P, cpu):
     """BiCGStab on nonsymmetric upwind convection-diffusion systems (512^2,
     mesh Peclet 1 and 8), every arithmetic from FP64 to QQW, to 1e-14."""
@@ -526,6 +594,8 @@ def run_workloads(args):
             res = run_words(torch, mw, P, not args.no_cpu)
         elif w == "bicg":
             res = run_bicg(torch, mw, P, not args.no_cpu)
+        elif w == "qqf":
+            res = run_qqf(torch, mw, P, not args.no_cpu)
         else:
             raise SystemExit(f"unknown workload {w}")
         res["wall_s"] = time.perf_counter() - t0
@@ -758,7 +828,8 @@ def main():
     ap.add_argument("--kernels-only", type=int, default=0, metavar="N",
                     help="run N iterations with each kernel launched on its own (mwcg_profile_kernels) and print "
                          "their mean durations; used for ncu captures")
-    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm", "pcg", "words", "bicg"],
+    ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm", "pcg", "words", "bicg",
+                                                                         "qqf"],
                     help="measure another configuration instead of the headline (one JSON line each)")
     ap.add_argument("--fd", type=int, default=32, help="finite-difference entries checked in c5")
     ap.add_argument("--plan", default=None, help="override the summation plan V,T,G (ncu / tuning runs)")

@@ -15,7 +15,10 @@
  * Conventions for every function:
  *  - Multi-word vectors are structure of arrays: a vector of n elements in an
  *    arithmetic with w words (mwcg_words) is a double[w*n] with word k of
- *    element i at [k*n + i]; word 0 is the leading word.
+ *    element i at [k*n + i]; word 0 is the leading word.  MWCG_QQF's four
+ *    FP32 words fill two 8-byte slots per element instead: slot k (k = 0, 1)
+ *    of element i, at [k*n + i], holds words 2k and 2k+1 as two consecutive
+ *    floats (word 2k at the lower address); mwcg_words returns 2 for it.
  *  - "device" pointers are CUDA global-memory pointers of the current device;
  *    "host" pointers are ordinary (preferably pinned) host memory.
  *  - Work is ordered on the caller's CUDA stream (`stream`, a cudaStream_t;
@@ -44,7 +47,19 @@ extern "C" {
  * (four words, about 212 bits) are listed in Sec. I without algorithms; here
  * QQW continues QTW's Algorithms 7-10 one level down (VecSum4 normalises it)
  * and QW is every QQW operation followed by a renormalisation to four
- * non-overlapping words. */
+ * non-overlapping words.
+ * QQF (four FP32 words, about 96 bits; Sec. II notes FP32-word arithmetic
+ * where FP64 is missing, Sec. VI processors with little FP64) runs QQW's
+ * sequences on FP32 words and operations.  FP64 inputs (the matrix values,
+ * b) enter through an exact split into three FP32 words (exact for
+ * 2^-97 <= |a| < 2^128, correctly rounded pieces otherwise).  Its CG keeps r
+ * and p scaled by a power of two 2^E so that FP32's exponent range follows
+ * the shrinking residual (x is unscaled, so its values must lie within
+ * FP32's range, |x_i| >= 2^-54 or so for full precision).  QQF supports
+ * mwcg_solve, mwcg_solve_history, mwcg_solve_host, mwcg_spmv, mwcg_dot and
+ * mwcg_word_op; the normalisation policy does not apply to it (r is
+ * normalised every iteration), and the preconditioner, BiCGStab, the
+ * adjoint, the batched solve and mwcg_dot_noalloc return MWCG_ERR_ARG. */
 typedef enum {
   MWCG_FP64 = 0,
   MWCG_DW = 1,
@@ -55,7 +70,8 @@ typedef enum {
   MWCG_QTW_NN = 6,
   MWCG_QW = 7,
   MWCG_QQW = 8,
-  MWCG_QQW_NN = 9
+  MWCG_QQW_NN = 9,
+  MWCG_QQF = 10
 } mwcg_arith;
 
 /* Solver status (>= 0) and error codes (< 0). */
@@ -90,7 +106,8 @@ typedef struct {
 
 typedef struct mwcg_csr mwcg_csr;
 
-/* Number of FP64 words of an arithmetic (1 to 4), or -1 if unknown. */
+/* Number of 8-byte slots per element of a vector in an arithmetic (its FP64
+ * words, 1 to 4; 2 for MWCG_QQF's four FP32 words), or -1 if unknown. */
 int mwcg_words(int arith);
 
 /* Message of the last error on this thread ("" if none).  Owned by the
@@ -256,7 +273,8 @@ int mwcg_adjoint(mwcg_csr* A, const double* x, const double* gx, int arith, doub
 int mwcg_spmv(mwcg_csr* A, int arith, const double* p, double* q, void* stream);
 
 /* u^T v in the arithmetic over n elements (u, v device double[w*n]) with
- * tiles of 256 rows over G blocks (1..1024); out: host double[w]. */
+ * tiles of 256 rows over G blocks (1..1024); out: host double[w], one word
+ * per double (host double[4] holding the four FP32 words for MWCG_QQF). */
 int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream, double* out);
 
 /* Capacity, in blocks, of the fixed scratch array of mwcg_dot_noalloc. */
@@ -289,7 +307,8 @@ int mwcg_dot_noalloc(int arith, int64_t n, const double* u, const double* v, int
 /* Element-wise word operations on device arrays of n elements:
  *   op 0 add c = a + b; 1 mul c = a * b; 2 dxmul c = a (FP64, double[n]) * b;
  *   3 div c = a / b; 4 normalize c = the arithmetic's normalisation of a
- *   (QuickTwoSum for QDW, VecSum3 for QTW, identity otherwise);
+ *   (QuickTwoSum for QDW, VecSum3 for QTW, VecSum4 for QQW and QQF,
+ *   identity otherwise);
  *   5 collapse c (double[n]) = a summed lowest word first. */
 int mwcg_word_op(int op, int arith, int64_t n, const double* a, const double* b, double* c, void* stream);
 

@@ -46,6 +46,7 @@ KernelTable table_qtw_nn();
 KernelTable table_qw();
 KernelTable table_qqw();
 KernelTable table_qqw_nn();
+KernelTable table_qqf();
 BiTable bitable_fp64();
 BiTable bitable_dw();
 BiTable bitable_qdw();
@@ -80,7 +81,7 @@ int fail(int code, const char* fmt, ...) {
                   cudaGetErrorString(e_));                                                        \
   } while (0)
 
-constexpr int kNArith = 10;   // MWCG_FP64 .. MWCG_QQW_NN
+constexpr int kNArith = 11;   // MWCG_FP64 .. MWCG_QQF
 constexpr int kMaxG = 1024;
 
 // Dynamic shared memory of the last-block reductions: G slots of up to w
@@ -105,10 +106,11 @@ const mwk::KernelTable* table(int arith) {
     t[7] = mwk::table_qw();
     t[8] = mwk::table_qqw();
     t[9] = mwk::table_qqw_nn();
+    t[10] = mwk::table_qqf();
     for (auto& k : t)
-      for (const void* f : {k.spmv, k.spmv_pol, k.init, k.init_pcg, k.update, k.update_pol, k.update_pcg,
-                            k.update_pcg_pol, k.dot})
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
+      for (const void* f : {k.init_pre, k.spmv, k.spmv_pol, k.init, k.init_pcg, k.update, k.update_pol,
+                            k.update_pcg, k.update_pcg_pol, k.dot})
+        if (f) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
     cudaGetLastError();
   });
   if (arith < 0 || arith >= kNArith) return nullptr;
@@ -131,10 +133,10 @@ const mwk::BiTable* bitable(int arith) {
     t[9] = mwk::bitable_qqw_nn();
     for (auto& k : t)
       for (const void* f : {k.init, k.spmv_v, k.s, k.spmv_t, k.xr})
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
+        if (f) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
     cudaGetLastError();
   });
-  if (arith < 0 || arith >= kNArith) return nullptr;
+  if (arith < 0 || arith >= kNArith || !t[arith].init) return nullptr;   // none for QQF
   return &t[arith];
 }
 
@@ -361,8 +363,10 @@ int ensure_graph(mwcg_csr* A, int arith) {
   cudaGraphNode_t n0, n1, n2, nw, b0, b1, b2;
   int rc;
   const int mode0 = 0, mode1 = 1;
+  cudaGraphNode_t npre = nullptr;
   if ((rc = add_kernel(&n0, g, nullptr, 0, kt->spmv, G, smem, M, W, mode0)) ||
-      (rc = add_kernel(&n1, g, &n0, 1, lk.init, G, smem, M, W)) ||
+      (kt->init_pre && (rc = add_kernel(&npre, g, &n0, 1, kt->init_pre, G, smem, M, W))) ||
+      (rc = add_kernel(&n1, g, npre ? &npre : &n0, 1, lk.init, G, smem, M, W)) ||
       (rc = add_kernel(&n2, g, &n1, 1, kt->zero_x, G, 0, M, W))) {
     cudaGraphDestroy(g);
     return rc;
@@ -445,6 +449,7 @@ int run_eager(mwcg_csr* A, int arith, cudaStream_t s) {
   void* a_mw[] = {(void*)&M, (void*)&W};
   const LoopKernels lk = loop_kernels(A, kt);
   CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
+  if (kt->init_pre) CK(cudaLaunchKernel(kt->init_pre, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(lk.init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
   mwk::DevState* h = A->h_st;
@@ -498,6 +503,8 @@ int run_cluster(mwcg_csr* A, const double* b, double* x, int arith, double tol, 
 int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
               cudaStream_t s, int32_t* iters_out, double* relres_out) {
   int rc;
+  if (A->prec == MWCG_PREC_JACOBI && !table(arith)->init_pcg)
+    return fail(MWCG_ERR_ARG, "arithmetic %d has no preconditioned solver", arith);
   if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
   bool undefined = false;
   if ((rc = ensure_weights(A, s, &undefined)) != MWCG_OK) return rc;
@@ -508,7 +515,7 @@ int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, in
   }
   const int64_t tiles = (A->n + mwk::TPB - 1) / mwk::TPB;
   const int small = mwb_host::small_cluster_size();
-  if (!eager_mode() && A->plan.G == small && tiles <= small)
+  if (!eager_mode() && A->plan.G == small && tiles <= small && arith != MWCG_QQF)
     return run_cluster(A, b, x, arith, tol, maxit, hist, s, iters_out, relres_out);
   const bool eager = eager_mode();
   if (!eager && (rc = ensure_graph(A, arith)) != MWCG_OK) return rc;
@@ -676,7 +683,7 @@ int check_solve_args(const mwcg_csr* A, const void* b, const void* x, int arith,
 extern "C" {
 
 int mwcg_words(int arith) {
-  static const int w[kNArith] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4};
+  static const int w[kNArith] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4, 2};   // QQF: 4 FP32 words in 2 slots
   return (arith >= 0 && arith < kNArith) ? w[arith] : -1;
 }
 
@@ -833,6 +840,7 @@ int mwcg_solve_bicgstab(mwcg_csr* A, const double* b, double* x, int arith, doub
   g_err.clear();
   int rc = check_solve_args(A, b, x, arith, tol, maxit);
   if (rc != MWCG_OK) return rc;
+  if (!bitable(arith)) return fail(MWCG_ERR_ARG, "arithmetic %d has no BiCGStab", arith);
   if (A->n == 0) {
     if (iters_out) *iters_out = 0;
     if (relres_out) *relres_out = 0.0;
@@ -888,6 +896,7 @@ int mwcg_adjoint(mwcg_csr* A, const double* x, const double* gx, int arith, doub
   g_err.clear();
   int rc = check_solve_args(A, gx, x, arith, tol, maxit);
   if (rc != MWCG_OK) return rc;
+  if (!table(arith)->grad_values) return fail(MWCG_ERR_ARG, "arithmetic %d has no adjoint", arith);
   if (A->n == 0) {
     if (iters_out) *iters_out = 0;
     if (relres_out) *relres_out = 0.0;
@@ -941,7 +950,7 @@ int mwcg_spmv(mwcg_csr* A, int arith, const double* p, double* q, void* stream) 
 int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream, double* out) {
   g_err.clear();
   if (!table(arith) || n < 0 || G < 1 || G > kMaxG || !out) return fail(MWCG_ERR_ARG, "bad argument");
-  const int w = mwcg_words(arith);
+  const int w = (arith == MWCG_QQF) ? 4 : mwcg_words(arith);      // one word per double
   if (n == 0) {
     for (int k = 0; k < w; ++k) out[k] = 0.0;
     return MWCG_OK;
@@ -1008,6 +1017,8 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
   cudaStream_t s = S(stream);
   const mwk::KernelTable* kt = table(arith);
+  if (A->prec == MWCG_PREC_JACOBI && !kt->init_pcg)
+    return fail(MWCG_ERR_ARG, "arithmetic %d has no preconditioned solver", arith);
   mwk::DevState* h = A->h_st;
   std::memset(h, 0, sizeof *h);
   h->b = b;
@@ -1027,6 +1038,7 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   void* a_mw[] = {(void*)&M, (void*)&W};
   const LoopKernels lk = loop_kernels(A, kt);
   CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
+  if (kt->init_pre) CK(cudaLaunchKernel(kt->init_pre, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(lk.init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
   std::vector<cudaEvent_t> ev(3 * (size_t)niters + 1);
@@ -1075,6 +1087,7 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
   for (int s = 0; s < nsys; ++s) {
     int rc = check_solve_args(A[s], b[s], x[s], arith[s], tol[s], maxit[s]);
     if (rc != MWCG_OK) return fail(rc, "system %d: %s", s, g_err.c_str());
+    if (arith[s] == MWCG_QQF) return fail(MWCG_ERR_ARG, "system %d: QQF is not batched", s);
     if (!seen.insert(A[s]).second) return fail(MWCG_ERR_ARG, "system %d: matrix handle repeated in the batch", s);
     if ((rc = ensure_ws(A[s])) != MWCG_OK) return rc;
   }

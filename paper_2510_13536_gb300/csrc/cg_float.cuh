@@ -1,0 +1,249 @@
+// CG in QQF (four FP32 words, mw_float.cuh) with power-of-two scaling.
+//
+// FP32's exponent stops at 2^-126 (2^-149 subnormal): the lower words of a
+// residual near 1e-14 |b|, and of the squares in r^T r, would underflow.  The
+// solver therefore keeps r = 2^E r~ and p = 2^E p~ with one integer exponent
+// E (DevState qe) chosen so that r~ has a root mean square near one; x is
+// unscaled.  With rho~ = r~^T r~, pi~ = p~^T q~ and q~ = A p~ (Algorithm 1
+// rewritten for the scaled vectors):
+//   alpha~ = rho~ / pi~                       (k_spmv, unchanged)
+//   x     += (alpha~ 2^E) p~
+//   r~'    = 2^-s normalise(r~ + (-alpha~) q~),  E' = E + s
+//   rho~'  = r~'^T r~',  ||r|| = 2^E' sqrt(rho~')
+//   beta~  = rho~' / rho~,  p~' = r~' + (beta~ 2^s) p~
+// The shift s of an iteration is fixed before it, from the rho~ of the r~ it
+// updates: floor((ilogb(rho~) - ilogb(n)) / 2), the floor of log2 of the root
+// mean square, clamped to [-100, 100] and so that |E + s| <= 1000.  E0 is the
+// same function of ||b||^2 (k_qqf_bnorm, a pass before the init), and
+// r~0 = split3(b_i 2^-E0) (+) 2^-E0 (-(A x0)).  Every scaled word is one
+// correctly rounded multiplication by a power of two.
+//
+// The kernels keep the plan's summation order (the vector kernels' tiles of
+// TPB rows over G blocks) and the stop tests of cg_kernels.cuh.
+#pragma once
+#include "cg_kernels.cuh"
+#include "mw_float.cuh"
+
+namespace mwk {
+
+// ilogb of a positive finite FP64 value, from the bits.
+__device__ __forceinline__ int ilogb_pos(double c) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(c);
+  const int e = (int)(u >> 52);
+  return e != 0 ? e - 1023 : -1011 - __clzll((long long)u);
+}
+__device__ __forceinline__ int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
+// floor(log2) of the root mean square of a vector whose squares sum to c.
+__device__ __forceinline__ int scale_exp(double c, int64_t n) {
+  if (!(c > 0.0) || !isfinite(c)) return 0;
+  return floor_half(ilogb_pos(c) - ilogb_pos((double)n));
+}
+__device__ __forceinline__ int clamp_shift(int t, int E) {
+  const int lo = max(-100, -1000 - E), hi = min(100, 1000 - E);
+  return min(hi, max(lo, t));
+}
+template <class A>
+__device__ __forceinline__ typename A::T load_scalar_f(const double* s) {
+  typename A::T t;
+#pragma unroll
+  for (int k = 0; k < A::W; ++k) t.w[k] = (float)s[k];
+  return t;
+}
+
+// ||b||_2^2 in FP64 in the init's order; sets ||b|| and E0.
+template <class A>
+__global__ void __launch_bounds__(TPB) k_qqf_bnorm(Csr M, Work W) {
+  DevState* S = W.st;
+  const int64_t n = M.n;
+  const double* __restrict__ b = S->b;
+  const int64_t ntiles = (n + TPB - 1) / TPB;
+  mw::MW<1> acc{{0.0}};
+  bool pacc = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i = t * TPB + threadIdx.x;
+    if (i < n) {
+      const mw::MW<1> l{{mw::dmul(b[i], b[i])}};
+      if (pacc) acc = mw::FP64::add(acc, l);
+      else { acc = l; pacc = true; }
+    }
+  }
+  block_tree<mw::FP64>(acc, pacc, 1);
+  mw::MW<1> tot;
+  bool ptot = false;
+  if (!grid_reduce<mw::FP64, 0>(W, acc, pacc, tot, ptot)) return;
+  if (threadIdx.x == 0) {
+    S->counter = 0;
+    const double bb = ptot ? tot.w[0] : 0.0;
+    S->bnorm = __dsqrt_rn(bb);
+    S->qe = scale_exp(bb, n);
+  }
+}
+
+// r~0 = split3(b 2^-E0) (+) 2^-E0 (-(A x0)) with A x0 in q, p~0 = r~0,
+// rho~0 = r~0^T r~0; the last block sets the scalars and the stop flags.
+template <class A>
+__global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
+  using T = typename A::T;
+  DevState* S = W.st;
+  const int64_t n = M.n;
+  const double* __restrict__ b = S->b;
+  const int E = S->qe;
+  const double sb = mw::pow2d(-E);
+  const int64_t ntiles = (n + TPB - 1) / TPB;
+  T acc = A::zero();
+  bool pacc = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i = t * TPB + threadIdx.x;
+    if (i < n) {
+      const T ri = A::add(A::from(__dmul_rn(b[i], sb)), A::scale(A::neg(ld<A>(W.q, n, i)), -E));
+      st<A>(W.r, n, i, ri);
+      st<A>(W.p, n, i, ri);
+      const T leaf = A::mul(ri, ri);
+      if (pacc) acc = A::add(acc, leaf);
+      else { acc = leaf; pacc = true; }
+    }
+  }
+  block_tree<A>(acc, pacc, 1);
+  T rho;
+  bool prho = false;
+  if (!grid_reduce<A, 0>(W, acc, pacc, rho, prho)) return;
+  if (threadIdx.x == 0) {
+    S->counter = 0;
+    if (!prho) rho = A::zero();
+    const double bnorm = S->bnorm;
+    S->iters = 0;
+    S->status = ST_CONVERGED;
+    S->done = 0;
+    S->zero_x = 0;
+#pragma unroll
+    for (int k = 0; k < A::W; ++k) S->rho[k] = rho.w[k];
+    if (bnorm == 0.0) {
+      S->relres = 0.0;
+      S->done = 1;
+      S->zero_x = 1;
+    } else {
+      bool rzero = true;
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) rzero = rzero && (rho.w[k] == 0.0f);
+      S->relres = __ddiv_rn(__dmul_rn(__dsqrt_rn(A::collapse(rho)), mw::pow2d(E)), bnorm);
+      if (rzero) {
+        S->relres = 0.0;
+        S->done = 1;
+      } else if (S->maxit <= 0) {
+        S->status = ST_MAXIT;
+        S->done = 1;
+      }
+    }
+    S->qs = 0;
+    S->qs_next = clamp_shift(scale_exp(A::collapse(rho), n), E);
+  }
+}
+
+// x += (alpha~ 2^E) p~; r~ = 2^-s normalise(r~ + (-alpha~) q~); rho~' = r~^T r~;
+// the stop test on 2^(E+s) sqrt(rho~') / ||b||; beta~; the next shift.
+template <class A>
+__global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
+  using T = typename A::T;
+  DevState* S = W.st;
+  if (S->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(W, 0);
+    return;
+  }
+  const int64_t n = M.n;
+  double* __restrict__ x = S->x;
+  const int E = S->qe, s = S->qs_next;
+  const T al = load_scalar_f<A>(S->alpha);
+  const T cx = A::scale(al, E);
+  const T mal = A::neg(al);
+  const float ps = mw::pow2f(-s);
+  const int64_t ntiles = (n + TPB - 1) / TPB;
+  T acc = A::zero();
+  bool pacc = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i = t * TPB + threadIdx.x;
+    if (i < n) {
+      st<A>(x, n, i, A::muladd(ld<A>(x, n, i), cx, ld<A>(W.p, n, i)));
+      T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
+      A::renorm(ri);
+#pragma unroll
+      for (int j = 0; j < A::W; ++j) ri.w[j] = mw::fmul(ri.w[j], ps);
+      st<A>(W.r, n, i, ri);
+      const T leaf = A::mul(ri, ri);
+      if (pacc) acc = A::add(acc, leaf);
+      else { acc = leaf; pacc = true; }
+    }
+  }
+  block_tree<A>(acc, pacc, 1);
+  T tot;
+  bool ptot = false;
+  if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  if (threadIdx.x == 0) {
+    S->counter = 0;
+    if (!ptot) tot = A::zero();
+    const int En = E + s;
+    const double c = A::collapse(tot);
+    const double relres = __ddiv_rn(__dmul_rn(__dsqrt_rn(c), mw::pow2d(En)), S->bnorm);
+    S->relres = relres;
+    const int it = S->iters;
+    if (S->hist) S->hist[it - 1] = relres;
+    unsigned cont = 0;
+    if (relres < S->tol) {
+      S->status = ST_CONVERGED;
+      S->done = 1;
+    } else if (!isfinite(relres)) {
+      S->status = ST_BREAKDOWN;
+      S->done = 1;
+    } else if (it >= S->maxit) {
+      S->status = ST_MAXIT;
+      S->done = 1;
+    } else {
+      const T rho = load_scalar_f<A>(S->rho);
+      const T be = A::div(tot, rho);
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) { S->beta[k] = be.w[k]; S->rho[k] = tot.w[k]; }
+      cont = 1;
+    }
+    S->qe = En;
+    S->qs = s;
+    S->qs_next = clamp_shift(scale_exp(c, n), En);
+    set_cond(W, cont);
+  }
+}
+
+// p~ = r~ + (beta~ 2^s) p~.
+template <class A>
+__global__ void __launch_bounds__(TPB, A::MINB) k_qqf_pupdate(Csr M, Work W) {
+  using T = typename A::T;
+  DevState* S = W.st;
+  if (S->done) return;
+  const int64_t n = M.n;
+  const T cp = A::scale(load_scalar_f<A>(S->beta), S->qs);
+  const int64_t stride = (int64_t)gridDim.x * TPB;
+  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride)
+    st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), cp, ld<A>(W.p, n, i)));
+}
+
+// The QQF kernel table: plain CG only (no normalisation policy, no
+// preconditioner, no adjoint gradient kernel); vectors of two 8-byte slots.
+inline KernelTable make_table_qqf() {
+  using A = mw::QQF;
+  KernelTable t{};
+  t.words = slots<A>();
+  t.init_pre = (const void*)&k_qqf_bnorm<A>;
+  t.spmv = (const void*)&k_spmv<A>;
+  t.spmv_pol = t.spmv;
+  t.init = (const void*)&k_qqf_init<A>;
+  t.update = (const void*)&k_qqf_update<A>;
+  t.pupdate = (const void*)&k_qqf_pupdate<A>;
+  t.update_pol = t.update;
+  t.pupdate_pol = t.pupdate;
+  t.init_pcg = t.update_pcg = t.pupdate_pcg = t.update_pcg_pol = t.pupdate_pcg_pol = nullptr;
+  t.zero_x = (const void*)&k_zero_x<slots<A>()>;
+  t.grad_values = nullptr;
+  t.collapse = (const void*)&k_collapse<A>;
+  t.dot = (const void*)&k_dot<A>;
+  t.word_op = (const void*)&k_word_op<A>;
+  return t;
+}
+
+}  // namespace mwk

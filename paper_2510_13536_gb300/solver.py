@@ -3,7 +3,9 @@
 Argument marshalling only -- every arithmetic step runs in libmwcg.so.
 Device arrays are torch CUDA tensors (float64, contiguous); multi-word
 vectors have shape (w, n) with word 0 leading (the C ABI's structure of
-arrays).  Work is issued on torch's current CUDA stream.
+arrays).  QQF vectors are float32 of shape (4, n) here; the C ABI packs their
+words two to an 8-byte slot, and the binding converts between the layouts.
+Work is issued on torch's current CUDA stream.
 """
 from __future__ import annotations
 
@@ -14,7 +16,7 @@ import numpy as np
 import torch
 
 from . import _capi
-from ._capi import ARITH, WORDS, Plan, check
+from ._capi import ARITH, FP32_WORDS, SLOTS, WORDS, Plan, check
 
 __all__ = ["CSRMatrix", "SolveResult", "solve", "solve_host", "solve_batched", "batched_cluster_size", "adjoint", "spmv", "dot",
            "word_op", "collapse", "words", "arith_id", "MWCGSolve", "solve_differentiable"]
@@ -31,6 +33,36 @@ def arith_id(arith) -> int:
 
 def words(arith) -> int:
     return WORDS[arith_id(arith)]
+
+
+def _pack(x: torch.Tensor, n: int) -> torch.Tensor:
+    """(4, n) FP32 words -> the C ABI's (2, n) slots (words 2k, 2k+1 in slot k)."""
+    f = x.to(torch.float32).reshape(2, 2, n).permute(0, 2, 1).contiguous()
+    return f.view(torch.float64).reshape(2, n).contiguous()
+
+
+def _unpack(x: torch.Tensor, n: int) -> torch.Tensor:
+    """The C ABI's (2, n) slots -> (4, n) FP32 words."""
+    return x.contiguous().view(torch.float32).reshape(2, n, 2).permute(0, 2, 1).reshape(4, n).contiguous()
+
+
+def _pack_np(x: np.ndarray, n: int) -> np.ndarray:
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(2, 2, n).transpose(0, 2, 1))
+    return f.view(np.float64).reshape(2, n).copy()
+
+
+def _unpack_np(x: np.ndarray, n: int) -> np.ndarray:
+    return np.ascontiguousarray(x.view(np.float32).reshape(2, n, 2).transpose(0, 2, 1).reshape(4, n))
+
+
+def _to_abi(a: int, x: torch.Tensor, n: int) -> torch.Tensor:
+    if a in FP32_WORDS:
+        return _pack(x, n)
+    return x.to(torch.float64).reshape(WORDS[a], n).contiguous()
+
+
+def _from_abi(a: int, x: torch.Tensor, n: int) -> torch.Tensor:
+    return _unpack(x, n) if a in FP32_WORDS else x
 
 
 def _stream():
@@ -155,9 +187,8 @@ def solve(A: CSRMatrix, b: torch.Tensor, arith="qtw", tol: float = 1e-14, maxit:
           x0: torch.Tensor | None = None, history: bool = False) -> SolveResult:
     """CG on A x = b in the given arithmetic (device tensors)."""
     a = arith_id(arith)
-    w = WORDS[a]
-    x = torch.zeros((w, A.n), dtype=torch.float64, device=b.device) if x0 is None else \
-        x0.to(torch.float64).reshape(w, A.n).clone().contiguous()
+    x = torch.zeros((SLOTS[a], A.n), dtype=torch.float64, device=b.device) if x0 is None else \
+        _to_abi(a, x0, A.n).clone()
     it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
     L = _capi.load()
     hist = None
@@ -169,7 +200,7 @@ def solve(A: CSRMatrix, b: torch.Tensor, arith="qtw", tol: float = 1e-14, maxit:
     else:
         st = check(L.mwcg_solve(A.handle, _ptr(b), _ptr(x), a, float(tol), int(maxit), _stream(),
                                 ctypes.byref(it), ctypes.byref(rr)))
-    return SolveResult(x, it.value, rr.value, st, hist)
+    return SolveResult(_from_abi(a, x, A.n), it.value, rr.value, st, hist)
 
 
 def solve_bicgstab(A: CSRMatrix, b: torch.Tensor, arith="qtw", tol: float = 1e-14, maxit: int = 20000,
@@ -197,12 +228,16 @@ def solve_host(A: CSRMatrix, b: np.ndarray, arith="qtw", tol: float = 1e-14, max
     a = arith_id(arith)
     w = WORDS[a]
     bb = np.ascontiguousarray(b, dtype=np.float64)
-    x = np.zeros((w, A.n)) if x0 is None else np.ascontiguousarray(np.asarray(x0, dtype=np.float64).reshape(w, A.n)).copy()
+    if a in FP32_WORDS:
+        x = np.zeros((SLOTS[a], A.n)) if x0 is None else _pack_np(x0, A.n)
+    else:
+        x = np.zeros((w, A.n)) if x0 is None else \
+            np.ascontiguousarray(np.asarray(x0, dtype=np.float64).reshape(w, A.n)).copy()
     it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
     st = check(_capi.load().mwcg_solve_host(A.handle, bb.ctypes.data_as(ctypes.c_void_p),
                                             x.ctypes.data_as(ctypes.c_void_p), a, float(tol), int(maxit), _stream(),
                                             ctypes.byref(it), ctypes.byref(rr)))
-    return x, it.value, rr.value, st
+    return (_unpack_np(x, A.n) if a in FP32_WORDS else x), it.value, rr.value, st
 
 
 def solve_batched(As, bs, arith, tol, maxit, x0s=None):
@@ -245,24 +280,26 @@ def adjoint(A: CSRMatrix, x: torch.Tensor, gx: torch.Tensor, arith="qtw", tol: f
     g_b = torch.empty(A.n, dtype=torch.float64, device=gx.device)
     g_val = torch.empty(A.nnz, dtype=torch.float64, device=gx.device)
     it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
-    st = check(_capi.load().mwcg_adjoint(A.handle, _ptr(x.contiguous()), _ptr(gx.contiguous()), a, float(tol),
-                                         int(maxit), _stream(), _ptr(g_b), _ptr(g_val), ctypes.byref(it),
-                                         ctypes.byref(rr)))
+    xc, gc = x.contiguous(), gx.contiguous()           # held until the call returns
+    st = check(_capi.load().mwcg_adjoint(A.handle, _ptr(xc), _ptr(gc), a, float(tol), int(maxit), _stream(),
+                                         _ptr(g_b), _ptr(g_val), ctypes.byref(it), ctypes.byref(rr)))
     return g_b, g_val, it.value, rr.value, st
 
 
 def spmv(A: CSRMatrix, arith, p: torch.Tensor) -> torch.Tensor:
     a = arith_id(arith)
-    q = torch.empty_like(p)
-    check(_capi.load().mwcg_spmv(A.handle, a, _ptr(p), _ptr(q), _stream()))
-    return q
+    pp = _to_abi(a, p, A.n)
+    q = torch.empty_like(pp)
+    check(_capi.load().mwcg_spmv(A.handle, a, _ptr(pp), _ptr(q), _stream()))
+    return _from_abi(a, q, A.n)
 
 
 def dot(arith, u: torch.Tensor, v: torch.Tensor, G: int) -> np.ndarray:
     a = arith_id(arith)
     out = np.zeros(WORDS[a])
     n = u.shape[-1]
-    check(_capi.load().mwcg_dot(a, n, _ptr(u), _ptr(v), int(G), _stream(), out.ctypes.data_as(ctypes.c_void_p)))
+    uu, vv = _to_abi(a, u, n), _to_abi(a, v, n)      # held until the call returns
+    check(_capi.load().mwcg_dot(a, n, _ptr(uu), _ptr(vv), int(G), _stream(), out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
 
@@ -274,16 +311,22 @@ def word_op(op: str, arith, a: torch.Tensor, b: torch.Tensor | None = None) -> t
     k = arith_id(arith)
     o = _OPS[op]
     n = a.shape[-1]
-    c = torch.empty(n if o == 5 else (WORDS[k], n), dtype=torch.float64, device=a.device)
+    if k in FP32_WORDS:                 # FP32 words: pack the multi-word operands
+        a = a if o == 2 else _to_abi(k, a, n)
+        b = None if b is None else _to_abi(k, b, n)
+    c = torch.empty(n if o == 5 else (SLOTS[k], n), dtype=torch.float64, device=a.device)
     check(_capi.load().mwcg_word_op(o, k, n, _ptr(a), _ptr(b), _ptr(c), _stream()))
-    return c
+    return c if o == 5 else _from_abi(k, c, n)
 
 
 def collapse(x: torch.Tensor) -> torch.Tensor:
-    """FP64 value of a (w, n) multi-word vector, lowest word first."""
+    """FP64 value of a (w, n) multi-word vector, lowest word first (QQF: float32 (4, n))."""
+    if x.dtype == torch.float32:
+        return word_op("collapse", "qqf", x)
     w, n = (1, x.shape[0]) if x.dim() == 1 else x.shape
     y = torch.empty(n, dtype=torch.float64, device=x.device)
-    check(_capi.load().mwcg_collapse(_ptr(x.contiguous()), int(w), int(n), _ptr(y), _stream()))
+    xc = x.contiguous()                                 # held until the call returns
+    check(_capi.load().mwcg_collapse(_ptr(xc), int(w), int(n), _ptr(y), _stream()))
     return y
 
 

@@ -1,0 +1,196 @@
+"""QQF (four FP32 words, scaled CG) on the CUDA path vs the oracle, bit for bit.
+
+The word algebra (add, mul, FP64 x QQF through the exact three-word split,
+division, VecSum4, collapse), the SpMV and dot, and the solver on the CUDA
+graph and on host-launched kernels, including right-hand sides far outside
+FP32's range (the power-of-two scaling of r and p) and the special cases.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_13536_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_13536_gb300 import build, solver
+    build.build()
+    return solver
+
+
+def same_bits(a, b):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if a.shape != b.shape:
+        return False
+    na, nb = np.isnan(a), np.isnan(b)
+    if not np.array_equal(na, nb):
+        return False
+    return np.array_equal(a.view(np.uint64)[~na], b.view(np.uint64)[~nb])
+
+
+def dev(x, dtype=np.float64):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=dtype), device="cuda")
+
+
+def rand_qqf(rng, n, emin=-20, emax=20):
+    """(4, n) FP32 expansions with non-overlapping words (float64 holding FP32 values)."""
+    w = np.empty((4, n), dtype=np.float32)
+    w[0] = (rng.uniform(1, 2, n) * rng.choice([-1, 1], n) * 2.0 ** rng.integers(emin, emax, n)).astype(np.float32)
+    for k in range(1, 4):
+        w[k] = (w[k - 1].astype(np.float64) * 2.0 ** -24 * rng.uniform(-1, 1, n)).astype(np.float32)
+    return w.astype(np.float64)
+
+
+def test_word_ops_bit_exact(mw, orc):
+    rng = np.random.default_rng(61)
+    n = 5000
+    a, b = rand_qqf(rng, n), rand_qqf(rng, n)
+    b[:, :7] = 0.0
+    b[0, :7] = [1.0, -1.0, 2.0 ** -60, 3.0, 0.5, 2.0 ** 60, 1.5]
+    for op in ("add", "mul", "div"):
+        g = mw.word_op(op, "qqf", dev(a, np.float32), dev(b, np.float32)).cpu().numpy()
+        assert g.dtype == np.float32 and g.shape == (4, n)
+        assert same_bits(g, getattr(orc, op)("qqf", a, b)), op
+    g = mw.word_op("normalize", "qqf", dev(a, np.float32)).cpu().numpy()
+    assert same_bits(g, orc.normalize("qqf", a))
+    g = mw.word_op("collapse", "qqf", dev(a, np.float32)).cpu().numpy()
+    assert same_bits(g, orc.collapse("qqf", a))
+    # FP64 x QQF over the split's fast range, its edges and the rounding path.
+    s = rng.uniform(1, 2, n) * rng.choice([-1, 1], n) * 2.0 ** rng.integers(-100, 128, n)
+    s[:12] = [0.0, -0.0, 5e-310, -3.3e-320, 2.0 ** -97, -2.0 ** -97 * 1.75, 2.0 ** -98, 1.3 * 2.0 ** -100,
+              -7.1e-35, 2.0 ** 127 * 1.999, 1.0, -1.0]
+    g = mw.word_op("dxmul", "qqf", dev(s), dev(b, np.float32)).cpu().numpy()
+    assert same_bits(g, orc.dxmul("qqf", s, b))
+
+
+def test_spmv_and_dot(mw, orc):
+    rng = np.random.default_rng(62)
+    for A, plan in ((P.power_law_laplacian(4000, seed=3, mean_deg=12, max_deg=300), None),
+                    (P.laplacian_3d(16, 1e-3), (2, 256, 37))):
+        M = mw.CSRMatrix.from_csr(A)
+        if plan:
+            M.plan = plan
+        p = rand_qqf(rng, A.n, -3, 3)
+        q = mw.spmv(M, "qqf", dev(p, np.float32)).cpu().numpy()
+        assert same_bits(q, orc.spmv("qqf", A, p, V=M.plan[0])), A.name
+    u, v = rand_qqf(rng, 70001, -4, 4), rand_qqf(rng, 70001, -4, 4)
+    for G in (1, 37, 456):
+        g = mw.dot("qqf", dev(u, np.float32), dev(v, np.float32), G)
+        assert same_bits(g, orc.dot("qqf", u, v, R=256, G=G)), G
+
+
+def _check(mw, orc, M, A, b, tol, maxit, tag, x0=None):
+    r = mw.solve(M, dev(b), "qqf", tol, maxit, history=True, x0=None if x0 is None else dev(x0, np.float32))
+    xo, ito, rro, sto, ho = orc.cg("qqf", A, b, x0=x0, tol=tol, maxit=maxit, plan=M.plan, history=True)
+    assert (r.iters, r.status) == (ito, sto), (tag, r.iters, ito, r.status, sto)
+    assert same_bits(np.array([r.relres]), np.array([rro])), (tag, r.relres, rro)
+    assert r.x.dtype.is_floating_point and r.x.shape == (4, A.n)
+    assert same_bits(r.x.cpu().numpy(), xo), tag
+    if r.iters:
+        assert same_bits(r.history.cpu().numpy(), ho), tag
+    return r
+
+
+def test_cg_graph_path(mw, orc):
+    for A, seed, tol, maxit in ((P.laplacian_3d(24, 1e-3), 71, 1e-22, 300),
+                                (P.diffusion_2d(90, 3), 72, 1e-20, 800),
+                                (P.power_law_laplacian(5000, seed=7, mean_deg=12, max_deg=300), 73, 1e-20, 300)):
+        b = P.rhs_uniform(A.n, seed)
+        M = mw.CSRMatrix.from_csr(A)
+        r = _check(mw, orc, M, A, b, tol, maxit, A.name)
+        assert r.iters > 20
+        M.plan = (2, 256, 37)
+        _check(mw, orc, M, A, b, tol, maxit, A.name + " V=2")
+
+
+def test_eager_launches(mw, orc, monkeypatch):
+    monkeypatch.setenv("MWCG_EAGER", "1")
+    A = P.diffusion_2d(60, 4)
+    b = P.rhs_uniform(A.n, 74)
+    M = mw.CSRMatrix.from_csr(A)
+    _check(mw, orc, M, A, b, 1e-20, 400, "eager")
+
+
+def test_small_systems_run_the_graph(mw, orc):
+    """Systems small enough for the one-cluster launch of the other arithmetics."""
+    for A in (P.laplacian_2d(40), P.laplacian_2d(5), P.random_spd_small(9, seed=3)):
+        b = P.rhs_uniform(A.n, 75)
+        M = mw.CSRMatrix.from_csr(A)
+        _check(mw, orc, M, A, b, 1e-22, 400, A.name)
+
+
+def test_scaling_far_outside_fp32_range(mw, orc):
+    """b 2^k with |k| > 126: E0 takes the FP64 route of the word scaling;
+    the iterations, residuals and history equal the unscaled problem's."""
+    A = P.laplacian_3d(20, 1e-3)
+    b = P.rhs_uniform(A.n, 76)
+    M = mw.CSRMatrix.from_csr(A)
+    r0 = _check(mw, orc, M, A, b, 1e-22, 300, "k=0")
+    for k in (-300, 300, -40, 90):
+        r = _check(mw, orc, M, A, b * 2.0 ** k, 1e-22, 300, f"k={k}")
+        assert (r.iters, r.relres) == (r0.iters, r0.relres), k
+        assert same_bits(r.history.cpu().numpy(), r0.history.cpu().numpy()), k
+
+
+def test_nonzero_x0_and_limits(mw, orc):
+    A = P.diffusion_2d(50, 6)
+    b = P.rhs_uniform(A.n, 77)
+    M = mw.CSRMatrix.from_csr(A)
+    rng = np.random.default_rng(78)
+    x0 = rand_qqf(rng, A.n, -2, 2)
+    _check(mw, orc, M, A, b, 1e-20, 500, "x0", x0=x0)
+    _check(mw, orc, M, A, b, 1e-300, 7, "maxit")
+    _check(mw, orc, M, A, b, 0.0, 3, "tol 0")
+
+
+def test_special_cases(mw, orc):
+    A = P.laplacian_2d(30)
+    M = mw.CSRMatrix.from_csr(A)
+    r = mw.solve(M, dev(np.zeros(A.n)), "qqf", 1e-10, 50, x0=dev(np.ones((4, A.n)), np.float32))
+    assert (r.iters, r.status, r.relres) == (0, 0, 0.0) and np.all(r.x.cpu().numpy() == 0)
+    b = P.matvec_exact(A, np.ones(A.n))
+    x0 = np.zeros((4, A.n))
+    x0[0] = 1.0
+    r = mw.solve(M, dev(b), "qqf", 1e-10, 50, x0=dev(x0, np.float32))       # r0 = 0 exactly
+    assert (r.iters, r.status, r.relres) == (0, 0, 0.0) and np.array_equal(r.x.cpu().numpy(), x0)
+    r = mw.solve(M, dev(b), "qqf", 1e-10, 0)
+    xo, ito, rro, sto = orc.cg("qqf", A, b, tol=1e-10, maxit=0, plan=M.plan)
+    assert (r.iters, r.status) == (ito, sto) == (0, 1) and r.relres == rro
+    one = P.CSR(1, np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([3.0]))
+    M1 = mw.CSRMatrix.from_csr(one)
+    _check(mw, orc, M1, one, np.array([1.0]), 1e-30, 5, "n=1")
+
+
+def test_host_buffers(mw, orc):
+    A = P.diffusion_2d(40, 8)
+    b = P.rhs_uniform(A.n, 79)
+    M = mw.CSRMatrix.from_csr(A)
+    x, it, rr, st = mw.solve_host(M, b, "qqf", 1e-20, 400)
+    xo, ito, rro, sto = orc.cg("qqf", A, b, tol=1e-20, maxit=400, plan=M.plan)
+    assert (it, st) == (ito, sto) and x.dtype == np.float32 and same_bits(x, xo)
+
+
+def test_unsupported_paths_rejected(mw):
+    import torch
+    from paper_2510_13536_gb300._capi import MWCGError
+    A = P.laplacian_2d(20)
+    M = mw.CSRMatrix.from_csr(A)
+    b = dev(P.rhs_uniform(A.n, 80))
+    with pytest.raises(MWCGError):
+        mw.solve_bicgstab(M, b, "qqf", 1e-10, 10)
+    with pytest.raises(MWCGError):
+        mw.solve_batched([M], [b], "qqf", 1e-10, 10)
+    with pytest.raises(MWCGError):
+        mw.adjoint(M, torch.zeros((2, A.n), dtype=torch.float64, device="cuda"), b, "qqf", 1e-10, 10)
+    M.preconditioner = "jacobi"
+    with pytest.raises(MWCGError):
+        mw.solve(M, b, "qqf", 1e-10, 10)
+    M.preconditioner = "none"
+    assert mw.solve(M, b, "qqf", 1e-10, 200).status == 0
