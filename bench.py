@@ -820,7 +820,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mwcg", choices=["mwcg", "reference"])
     ap.add_argument("--arith", default="qtw", choices=["qtw", "dw", "qdw", "tw", "fp64", "qdw_nn", "qtw_nn", "qw", "qqw",
-                                                       "qqw_nn"])
+                                                       "qqw_nn", "qqf"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no DW, profile, e2e or CPU legs); used for ncu captures")

@@ -43,6 +43,7 @@ int small_cluster_size() {
   if (g_small_cluster[dev]) return g_small_cluster[dev];
   int best = mwb::kCluster;
   const void* kern = mwb::kernel_00();
+  cudaFree(nullptr);          // the context exists before the attribute calls (see capi.cu)
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mwb::kPadSmem) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <set>
 #include <string>
@@ -92,9 +93,24 @@ constexpr int kMaxG = 1024;
 // need the default 48 KB).
 size_t red_smem(int G, int w) { return (size_t)G * (8 * w + 20); }
 
+// Creates the CUDA context with an ordinary runtime call before the kernel
+// tables' one-time set-up.  Observed on GB300 (driver 580): when a
+// cudaFuncSetAttribute inside that std::call_once was the first call of the
+// process to touch the context, the driver crashed the process (SIGSEGV in
+// cuKernelGetFunction); with the context created first it never did.
+void init_runtime() {
+  static std::atomic<int> done{0};
+  if (!done.load(std::memory_order_acquire)) {
+    cudaFree(nullptr);
+    cudaGetLastError();
+    done.store(1, std::memory_order_release);
+  }
+}
+
 const mwk::KernelTable* table(int arith) {
   static mwk::KernelTable t[kNArith];
   static std::once_flag once;
+  init_runtime();
   std::call_once(once, [] {
     t[0] = mwk::table_fp64();
     t[1] = mwk::table_dw();
@@ -120,6 +136,7 @@ const mwk::KernelTable* table(int arith) {
 const mwk::BiTable* bitable(int arith) {
   static mwk::BiTable t[kNArith];
   static std::once_flag once;
+  init_runtime();
   std::call_once(once, [] {
     t[0] = mwk::bitable_fp64();
     t[1] = mwk::bitable_dw();
