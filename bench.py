@@ -736,10 +736,13 @@ def run_gpu(args):
                                                   ctypes.c_void_p(x.data_ptr()), mw.arith_id(arith), 30,
                                                   ctypes.c_void_p(stream.cuda_stream), kms))
     spmv_ms = kms[0]
-    per_nnz, per_row = SPMV_OPS[arith]
+    fp32 = arith == "qqf"                 # FP32 words: the FP32 pipe, 16 bytes per element
+    elem = 16 if fp32 else 8 * w
+    per_nnz, per_row = QQF_SPMV_OPS if fp32 else SPMV_OPS[arith]
     ops = per_nnz * A.nnz + per_row * A.n
     achieved = ops / (spmv_ms * 1e-3)
-    spmv_bytes = 12 * A.nnz + 8 * (A.n + 1) + 2 * 8 * w * A.n
+    peak_ops = FP32_PEAK_OPS if fp32 else FP64_PEAK_OPS
+    spmv_bytes = 12 * A.nnz + 8 * (A.n + 1) + 2 * elem * A.n
     traffic = _profiled_traffic(arith)
 
     # FP64 / integer pipe rates measured now on this GPU (roofline context).
@@ -756,7 +759,7 @@ def run_gpu(args):
     # End to end through the C ABI with host buffers (pinned), copies included.
     bh = torch.empty(A.n, dtype=torch.float64, pin_memory=True)
     bh.copy_(torch.as_tensor(b_np))
-    xh = torch.zeros((w, A.n), dtype=torch.float64, pin_memory=True)
+    xh = torch.zeros((w, A.n), dtype=torch.float32 if fp32 else torch.float64, pin_memory=True)
     e2e_s = []
     for _ in range(2):
         xh.zero_()
@@ -764,8 +767,8 @@ def run_gpu(args):
         t0 = time.perf_counter()
         _xh, ith, rrh, sth = mw.solve_host(M, bh.numpy(), arith, tol, maxit, x0=xh.numpy())
         e2e_s.append(time.perf_counter() - t0)
-    e2e = {"value": min(e2e_s), "unit": "s", "h2d_bytes_per_step": 8 * A.n + 8 * w * A.n,
-           "d2h_bytes_per_step": 8 * w * A.n + 160}
+    e2e = {"value": min(e2e_s), "unit": "s", "h2d_bytes_per_step": 8 * A.n + elem * A.n,
+           "d2h_bytes_per_step": elem * A.n + 160}
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only).
     cpu = None
@@ -778,7 +781,7 @@ def run_gpu(args):
                "sample": f"2 CG iterations + init of the full system, single thread, scaled to {tot} iterations "
                          f"({src}); {per_it:.3f} s per iteration"}
 
-    alg_bytes_iter = 12 * A.nnz + 8 * (A.n + 1) + 88 * w * A.n
+    alg_bytes_iter = 12 * A.nnz + 8 * (A.n + 1) + 11 * elem * A.n
     out = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -794,12 +797,14 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": args.steps * (3 + 3 * it),
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_OPS / 1e12,
-                     "unit": "TFLOP64-op/s (FMA = 1)", "frac": achieved / FP64_PEAK_OPS, "traffic": traffic,
-                     "kernel": "k_spmv<QTW> (SpMV + p^T q + alpha)", "ops_per_launch": ops,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": ("TFLOP32-op/s (FMA = 1)" if fp32 else "TFLOP64-op/s (FMA = 1)"),
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "kernel": f"k_spmv<{arith.upper()}> (SpMV + p^T q + alpha)", "ops_per_launch": ops,
                      "alg_bytes_per_launch": spmv_bytes,
                      "hbm_frac_of_measured": spmv_bytes / (spmv_ms * 1e-3) / 6691.8e9,
-                     "peak_source": "2 FP64 op/clk/SM x 152 SMs x 2070 MHz (derived; probe below measures it)",
+                     "peak_source": ("128 FP32 op/clk/SM x 152 SMs x 2070 MHz (derived)" if fp32 else
+                                     "2 FP64 op/clk/SM x 152 SMs x 2070 MHz (derived; probe below measures it)"),
                      "probe_measured_now": probe,
                      # frac counts the paper's operations, part of which the integer pipe
                      # executes; the FP64 pipe's own busy fraction comes from ncu.

@@ -48,6 +48,7 @@ KernelTable table_qw();
 KernelTable table_qqw();
 KernelTable table_qqw_nn();
 KernelTable table_qqf();
+const void* qqf_init_pre();   // QQF: ||b|| and the first scale, before its init
 BiTable bitable_fp64();
 BiTable bitable_dw();
 BiTable bitable_qdw();
@@ -124,14 +125,17 @@ const mwk::KernelTable* table(int arith) {
     t[9] = mwk::table_qqw_nn();
     t[10] = mwk::table_qqf();
     for (auto& k : t)
-      for (const void* f : {k.init_pre, k.spmv, k.spmv_pol, k.init, k.init_pcg, k.update, k.update_pol,
-                            k.update_pcg, k.update_pcg_pol, k.dot})
+      for (const void* f : {k.spmv, k.spmv_pol, k.init, k.init_pcg, k.update, k.update_pol, k.update_pcg,
+                            k.update_pcg_pol, k.dot})
         if (f) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
     cudaGetLastError();
   });
   if (arith < 0 || arith >= kNArith) return nullptr;
   return &t[arith];
 }
+
+// Kernel run between the x0 SpMV and the init, or null (QQF only).
+const void* init_pre(int arith) { return arith == MWCG_QQF ? mwk::qqf_init_pre() : nullptr; }
 
 const mwk::BiTable* bitable(int arith) {
   static mwk::BiTable t[kNArith];
@@ -381,8 +385,9 @@ int ensure_graph(mwcg_csr* A, int arith) {
   int rc;
   const int mode0 = 0, mode1 = 1;
   cudaGraphNode_t npre = nullptr;
+  const void* pre = init_pre(arith);
   if ((rc = add_kernel(&n0, g, nullptr, 0, kt->spmv, G, smem, M, W, mode0)) ||
-      (kt->init_pre && (rc = add_kernel(&npre, g, &n0, 1, kt->init_pre, G, smem, M, W))) ||
+      (pre && (rc = add_kernel(&npre, g, &n0, 1, pre, G, smem, M, W))) ||
       (rc = add_kernel(&n1, g, npre ? &npre : &n0, 1, lk.init, G, smem, M, W)) ||
       (rc = add_kernel(&n2, g, &n1, 1, kt->zero_x, G, 0, M, W))) {
     cudaGraphDestroy(g);
@@ -466,7 +471,7 @@ int run_eager(mwcg_csr* A, int arith, cudaStream_t s) {
   void* a_mw[] = {(void*)&M, (void*)&W};
   const LoopKernels lk = loop_kernels(A, kt);
   CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
-  if (kt->init_pre) CK(cudaLaunchKernel(kt->init_pre, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
+  if (const void* pre = init_pre(arith)) CK(cudaLaunchKernel(pre, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(lk.init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
   mwk::DevState* h = A->h_st;
@@ -1055,7 +1060,7 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   void* a_mw[] = {(void*)&M, (void*)&W};
   const LoopKernels lk = loop_kernels(A, kt);
   CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
-  if (kt->init_pre) CK(cudaLaunchKernel(kt->init_pre, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
+  if (const void* pre = init_pre(arith)) CK(cudaLaunchKernel(pre, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(lk.init, dim3(G), dim3(mwk::TPB), a_mw, smem, s));
   CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_mw, 0, s));
   std::vector<cudaEvent_t> ev(3 * (size_t)niters + 1);

@@ -3,7 +3,7 @@
 // FP32's exponent stops at 2^-126 (2^-149 subnormal): the lower words of a
 // residual near 1e-14 |b|, and of the squares in r^T r, would underflow.  The
 // solver therefore keeps r = 2^E r~ and p = 2^E p~ with one integer exponent
-// E (DevState qe) chosen so that r~ has a root mean square near one; x is
+// E chosen so that r~ has a root mean square near one; x is
 // unscaled.  With rho~ = r~^T r~, pi~ = p~^T q~ and q~ = A p~ (Algorithm 1
 // rewritten for the scaled vectors):
 //   alpha~ = rho~ / pi~                       (k_spmv, unchanged)
@@ -19,12 +19,41 @@
 // correctly rounded multiplication by a power of two.
 //
 // The kernels keep the plan's summation order (the vector kernels' tiles of
-// TPB rows over G blocks) and the stop tests of cg_kernels.cuh.
+// TPB rows over G blocks) and the stop tests of cg_kernels.cuh.  QQF runs no
+// BiCGStab, so E, the shift applied by this iteration's update and the shift
+// the next update applies are kept in the DevState's BiCGStab slot omega[0..2]
+// (small integers, exact as doubles).
 #pragma once
 #include "cg_kernels.cuh"
 #include "mw_float.cuh"
 
 namespace mwk {
+
+// Packed storage of QQF vectors: slot k of element i, at k n + i, holds words
+// 2k and 2k+1 as a float2 (explicit specialisations of cg_kernels.cuh's
+// loads and stores, so every generic kernel reads and writes the packed form).
+template <>
+__device__ __forceinline__ mw::QQF::T ld<mw::QQF>(const double* __restrict__ v, int64_t n, int64_t i) {
+  const float2* __restrict__ f = reinterpret_cast<const float2*>(v);
+  const float2 u0 = f[i], u1 = f[n + i];
+  return mw::QQF::T{{u0.x, u0.y, u1.x, u1.y}};
+}
+template <>
+__device__ __forceinline__ void st<mw::QQF>(double* __restrict__ v, int64_t n, int64_t i, const mw::QQF::T& t) {
+  float2* __restrict__ f = reinterpret_cast<float2*>(v);
+  f[i] = make_float2(t.w[0], t.w[1]);
+  f[n + i] = make_float2(t.w[2], t.w[3]);
+}
+constexpr int kQqfSlots = 2;          // 8-byte slots per element
+
+__device__ __forceinline__ int qqf_E(const DevState* S) { return (int)S->omega[0]; }
+__device__ __forceinline__ int qqf_shift(const DevState* S) { return (int)S->omega[1]; }
+__device__ __forceinline__ int qqf_next_shift(const DevState* S) { return (int)S->omega[2]; }
+__device__ __forceinline__ void qqf_set_scale(DevState* S, int E, int s, int s_next) {
+  S->omega[0] = (double)E;
+  S->omega[1] = (double)s;
+  S->omega[2] = (double)s_next;
+}
 
 // ilogb of a positive finite FP64 value, from the bits.
 __device__ __forceinline__ int ilogb_pos(double c) {
@@ -75,7 +104,7 @@ __global__ void __launch_bounds__(TPB) k_qqf_bnorm(Csr M, Work W) {
     S->counter = 0;
     const double bb = ptot ? tot.w[0] : 0.0;
     S->bnorm = __dsqrt_rn(bb);
-    S->qe = scale_exp(bb, n);
+    qqf_set_scale(S, scale_exp(bb, n), 0, 0);
   }
 }
 
@@ -87,7 +116,7 @@ __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
   DevState* S = W.st;
   const int64_t n = M.n;
   const double* __restrict__ b = S->b;
-  const int E = S->qe;
+  const int E = qqf_E(S);
   const double sb = mw::pow2d(-E);
   const int64_t ntiles = (n + TPB - 1) / TPB;
   T acc = A::zero();
@@ -134,8 +163,7 @@ __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
         S->done = 1;
       }
     }
-    S->qs = 0;
-    S->qs_next = clamp_shift(scale_exp(A::collapse(rho), n), E);
+    qqf_set_scale(S, E, 0, clamp_shift(scale_exp(A::collapse(rho), n), E));
   }
 }
 
@@ -151,7 +179,7 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
   }
   const int64_t n = M.n;
   double* __restrict__ x = S->x;
-  const int E = S->qe, s = S->qs_next;
+  const int E = qqf_E(S), s = qqf_next_shift(S);
   const T al = load_scalar_f<A>(S->alpha);
   const T cx = A::scale(al, E);
   const T mal = A::neg(al);
@@ -203,9 +231,7 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
       for (int k = 0; k < A::W; ++k) { S->beta[k] = be.w[k]; S->rho[k] = tot.w[k]; }
       cont = 1;
     }
-    S->qe = En;
-    S->qs = s;
-    S->qs_next = clamp_shift(scale_exp(c, n), En);
+    qqf_set_scale(S, En, s, clamp_shift(scale_exp(c, n), En));
     set_cond(W, cont);
   }
 }
@@ -217,7 +243,7 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_pupdate(Csr M, Work W) {
   DevState* S = W.st;
   if (S->done) return;
   const int64_t n = M.n;
-  const T cp = A::scale(load_scalar_f<A>(S->beta), S->qs);
+  const T cp = A::scale(load_scalar_f<A>(S->beta), qqf_shift(S));
   const int64_t stride = (int64_t)gridDim.x * TPB;
   for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride)
     st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), cp, ld<A>(W.p, n, i)));
@@ -225,11 +251,11 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_pupdate(Csr M, Work W) {
 
 // The QQF kernel table: plain CG only (no normalisation policy, no
 // preconditioner, no adjoint gradient kernel); vectors of two 8-byte slots.
+// Its init is preceded by k_qqf_bnorm (qqf_init_pre in inst_qqf.cu).
 inline KernelTable make_table_qqf() {
   using A = mw::QQF;
   KernelTable t{};
-  t.words = slots<A>();
-  t.init_pre = (const void*)&k_qqf_bnorm<A>;
+  t.words = kQqfSlots;
   t.spmv = (const void*)&k_spmv<A>;
   t.spmv_pol = t.spmv;
   t.init = (const void*)&k_qqf_init<A>;
@@ -238,7 +264,7 @@ inline KernelTable make_table_qqf() {
   t.update_pol = t.update;
   t.pupdate_pol = t.pupdate;
   t.init_pcg = t.update_pcg = t.pupdate_pcg = t.update_pcg_pol = t.pupdate_pcg_pol = nullptr;
-  t.zero_x = (const void*)&k_zero_x<slots<A>()>;
+  t.zero_x = (const void*)&k_zero_x<kQqfSlots>;
   t.grad_values = nullptr;
   t.collapse = (const void*)&k_collapse<A>;
   t.dot = (const void*)&k_dot<A>;

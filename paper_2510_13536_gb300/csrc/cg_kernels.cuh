@@ -27,7 +27,6 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
-#include <type_traits>
 #include "mw_device.cuh"
 
 namespace mwk {
@@ -69,10 +68,6 @@ struct DevState {
   double omega[4];          // BiCGStab: omega
   int32_t early;            // BiCGStab: ||s|| met the tolerance (x += alpha p ends the solve)
   int32_t pad1;
-  int32_t qe;               // QQF: r = 2^qe r~, p = 2^qe p~ (power-of-two scaling)
-  int32_t qs;               // QQF: the shift applied to r~ by this iteration's update
-  int32_t qs_next;          // QQF: the shift the next update applies
-  int32_t pad2;
 };
 
 // Normalisation places (an extension of Sec. IV-D, which normalises r after
@@ -111,39 +106,17 @@ struct Work {
   const double* w;          // Jacobi weights fl(1/a_ii) (preconditioned CG), else null
 };
 
-// Arithmetics with FP32 words (A::PACKED) store two words per 8-byte slot:
-// slot k of element i, at k n + i, holds words 2k and 2k+1 as a float2.
-template <class A, class = void> struct Packed { static constexpr bool value = false; };
-template <class A> struct Packed<A, std::void_t<decltype(A::PACKED)>> { static constexpr bool value = A::PACKED; };
-template <class A> constexpr int slots() { return Packed<A>::value ? A::W / 2 : A::W; }
-
 template <class A>
 __device__ __forceinline__ typename A::T ld(const double* __restrict__ v, int64_t n, int64_t i) {
   typename A::T t;
-  if constexpr (Packed<A>::value) {
-    const float2* __restrict__ f = reinterpret_cast<const float2*>(v);
 #pragma unroll
-    for (int k = 0; k < A::W / 2; ++k) {
-      const float2 u = f[k * n + i];
-      t.w[2 * k] = u.x;
-      t.w[2 * k + 1] = u.y;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < A::W; ++k) t.w[k] = v[k * n + i];
-  }
+  for (int k = 0; k < A::W; ++k) t.w[k] = v[k * n + i];
   return t;
 }
 template <class A>
 __device__ __forceinline__ void st(double* __restrict__ v, int64_t n, int64_t i, const typename A::T& t) {
-  if constexpr (Packed<A>::value) {
-    float2* __restrict__ f = reinterpret_cast<float2*>(v);
 #pragma unroll
-    for (int k = 0; k < A::W / 2; ++k) f[k * n + i] = make_float2(t.w[2 * k], t.w[2 * k + 1]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < A::W; ++k) v[k * n + i] = t.w[k];
-  }
+  for (int k = 0; k < A::W; ++k) v[k * n + i] = t.w[k];
 }
 template <class A>
 __device__ __forceinline__ typename A::T shfl_down(const typename A::T& v, int off) {
@@ -894,8 +867,7 @@ __global__ void __launch_bounds__(TPB) k_word_op(int op, int64_t n, const double
 
 // Kernel table of one arithmetic, used by the host runtime.
 struct KernelTable {
-  int words;                // 8-byte slots per element of a vector
-  const void* init_pre;     // run before init when set (QQF: ||b|| and the first scale)
+  int words;
   const void* spmv;
   const void* spmv_pol;     // the three loop kernels under a non-default normalisation policy
   const void* update_pol;
@@ -921,7 +893,6 @@ template <class A, class AS = A>
 KernelTable make_table() {
   KernelTable t;
   t.words = A::W;
-  t.init_pre = nullptr;
   t.spmv = (const void*)&k_spmv<AS>;
   t.init_pcg = (const void*)&k_init<A, true>;
   t.update_pcg = (const void*)&k_update<A, false, true>;

@@ -3,4 +3,5 @@
 
 namespace mwk {
 KernelTable table_qqf() { return make_table_qqf(); }
+const void* qqf_init_pre() { return (const void*)&k_qqf_bnorm<mw::QQF>; }
 }  // namespace mwk

@@ -76,3 +76,6 @@ def test_null_arguments_rejected(lib):
     assert lib.mwcg_word_op(9, 4, 10, None, None, None, None) == -1
     assert lib.mwcg_dot(4, 10, None, None, 0, None, None) == -1
     assert lib.mwcg_collapse(None, 4, 10, None, None) == -1
+    out = (ctypes.c_double * 4)()
+    assert lib.mwcg_dot_noalloc(10, 10, None, None, 1, None, out) == -1      # QQF has no no-alloc dot
+    assert b"unknown arithmetic" in lib.mwcg_last_error()
