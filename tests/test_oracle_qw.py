@@ -1,4 +1,4 @@
-"""Pins of the oracle's four-word arithmetics (SURVEY rank-3 extension).
+"""Pins of the oracle's four-word arithmetics QW and QQW (an extension; Sec. I lists both).
 
 The paper lists QW (Hida et al.) and QQW (Ozaki and Imamura) among the
 multi-word arithmetics (Sec. I) but evaluates neither and prints no
