@@ -56,10 +56,11 @@ extern "C" {
  * and p scaled by a power of two 2^E so that FP32's exponent range follows
  * the shrinking residual (x is unscaled, so its values must lie within
  * FP32's range, |x_i| >= 2^-54 or so for full precision).  QQF supports
- * mwcg_solve, mwcg_solve_history, mwcg_solve_host, mwcg_spmv, mwcg_dot and
- * mwcg_word_op; the normalisation policy does not apply to it (r is
- * normalised every iteration), and the preconditioner, BiCGStab, the
- * adjoint, the batched solve and mwcg_dot_noalloc return MWCG_ERR_ARG. */
+ * mwcg_solve, mwcg_solve_history, mwcg_solve_host, mwcg_spmv, mwcg_dot,
+ * mwcg_word_op (op 5 collapses its words to FP64) and mwcg_profile_kernels;
+ * the normalisation policy does not apply to it (r is normalised every
+ * iteration), and the preconditioner, BiCGStab, the adjoint, the batched
+ * solve and mwcg_dot_noalloc return MWCG_ERR_ARG. */
 typedef enum {
   MWCG_FP64 = 0,
   MWCG_DW = 1,
