@@ -37,21 +37,29 @@ def words(arith) -> int:
 
 def _pack(x: torch.Tensor, n: int) -> torch.Tensor:
     """(4, n) FP32 words -> the C ABI's (2, n) slots (words 2k, 2k+1 in slot k)."""
+    if n == 0:
+        return torch.empty((2, 0), dtype=torch.float64, device=x.device)
     f = x.to(torch.float32).reshape(2, 2, n).permute(0, 2, 1).contiguous()
     return f.view(torch.float64).reshape(2, n).contiguous()
 
 
 def _unpack(x: torch.Tensor, n: int) -> torch.Tensor:
     """The C ABI's (2, n) slots -> (4, n) FP32 words."""
+    if n == 0:
+        return torch.empty((4, 0), dtype=torch.float32, device=x.device)
     return x.contiguous().view(torch.float32).reshape(2, n, 2).permute(0, 2, 1).reshape(4, n).contiguous()
 
 
 def _pack_np(x: np.ndarray, n: int) -> np.ndarray:
+    if n == 0:
+        return np.empty((2, 0))
     f = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(2, 2, n).transpose(0, 2, 1))
     return f.view(np.float64).reshape(2, n).copy()
 
 
 def _unpack_np(x: np.ndarray, n: int) -> np.ndarray:
+    if n == 0:
+        return np.empty((4, 0), dtype=np.float32)
     return np.ascontiguousarray(x.view(np.float32).reshape(2, n, 2).transpose(0, 2, 1).reshape(4, n))
 
 

@@ -43,3 +43,10 @@ def test_abi_conversion_per_arithmetic():
         y = torch.ones((_capi.WORDS[a], n), dtype=torch.float64)
         assert solver._to_abi(a, y, n).data_ptr() == y.data_ptr()       # no copy for FP64 words
         assert solver._from_abi(a, y, n) is y
+
+
+def test_empty_vectors():
+    assert solver._pack(torch.zeros((4, 0), dtype=torch.float32), 0).shape == (2, 0)
+    assert solver._unpack(torch.zeros((2, 0), dtype=torch.float64), 0).shape == (4, 0)
+    assert solver._pack_np(np.zeros((4, 0), dtype=np.float32), 0).shape == (2, 0)
+    assert solver._unpack_np(np.zeros((2, 0)), 0).shape == (4, 0)

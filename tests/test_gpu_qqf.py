@@ -166,6 +166,9 @@ def test_special_cases(mw, orc):
     one = P.CSR(1, np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([3.0]))
     M1 = mw.CSRMatrix.from_csr(one)
     _check(mw, orc, M1, one, np.array([1.0]), 1e-30, 5, "n=1")
+    E = P.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    r = mw.solve(mw.CSRMatrix.from_csr(E), dev(np.zeros(0)), "qqf", 1e-10, 10)
+    assert (r.iters, r.status, r.relres) == (0, 0, 0.0) and tuple(r.x.shape) == (4, 0)
 
 
 def test_host_buffers(mw, orc):
