@@ -69,7 +69,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if os.environ.get("MWCG_QTS_INT") == "1":
         extra.append("-DMWCG_QTS_INT=1")
     for key in ("MWCG_QTW_P_SPMV", "MWCG_QTW_P_VEC", "MWCG_DW_P_SPMV", "MWCG_DW_P_VEC", "MWCG_QDW_P_SPMV",
-                "MWCG_QDW_P_VEC", "MWCG_TW_P", "MWCG_ILP_FP64", "MWCG_ILP_MW", "MWCG_CHUNK_FP64", "MWCG_ILP_SPMV_MW", "MWCG_MINB_MW", "MWCG_MINB_FP64"):
+                "MWCG_QDW_P_VEC", "MWCG_TW_P", "MWCG_ILP_FP64", "MWCG_ILP_MW", "MWCG_CHUNK_FP64", "MWCG_ILP_SPMV_MW", "MWCG_MINB_MW", "MWCG_MINB_FP64",
+                "MWCG_ILP_SPMV_QQF"):
         if os.environ.get(key, "").isdigit():
             extra.append(f"-D{key}={os.environ[key]}")
     if os.environ.get("MWCG_ADD_FMA") in ("1", "2"):

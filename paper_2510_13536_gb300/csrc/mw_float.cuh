@@ -83,10 +83,14 @@ __device__ __forceinline__ void split3(double a, float& a0, float& a1, float& a2
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
 __device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
 
+#ifndef MWCG_ILP_SPMV_QQF
+#define MWCG_ILP_SPMV_QQF 1        // rows per thread in flight in the SpMV (same summation order)
+#endif
+
 struct QQF {
   static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
-  static constexpr int ILP_SPMV = 1;
+  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_QQF;
   static constexpr int MINB = 3;
   static constexpr int W = 4;
   static constexpr bool QUASI = true;
