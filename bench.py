@@ -445,6 +445,12 @@ def run_qqf(torch, mw, P, cpu):
         fe.append({"arith": ar, "tol": tl, "iters": r.iters, "status": r.status, "time_s": ms / 1e3,
                    "forward_error": _forward_error(x, xs)})
     out["exact_solution_twin"] = {"workload": P.NORM_SYSTEMS["norm_poisson"], "runs": fe}
+    if cpu:                               # the oracle on a bounded sample of the same QQF solve
+        it_q = next(r["iters"] for r in out["runs"] if r["arith"] == "qqf")
+        est, per_it, _init = oracle_sample(A, b, "qqf", 2, it_q, M.plan)
+        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+                               "sample": f"2 QQF CG iterations + init of the full system, single thread, "
+                                         f"scaled to {it_q} iterations; {per_it:.3f} s per iteration"}
     return out
 
 
