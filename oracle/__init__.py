@@ -18,9 +18,9 @@ _SRC = os.path.join(_HERE, "mwcg_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 ARITHS = {"fp64": 0, "dw": 1, "qdw": 2, "tw": 3, "qtw": 4, "qdw_nn": 5, "qtw_nn": 6, "qw": 7, "qqw": 8, "qqw_nn": 9,
-          "qqf": 10}
-# Words per element; QQF's four words are FP32 values, held here as float64.
-WORDS = {0: 1, 1: 2, 2: 2, 3: 3, 4: 3, 5: 2, 6: 3, 7: 4, 8: 4, 9: 4, 10: 4}
+          "qqf": 10, "qf": 11}
+# Words per element; QQF's and QF's four words are FP32 values, held here as float64.
+WORDS = {0: 1, 1: 2, 2: 2, 3: 3, 4: 3, 5: 2, 6: 3, 7: 4, 8: 4, 9: 4, 10: 4, 11: 4}
 STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "bad_preconditioner"}
 
 

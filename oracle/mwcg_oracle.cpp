@@ -14,10 +14,11 @@
 // Where the paper is silent the reading taken is stated at the function.
 // Extensions for the directions Sec. VI names: Jacobi-preconditioned CG,
 // BiCGStab, the four-word arithmetics QW / QQW (listed in Sec. I) and QQF,
-// four FP32 words (Sec. II, Sec. VI), with its power-of-two-scaled CG.
+// four FP32 words (Sec. II, Sec. VI), with its power-of-two-scaled CG, and
+// QF, QQF normalised after every operation.
 //
 // Parity unpinned against a cited source: TW (Fabiano et al.), QW (Hida et
-// al.), QQW (Ozaki and Imamura) and QQF -- the paper prints none of their
+// al.), QQW (Ozaki and Imamura), QQF and QF -- the paper prints none of their
 // sequences, so these are this project's restatements; their accuracy is
 // pinned in exact rationals by the tests.
 //
@@ -701,6 +702,29 @@ inline MWF<4> scale_words(const MWF<4>& a, int k) {
   return c;
 }
 
+// ---- QF: QQF with every addition and product followed by VecSum4 (an
+// extension; the non-quasi counterpart, as DW relates to QDW in Sec. III).
+// The quasi arithmetic's error is relative to its operands, so on strongly
+// cancelling SpMV rows QQF's ~96 bits leave about FP64's precision in the
+// result; renormalising every result keeps the words ordered.  Reading
+// (parity unpinned; accuracy pinned by the tests).
+struct QF {
+  static constexpr int W = 4;
+  using T = MWF<4>;
+  static T fix(T c) { QQF::renorm(c); return c; }
+  static T zero() { return QQF::zero(); }
+  static T from(double a) { return QQF::from(a); }
+  static T add(const T& a, const T& b) { return fix(QQF::add(a, b)); }
+  static T mul(const T& a, const T& b) { return fix(QQF::mul(a, b)); }
+  static T dxmul(double a, const T& b) { return fix(QQF::dxmul(a, b)); }
+  static T muladd(const T& acc, const T& a, const T& b) { return add(acc, mul(a, b)); }
+  static T dxmuladd(const T& acc, double a, const T& b) { return add(acc, dxmul(a, b)); }
+  static void renorm(T& a) { QQF::renorm(a); }
+  static void normalize(T& a) { QQF::renorm(a); }
+  static T div(const T& a, const T& b) { return QQF::div(a, b); }
+  static double collapse(const T& a) { return QQF::collapse(a); }
+};
+
 // ---------------------------------------------------------------------------
 // SoA vectors: word k of element i at v[k*n + i].
 // ---------------------------------------------------------------------------
@@ -995,10 +1019,12 @@ inline int clamp_shift(int t, int E) {
   return std::min(hi, std::max(lo, t));
 }
 
+// The same iteration serves QF (four FP32 words, normalised after every
+// operation); A is QQF or QF.
+template <class A>
 CGResult cg_qqf(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
                 const double* b, double* x, double tol, int maxit, Plan plan, double* hist) {
-  using A = QQF;
-  using T = A::T;
+  using T = typename A::T;
   const int W = A::W;
   const bool plain = plan.V <= 0;
   const int V = plain ? 1 : plan.V;
@@ -1299,7 +1325,7 @@ void grad_values(int64_t n, const int64_t* rp, const int32_t* col, const double*
 
 // Arithmetic dispatch: 0 FP64, 1 DW, 2 QDW, 3 TW, 4 QTW, 5 QDW-NN, 6 QTW-NN,
 // 7 QW, 8 QQW, 9 QQW-NN, 10 QQF (four FP32 words; the arrays hold FP32 values
-// as FP64).
+// as FP64), 11 QF (QQF normalised after every operation; no CUDA counterpart yet).
 template <template <class> class F, class... Args>
 int dispatch(int arith, Args... args) {
   switch (arith) {
@@ -1314,6 +1340,7 @@ int dispatch(int arith, Args... args) {
     case 8: return F<QQW>::run(args...);
     case 9: return F<QQW_NN>::run(args...);
     case 10: return F<QQF>::run(args...);
+    case 11: return F<QF>::run(args...);
   }
   return -1;
 }
@@ -1423,31 +1450,32 @@ template <class A> struct OpGrad {
   }
 };
 
-// QQF runs Algorithm 1 with the scaling of cg_qqf(); the policy, the
+// QQF and QF run Algorithm 1 with the scaling of cg_qqf(); the policy, the
 // preconditioned solver, BiCGStab and the adjoint's gradient are not defined
-// for it (status -2).
-template <> struct OpCG<QQF> {
+// for them (status -2).
+template <class A> struct OpCGScaled {
   static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
                  const double* b, double* x, double tol, int maxit, int V, int T, int G,
                  int* iters, double* relres, double* hist) {
-    CGResult r = cg_qqf(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist);
+    CGResult r = cg_qqf<A>(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist);
     *iters = r.iters;
     *relres = r.relres;
     return r.status;
   }
 };
-template <> struct OpCGNorm<QQF> {
+template <> struct OpCG<QQF> : OpCGScaled<QQF> {};
+template <> struct OpCG<QF> : OpCGScaled<QF> {};
+struct Unsupported {
   template <class... Args> static int run(Args...) { return -2; }
 };
-template <> struct OpPCG<QQF> {
-  template <class... Args> static int run(Args...) { return -2; }
-};
-template <> struct OpBiCG<QQF> {
-  template <class... Args> static int run(Args...) { return -2; }
-};
-template <> struct OpGrad<QQF> {
-  template <class... Args> static int run(Args...) { return -2; }
-};
+template <> struct OpCGNorm<QQF> : Unsupported {};
+template <> struct OpPCG<QQF> : Unsupported {};
+template <> struct OpBiCG<QQF> : Unsupported {};
+template <> struct OpGrad<QQF> : Unsupported {};
+template <> struct OpCGNorm<QF> : Unsupported {};
+template <> struct OpPCG<QF> : Unsupported {};
+template <> struct OpBiCG<QF> : Unsupported {};
+template <> struct OpGrad<QF> : Unsupported {};
 
 }  // namespace
 
@@ -1532,8 +1560,8 @@ int orc_grad_values(int arith, int64_t n, const int64_t* rp, const int32_t* col,
   return dispatch<OpGrad>(arith, n, rp, col, lam, x, g);
 }
 int orc_words(int arith) {
-  static const int w[11] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4, 4};
-  return (arith >= 0 && arith < 11) ? w[arith] : -1;
+  static const int w[12] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4, 4, 4};
+  return (arith >= 0 && arith < 12) ? w[arith] : -1;
 }
 
 }  // extern "C"
