@@ -21,17 +21,26 @@ ARITHS = {"fp64": 0, "dw": 1, "qdw": 2, "tw": 3, "qtw": 4, "qdw_nn": 5, "qtw_nn"
           "qqf": 10, "qf": 11}
 # Words per element; QQF's and QF's four words are FP32 values, held here as float64.
 WORDS = {0: 1, 1: 2, 2: 2, 3: 3, 4: 3, 5: 2, 6: 3, 7: 4, 8: 4, 9: 4, 10: 4, 11: 4}
-STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "bad_preconditioner"}
+STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "bad_preconditioner", 4: "out_of_range"}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (strict IEEE: no contraction, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle with g++ at -O3 (strict IEEE: no contraction, no
+    fast-math, so the optimiser may not reassociate or fuse any operation and
+    the results are those of the source's operation order).  No -march flag:
+    the same source builds on x86-64 and aarch64 hosts."""
+    flags = ["-std=c++17", "-O3", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    stamp = _LIB + ".cmd"                 # the flags the library was built with
+    try:
+        same_flags = open(stamp).read() == " ".join(flags)
+    except OSError:
+        same_flags = False
+    if force or not same_flags or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC]
-        subprocess.run(cmd, check=True)
+        subprocess.run(["g++", *flags, "-o", tmp, _SRC], check=True)
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(" ".join(flags))
     return _LIB
 
 

@@ -1007,8 +1007,15 @@ CGResult cg(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
 //  * The FP64 relative residual is 2^E sqrt(collapse(rho~)) / ||b||_2.
 //  * The normalisation policy is fixed at the default (r every iteration);
 //    everything else (stop tests, breakdown, zero b, zero r0, maxit) as cg().
-// x must lie within FP32's range: its words are FP32 numbers, unscaled.
+//  * Range of x (its words are FP32 numbers, unscaled; the scaling keeps only
+//    r and p in range): after each x update, a leading word of x that is not
+//    finite ends the solve with status ST_RANGE; a solve that would end
+//    converged or at maxit with every leading word of x below 2^-126 in
+//    magnitude (the whole solution under FP32's normal range) ends with
+//    ST_RANGE instead.  The recurrence residual never looks at x, so without
+//    this test such a solve would report convergence.
 // ---------------------------------------------------------------------------
+enum { ST_RANGE = 4 };
 inline int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
 inline int scale_exp(double c, int64_t n) {
   if (!(c > 0.0) || !std::isfinite(c)) return 0;
@@ -1066,9 +1073,13 @@ CGResult cg_qqf(int64_t n, const int64_t* rp, const int32_t* col, const double* 
     T alpha = A::div(rho, pq);
     T cx = scale_words(alpha, E);
     T malpha = neg<A>(alpha);
+    double xmax = 0.0;                 // largest |leading word of x|
+    bool xfinite = true;
     for (int64_t i = 0; i < n; ++i) {
       T xi = A::muladd(load<A>(x, n, i), cx, load<A>(p.data(), n, i));
       store<A>(x, n, i, xi);
+      if (!std::isfinite(xi.w[0])) xfinite = false;
+      else xmax = std::max(xmax, (double)std::fabs(xi.w[0]));
       T ri = A::muladd(load<A>(r.data(), n, i), malpha, load<A>(q.data(), n, i));
       A::normalize(ri);
       store<A>(r.data(), n, i, scale_words(ri, -s));
@@ -1078,9 +1089,11 @@ CGResult cg_qqf(int64_t n, const int64_t* rp, const int32_t* col, const double* 
     relres = fdiv(std::ldexp(fsqrt(A::collapse(rho1)), E), bn);
     res.relres = relres;
     if (hist) hist[res.iters - 1] = relres;
-    if (relres < tol) { res.status = ST_CONVERGED; return res; }
+    const bool x_under = xmax < std::ldexp(1.0, -126);
+    if (!xfinite) { res.status = ST_RANGE; return res; }
+    if (relres < tol) { res.status = x_under ? (int)ST_RANGE : (int)ST_CONVERGED; return res; }
     if (!std::isfinite(relres)) { res.status = ST_BREAKDOWN; return res; }
-    if (res.iters >= maxit) { res.status = ST_MAXIT; return res; }
+    if (res.iters >= maxit) { res.status = x_under ? (int)ST_RANGE : (int)ST_MAXIT; return res; }
     T beta = A::div(rho1, rho);
     T cp = scale_words(beta, s);
     for (int64_t i = 0; i < n; ++i)
