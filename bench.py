@@ -36,15 +36,17 @@ import numpy as np  # noqa: E402
 METRIC = "QTW-CG time-to-1e-14 residual (3-D Poisson 128^3, 7-point)"
 WORKLOAD = "c2"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_c2.json")
-# FP64 peak of the GB300 for the ALU roofline: 2 FP64 operations per clock per
-# SM (FMA counted as one operation, as the paper counts), 152 SMs, 2070 MHz.
+# Nominal FP64 rate of the GB300 (context only): 2 FP64 operations per clock
+# per SM (FMA counted as one operation, as the paper counts), 152 SMs, 2070 MHz.
 FP64_OPS_PER_CLK_SM = 2
 SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_OPS = FP64_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6
-# FP64 operations (FMA = 1) per stored entry and per row of the fused SpMV + p^T q
-# kernel: FP64 x MW product + MW add per entry, minus the add saved on each
-# row's first product, plus the dot leaf (MW product) and its accumulation.
+# The paper's FP64 operation counts (FMA = 1) per stored entry and per row of
+# the fused SpMV + p^T q kernel: FP64 x MW product + MW add per entry, minus the
+# add saved on each row's first product, plus the dot leaf (MW product) and its
+# accumulation.  Reported as `paper_ops_per_s`; part of this work runs on the
+# integer pipe, so it is not a fraction of any one pipe.
 SPMV_OPS = {  # arith: (per nnz, per row)
     "fp64": (1, 1 + 1),
     "dw": (6 + 11, 7 + 11 - 11),
@@ -53,8 +55,23 @@ SPMV_OPS = {  # arith: (per nnz, per row)
 }
 SPMV_OPS["qdw_nn"] = SPMV_OPS["qdw"]
 SPMV_OPS["qtw_nn"] = SPMV_OPS["qtw"]
+# FP64 instructions the SpMV kernel executes per operation (thread level:
+# DADD, DFMA, DMUL), from the device sequences: TwoSum errors (and the
+# double-word TwoProd errors) come from the integer pipe, a power-of-two
+# matrix entry scales the words exactly on the integer pipe, and the QTW SpMV
+# adds the product's last word on the integer pipe.  Keys: FP64 x MW product
+# with a general entry ("dx") and with a power-of-two entry ("dx2"), MW add,
+# MW product.  These counts reproduce ncu's executed-instruction counters
+# (profiles/k_spmv_*_c2.md).
+SPMV_INSTR = {
+    "qtw": {"dx": (1, 3, 2), "dx2": (0, 0, 0), "add": (6, 0, 0), "mul": (5, 6, 3)},
+    "dw": {"dx": (3, 1, 1), "dx2": (3, 0, 0), "add": (6, 0, 0), "mul": (3, 2, 1)},
+    "qdw": {"dx": (0, 1, 1), "dx2": (0, 0, 0), "add": (3, 0, 0), "mul": (0, 2, 1)},
+}
+SPMV_INSTR["qtw_nn"] = SPMV_INSTR["qtw"]
+SPMV_INSTR["qdw_nn"] = SPMV_INSTR["qdw"]
 WORDS = {"fp64": 1, "dw": 2, "qdw": 2, "qtw": 3, "tw": 3, "qdw_nn": 2, "qtw_nn": 3, "qw": 4, "qqw": 4, "qqw_nn": 4,
-         "qqf": 4}
+         "qqf": 4, "qf": 4}
 # FP32 pipe: 128 lanes per SM (FMA = 1 operation).
 FP32_PEAK_OPS = 128 * SMS * SM_MAX_MHZ * 1e6
 # FP32 operations of the QQF SpMV + p^T q kernel: per stored entry the FP64 x
@@ -63,6 +80,41 @@ FP32_PEAK_OPS = 128 * SMS * SM_MAX_MHZ * 1e6
 # QQF add (6 TwoSum x 6 + 4 = 40), less the add saved on each row's first
 # product; per row the dot leaf (product 72 + add 40).
 QQF_SPMV_OPS = (72 + 2 + 40, 72 + 40 - 40)
+# QF: every product and addition followed by VecSum4 (3 TwoSums, 18 operations).
+FP32_SPMV_OPS = {"qqf": QQF_SPMV_OPS, "qf": (72 + 2 + 18 + 40 + 18, 72 + 18 + 40 + 18 - (40 + 18))}
+
+
+def is_pow2(v):
+    """The device's power-of-two test (mwi::is_pow2): zero fraction, normal exponent."""
+    u = np.ascontiguousarray(v, dtype=np.float64).view(np.uint64)
+    e = (u >> np.uint64(52)) & np.uint64(0x7FF)
+    return ((u & np.uint64((1 << 52) - 1)) == 0) & (e >= 1) & (e <= 2046)
+
+
+def spmv_fp64_instr(arith, A, V):
+    """(DADD, DFMA, DMUL) thread-level FP64 instructions of one k_spmv launch
+    (mode 1) with V lanes per row, or None when no model exists for `arith`.
+    Every stored entry is one FP64 x MW product; a row of L > 0 entries adds
+    L - 1 products (each lane sums its entries, the lane tree combines the
+    lanes); each of the n rows gives a dot leaf, and the n leaves are summed by
+    n - 1 additions (slot accumulation, block tree, grid tree).  FP64: a lane's
+    first product is a DMUL, the rest are FMAs, the lane tree DADDs."""
+    lens = np.diff(np.asarray(A.row_ptr, dtype=np.int64))
+    n, nnz = int(A.n), int(A.nnz)
+    if arith == "fp64":
+        first = int(np.minimum(lens, V).sum())
+        tree = int(np.maximum(np.minimum(lens, V) - 1, 0).sum())
+        return (tree + max(n - 1, 0), nnz - first, first + n)
+    m = SPMV_INSTR.get(arith)
+    if m is None:
+        return None
+    p2 = int(is_pow2(A.val).sum())
+    adds = (nnz - int((lens > 0).sum())) + max(n - 1, 0)
+    tot = [0, 0, 0]
+    for key, cnt in (("dx", nnz - p2), ("dx2", p2), ("add", adds), ("mul", n)):
+        for j in range(3):
+            tot[j] += m[key][j] * cnt
+    return tuple(tot)
 
 
 def _dist():
@@ -211,19 +263,113 @@ def _golden_iters(arith):
 
 
 def oracle_sample(A, b, arith, iters_sample, total_iters, plan):
-    """Time the CPU oracle (single thread) on `iters_sample` iterations of the
-    workload and scale to `total_iters` iterations.  Returns (seconds, per_iter, detail)."""
+    """Time the CPU oracle (single thread) on `iters_sample` CG iterations of
+    the workload and project a complete solve of `total_iters` iterations.
+    Returns (projected seconds, seconds per iteration, init seconds, seconds
+    actually spent, residual history of the timed run)."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
     oracle.cg(arith, A, b, tol=0.0, maxit=1, plan=plan)
     t_init1 = time.perf_counter() - t0                      # init + 1 iteration
     t0 = time.perf_counter()
-    oracle.cg(arith, A, b, tol=0.0, maxit=1 + iters_sample, plan=plan)
+    *_, hist = oracle.cg(arith, A, b, tol=0.0, maxit=1 + iters_sample, plan=plan, history=True)
     t_run = time.perf_counter() - t0                        # init + 1 + k iterations
     per_it = max(t_run - t_init1, 1e-9) / iters_sample
     init = max(t_init1 - per_it, 0.0)
-    return init + per_it * total_iters, per_it, init
+    return init + per_it * total_iters, per_it, init, t_init1 + t_run, hist
+
+
+CPU_SAMPLE_ITERS = 40       # oracle iterations timed for cpu_baseline (about 10 s of CPU work at c2)
+
+
+def cpu_baseline(torch, mw, M, A, b_np, b_dev, arith, tol, gpu_iters, k=CPU_SAMPLE_ITERS):
+    """The oracle (as it stands, one thread) timed on the first k CG iterations
+    of the same solve, projected to the solve's iteration count; the GPU's
+    first k + 1 residuals are checked bit for bit against the timed run's."""
+    gi, src = _golden_iters(arith)
+    tot = gi if gi is not None else gpu_iters
+    src = src or "the GPU's iteration count (equal to the oracle's by the parity tests)"
+    est, per_it, init, spent, hist = oracle_sample(A, b_np, arith, k, tot, M.plan)
+    r = mw.solve(M, b_dev, arith, 0.0, 1 + k, history=True)
+    same = bool(np.array_equal(r.history.cpu().numpy().view(np.uint64), np.asarray(hist).view(np.uint64)))
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"{k + 1} CG iterations + init of the full system timed (one thread, {spent:.1f} s), "
+                      f"{per_it:.4f} s per iteration projected to {tot} iterations ({src}); the oracle is "
+                      f"the test oracle built -O3 -ffp-contract=off, not tuned",
+            "iterations_timed": k + 1, "projected": True, "seconds_timed": spent,
+            "history_bits_match_gpu": same}
+
+
+def spmv_roofline(arith, A, plan, spmv_ms, probe, elem):
+    """Roofline of the dominant kernel, k_spmv (SpMV + p^T q + alpha), from its
+    mean duration over 30 launches (CUDA events on the launching stream).
+
+    Two ceilings: HBM (algorithmic bytes / the measured copy bandwidth) and the
+    pipe that executes the arithmetic.  For the FP64-word arithmetics that is
+    the FP64 pipe, whose rate depends on the instruction: the executed
+    DADD / DFMA / DMUL counts (spmv_fp64_instr) over the rates the probe
+    measured in this run give the time the pipe needs; `frac` is that time over
+    the kernel's duration, reported as DADD-equivalent instructions per second
+    against the measured DADD rate.  For QQF it is the FP32 pipe (operations of
+    the sequences over 128 lanes x SMs x clock).  `bound` is the larger of the
+    two fractions' ceilings."""
+    t = spmv_ms * 1e-3
+    n, nnz = int(A.n), int(A.nnz)
+    alg_bytes = 12 * nnz + 8 * (n + 1) + 2 * elem * n      # val + col, row_ptr (int64), p once, q written
+    hbm = _measured_hbm_gbs() * 1e9
+    hbm_frac = alg_bytes / t / hbm
+    kv = _profile_fields(arith) or {}
+
+    def pct(prefix):
+        for k2, v in kv.items():
+            if k2.startswith(prefix):
+                try:
+                    return float(v.split("%")[0].strip()) / 100.0
+                except ValueError:
+                    return None
+        return None
+
+    out = {"kernel": f"k_spmv<{arith.upper()}> (SpMV + p^T q + alpha)", "kernel_ms": spmv_ms,
+           "alg_bytes_per_launch": alg_bytes, "hbm_gbs": alg_bytes / t / 1e9, "hbm_peak_gbs": hbm / 1e9,
+           "hbm_frac_of_measured": hbm_frac, "traffic": _profiled_traffic(arith),
+           "fp64_pipe_active_ncu": pct("FP64 pipe active"), "int_pipe_active_ncu": pct("ALU (integer) pipe")}
+    if arith in SPMV_OPS:
+        per_nnz, per_row = SPMV_OPS[arith]
+        ops = per_nnz * nnz + per_row * n
+        out["paper_ops_per_launch"] = ops
+        out["paper_ops_per_s"] = ops / t
+    if arith in FP32_SPMV_OPS:
+        ops = FP32_SPMV_OPS[arith][0] * nnz + FP32_SPMV_OPS[arith][1] * n
+        f32 = ops / t / FP32_PEAK_OPS
+        out["fp32_ops_per_launch"] = ops
+        out["fp32_frac_of_derived_peak"] = f32
+        alu = {"achieved": ops / t / 1e12, "peak": FP32_PEAK_OPS / 1e12, "unit": "T FP32 op/s (FMA = 1)",
+               "frac": f32, "peak_source": "128 FP32 lanes/clk/SM x 152 SMs x 2070 MHz (derived)"}
+    else:
+        instr = spmv_fp64_instr(arith, A, plan[0])
+        if instr is None:
+            out.update({"bound": "hbm", "achieved": alg_bytes / t / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                        "frac": hbm_frac, "fp64_model": None})
+            return out
+        dadd, dfma, dmul = instr
+        r_add, r_fma, r_mul = probe["dadd_ops_per_s"], probe["dfma_ops_per_s"], probe["dmul_ops_per_s"]
+        pipe_s = dadd / r_add + dfma / r_fma + dmul / r_mul
+        out["fp64_instr_per_launch"] = {"dadd": dadd, "dfma": dfma, "dmul": dmul}
+        out["fp64_pipe_s_per_launch"] = pipe_s
+        out["fp64_frac_of_nominal"] = (dadd + dfma + dmul) / t / FP64_PEAK_OPS
+        alu = {"achieved": pipe_s * r_add / t / 1e12, "peak": r_add / 1e12,
+               "unit": "T FP64 instructions/s (DADD-equivalent: DFMA and DMUL weighted by the measured rates)",
+               "frac": pipe_s / t,
+               "peak_source": "DADD rate measured in this run (mwcg_probe_peak); nominal 2 op/clk/SM x 152 x "
+                              "2070 MHz = 0.629 T"}
+    if alu["frac"] >= hbm_frac:
+        out.update({"bound": "alu", **alu})
+    else:
+        out.update({"bound": "hbm", "achieved": alg_bytes / t / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                    "frac": hbm_frac, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                    "alu_frac": alu["frac"]})
+    return out
 
 
 def _timed(torch, fn, reps=1):
@@ -447,10 +593,11 @@ def run_qqf(torch, mw, P, cpu):
     out["exact_solution_twin"] = {"workload": P.NORM_SYSTEMS["norm_poisson"], "runs": fe}
     if cpu:                               # the oracle on a bounded sample of the same QQF solve
         it_q = next(r["iters"] for r in out["runs"] if r["arith"] == "qqf")
-        est, per_it, _init = oracle_sample(A, b, "qqf", 2, it_q, M.plan)
-        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-                               "sample": f"2 QQF CG iterations + init of the full system, single thread, "
-                                         f"scaled to {it_q} iterations; {per_it:.3f} s per iteration"}
+        est, per_it, _init, spent, _h = oracle_sample(A, b, "qqf", 10, it_q, M.plan)
+        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "projected": True,
+                               "sample": f"11 QQF CG iterations + init of the full system timed (one thread, "
+                                         f"{spent:.1f} s), {per_it:.3f} s per iteration projected to {it_q} "
+                                         "iterations"}
     return out
 
 
@@ -575,6 +722,23 @@ def run_c5(torch, mw, P, cpu, n_fd=32):
     return out
 
 
+def qtw_over_dw_general(torch, mw, P):
+    """QTW / DW time to 1e-14 on the c5 diffusion matrix, whose entries are
+    not powers of two (the 128^3 Poisson entries are, and take an exact
+    integer-pipe scaling path)."""
+    A, b, _tol, maxit = P.workload("c5")
+    M = mw.CSRMatrix.from_csr(A)
+    db = torch.as_tensor(b, device="cuda")
+    out = {"workload": "c5 matrix (" + P.WORKLOADS["c5"].split(",")[0] + "), b = c5's b, tol 1e-14",
+           "pow2_entries_frac": float(is_pow2(A.val).mean())}
+    for ar in ("dw", "qtw"):
+        mw.solve(M, db, ar, 1e-14, 2)
+        r, ms = _timed(torch, lambda: mw.solve(M, db, ar, 1e-14, maxit))
+        out[ar] = {"time_s": ms / 1e3, "iters": r.iters, "status": r.status}
+    out["ratio"] = out["qtw"]["time_s"] / out["dw"]["time_s"]
+    return out
+
+
 def run_workloads(args):
     """--workload c1|c3|c4|c5: the other configurations, one JSON line each."""
     import torch
@@ -609,10 +773,19 @@ def run_workloads(args):
     return 0
 
 
+REF_SAMPLE_ITERS = 20      # oracle iterations per reference-arm step
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on one host core.  Each
+    step times the initialisation and REF_SAMPLE_ITERS + 1 CG iterations of the
+    headline solve; `value` projects the complete solve from the measured time
+    per iteration and the oracle's own iteration count for it, while
+    `ms_per_step` is the time the step actually took."""
     ws, rk = _dist()
     if rk != 0:
         return 0
+    import oracle
     from paper_2510_13536_gb300 import problems as P
     A, b, tol, maxit = P.workload(WORKLOAD)
     iters, src = _golden_iters("qtw")
@@ -620,18 +793,31 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "oracle iteration count for the full solve missing "
                                                                "(tests/golden/fullsize_c2.json)"}))
         return 0
-    vals = []
+    oracle.build()
+    plan = _golden_plan()
+    t0 = time.perf_counter()
+    oracle.cg("qtw", A, b, tol=0.0, maxit=1, plan=plan)
+    t_init1 = time.perf_counter() - t0                      # init + 1 iteration, once
+    k = REF_SAMPLE_ITERS
+    ests, step_s = [], []
     for s in range(args.warmup + args.steps):
-        est, per_it, init = oracle_sample(A, b, "qtw", 2, iters, _golden_plan())
+        t0 = time.perf_counter()
+        oracle.cg("qtw", A, b, tol=0.0, maxit=1 + k, plan=plan)
+        t_run = time.perf_counter() - t0
+        per_it = max(t_run - t_init1, 1e-9) / k
         if s >= args.warmup:
-            vals.append(est)
-    v = statistics.median(vals)
-    cb = {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-          "sample": f"2 QTW CG iterations of the full 128^3 system per step (plus init), single thread, "
-                    f"scaled to {iters} iterations ({src})"}
+            ests.append(max(t_init1 - per_it, 0.0) + per_it * iters)
+            step_s.append(t_run)
+    v = statistics.median(ests)
+    cb = {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "projected": True, "iterations_timed": k + 1,
+          "sample": f"{k + 1} QTW CG iterations + init of the full 128^3 system per step, one thread, "
+                    f"{statistics.median(step_s):.2f} s per step; the solve's time projected to {iters} "
+                    f"iterations ({src}); the test oracle built -O3 -ffp-contract=off, not tuned"}
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": 0, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "warmup": args.warmup, "ms_per_step": statistics.mean(step_s) * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "value_is": "projected time-to-1e-14 of the complete solve (init + iterations x measured s/iteration); "
+                       "ms_per_step is the bounded sample each step actually ran",
            "config": {"workload": WORKLOAD + ": " + P.WORKLOADS[WORKLOAD], "arith": "qtw", "tol": tol},
            "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -742,16 +928,11 @@ def run_gpu(args):
                                                   ctypes.c_void_p(x.data_ptr()), mw.arith_id(arith), 30,
                                                   ctypes.c_void_p(stream.cuda_stream), kms))
     spmv_ms = kms[0]
-    fp32 = arith == "qqf"                 # FP32 words: the FP32 pipe, 16 bytes per element
+    fp32 = arith in FP32_SPMV_OPS         # FP32 words: the FP32 pipe, 16 bytes per element
     elem = 16 if fp32 else 8 * w
-    per_nnz, per_row = QQF_SPMV_OPS if fp32 else SPMV_OPS[arith]
-    ops = per_nnz * A.nnz + per_row * A.n
-    achieved = ops / (spmv_ms * 1e-3)
-    peak_ops = FP32_PEAK_OPS if fp32 else FP64_PEAK_OPS
-    spmv_bytes = 12 * A.nnz + 8 * (A.n + 1) + 2 * elem * A.n
-    traffic = _profiled_traffic(arith)
 
-    # FP64 / integer pipe rates measured now on this GPU (roofline context).
+    # FP64 / integer pipe rates measured now on this GPU (the FP64 roofline's
+    # denominators: the pipe's rate depends on the instruction).
     probe = {}
     scratch = torch.empty(torch.cuda.get_device_properties(dev).multi_processor_count * 8 * 256,
                           dtype=torch.float64, device=dev)
@@ -761,6 +942,7 @@ def run_gpu(args):
         _capi.check(_capi.load().mwcg_probe_peak(kind, ctypes.c_void_p(scratch.data_ptr()), scratch.numel() * 8,
                                                  ctypes.c_void_p(stream.cuda_stream), ctypes.byref(v)))
         probe[name] = v.value
+    roofline = spmv_roofline(arith, A, M.plan, spmv_ms, probe, elem)
 
     # End to end through the C ABI with host buffers (pinned), copies included.
     bh = torch.empty(A.n, dtype=torch.float64, pin_memory=True)
@@ -776,16 +958,16 @@ def run_gpu(args):
     e2e = {"value": min(e2e_s), "unit": "s", "h2d_bytes_per_step": 8 * A.n + elem * A.n,
            "d2h_bytes_per_step": elem * A.n + 160}
 
-    # CPU oracle on a bounded sample (rank 0, N = 1 only).
-    cpu = None
+    # CPU oracle on a bounded sample (rank 0, N = 1 only), and the two other
+    # metrics of the workload family: batched vs one-by-one solves/s (c4) and
+    # the gradient against TW finite differences (c5), outside the timed region.
+    cpu = batched = grad = None
     if rk == 0 and ws == 1 and not args.no_cpu:
-        gi, src = _golden_iters(arith)
-        tot = gi if gi is not None else it
-        src = src or "iteration count of this run (oracle count missing)"
-        est, per_it, init = oracle_sample(A, b_np, arith, 2, tot, M.plan)
-        cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"2 CG iterations + init of the full system, single thread, scaled to {tot} iterations "
-                         f"({src}); {per_it:.3f} s per iteration"}
+        cpu = cpu_baseline(torch, mw, M, A, b_np, b, arith, tol, it)
+    if rk == 0 and ws == 1 and not args.no_extras:
+        batched = run_c4(torch, mw, P, False)
+        grad = run_c5(torch, mw, P, False, args.fd_bench)
+        grad["qtw_over_dw"] = qtw_over_dw_general(torch, mw, P)
 
     alg_bytes_iter = 12 * A.nnz + 8 * (A.n + 1) + 11 * elem * A.n
     out = {
@@ -803,19 +985,10 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": args.steps * (3 + 3 * it),
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": ("TFLOP32-op/s (FMA = 1)" if fp32 else "TFLOP64-op/s (FMA = 1)"),
-                     "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": f"k_spmv<{arith.upper()}> (SpMV + p^T q + alpha)", "ops_per_launch": ops,
-                     "alg_bytes_per_launch": spmv_bytes,
-                     "hbm_frac_of_measured": spmv_bytes / (spmv_ms * 1e-3) / 6691.8e9,
-                     "peak_source": ("128 FP32 op/clk/SM x 152 SMs x 2070 MHz (derived)" if fp32 else
-                                     "2 FP64 op/clk/SM x 152 SMs x 2070 MHz (derived; probe below measures it)"),
-                     "probe_measured_now": probe,
-                     # frac counts the paper's operations, part of which the integer pipe
-                     # executes; the FP64 pipe's own busy fraction comes from ncu.
-                     "fp64_pipe_active_ncu": _profiled_fp64_pipe(arith)},
+        "roofline": roofline,
         "cpu_baseline": cpu,
+        "batched": batched,
+        "grad_fd": grad,
     }
     if rk == 0:
         print(json.dumps(out))
@@ -830,7 +1003,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mwcg", choices=["mwcg", "reference"])
-    ap.add_argument("--arith", default="qtw", choices=["qtw", "dw", "qdw", "tw", "fp64", "qdw_nn", "qtw_nn", "qw", "qqw",
+    ap.add_argument("--arith", default="qtw", choices=["qtw", "dw", "qdw", "tw", "fp64", "qdw_nn", "qtw_nn", "qw", "qqw", "qf",
                                                        "qqw_nn", "qqf"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--only-solve", action="store_true",
@@ -842,7 +1015,11 @@ def main():
     ap.add_argument("--workload", nargs="+", default=None, choices=["c1", "c3", "c4", "c5", "norm", "pcg", "words", "bicg",
                                                                          "qqf"],
                     help="measure another configuration instead of the headline (one JSON line each)")
-    ap.add_argument("--fd", type=int, default=32, help="finite-difference entries checked in c5")
+    ap.add_argument("--fd", type=int, default=32, help="finite-difference entries checked in --workload c5")
+    ap.add_argument("--fd-bench", type=int, default=4,
+                    help="finite-difference entries checked in the default line's grad_fd object")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (c4) and gradient (c5) objects of the default line")
     ap.add_argument("--plan", default=None, help="override the summation plan V,T,G (ncu / tuning runs)")
     args = ap.parse_args()
     if args.workload:

@@ -60,7 +60,12 @@ extern "C" {
  * mwcg_word_op (op 5 collapses its words to FP64) and mwcg_profile_kernels;
  * the normalisation policy does not apply to it (r is normalised every
  * iteration), and the preconditioner, BiCGStab, the adjoint, the batched
- * solve and mwcg_dot_noalloc return MWCG_ERR_ARG. */
+ * solve and mwcg_dot_noalloc return MWCG_ERR_ARG.  A solve whose x leaves
+ * FP32's range returns MWCG_OUT_OF_RANGE.
+ * QF is QQF with every addition and product (FP64 x QF included) followed
+ * by VecSum4, the non-quasi counterpart of QQF as DW is of QDW: on strongly
+ * cancelling rows its precision stays relative to the result.  It has QQF's
+ * storage, entry points, scaled CG and limits. */
 typedef enum {
   MWCG_FP64 = 0,
   MWCG_DW = 1,
@@ -72,7 +77,8 @@ typedef enum {
   MWCG_QW = 7,
   MWCG_QQW = 8,
   MWCG_QQW_NN = 9,
-  MWCG_QQF = 10
+  MWCG_QQF = 10,
+  MWCG_QF = 11
 } mwcg_arith;
 
 /* Solver status (>= 0) and error codes (< 0). */
@@ -81,6 +87,8 @@ enum {
   MWCG_NOT_CONVERGED = 1,   /* maxit iterations done without reaching tol               */
   MWCG_BREAKDOWN = 2,       /* collapse(p^T q) not > 0, or a non-finite residual        */
   MWCG_BAD_PRECONDITIONER = 3, /* Jacobi: a diagonal entry missing, <= 0 or not finite; x0 untouched */
+  MWCG_OUT_OF_RANGE = 4,    /* QQF, QF: x left FP32's range -- a leading word of x not finite after an   */
+                            /* update, or every one below 2^-126 when the solve ends (x is invalid)  */
   MWCG_ERR_ARG = -1,        /* invalid argument (sizes, pointers, CSR structure, plan)  */
   MWCG_ERR_CUDA = -2,       /* a CUDA runtime call failed                               */
   MWCG_ERR_GUARD = -3,      /* device loop guard tripped (internal consistency failure) */
@@ -108,7 +116,8 @@ typedef struct {
 typedef struct mwcg_csr mwcg_csr;
 
 /* Number of 8-byte slots per element of a vector in an arithmetic (its FP64
- * words, 1 to 4; 2 for MWCG_QQF's four FP32 words), or -1 if unknown. */
+ * words, 1 to 4; 2 for the four FP32 words of MWCG_QQF and MWCG_QF), or -1
+ * if unknown. */
 int mwcg_words(int arith);
 
 /* Message of the last error on this thread ("" if none).  Owned by the
@@ -292,7 +301,8 @@ int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, 
  * one counter block, about 99 KB, held by every GPU that loads the library
  * until the process exits).  The function calls no cudaMalloc, cudaFree or
  * allocating library routine.
- *   arith, n, u, v, G  as in mwcg_dot (u, v device double[w*n]); G in
+ *   arith    0..9 (MWCG_FP64 .. MWCG_QQW_NN); MWCG_QQF and MWCG_QF return MWCG_ERR_ARG;
+ *   n, u, v, G  as in mwcg_dot (u, v device double[w*n]); G in
  *            1..MWCG_DOT_NOALLOC_MAX_G, larger G returns MWCG_ERR_ARG;
  *   out      device double[w] (caller-owned), written in stream order; the
  *            function does not synchronise the stream.

@@ -13,14 +13,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmwcg.so")
 
 ARITH = {"fp64": 0, "dw": 1, "qdw": 2, "tw": 3, "qtw": 4, "qdw_nn": 5, "qtw_nn": 6, "qw": 7, "qqw": 8, "qqw_nn": 9,
-         "qqf": 10}
-WORDS = {0: 1, 1: 2, 2: 2, 3: 3, 4: 3, 5: 2, 6: 3, 7: 4, 8: 4, 9: 4, 10: 4}
-# 8-byte slots per element in the C ABI's vectors (mwcg_words): QQF's four
-# FP32 words are packed two to a slot; every other arithmetic has one FP64
-# word per slot.
-SLOTS = {**WORDS, 10: 2}
-FP32_WORDS = {10}
-STATUS = {0: "converged", 1: "not_converged", 2: "breakdown", 3: "bad_preconditioner"}
+         "qqf": 10, "qf": 11}
+WORDS = {0: 1, 1: 2, 2: 2, 3: 3, 4: 3, 5: 2, 6: 3, 7: 4, 8: 4, 9: 4, 10: 4, 11: 4}
+# 8-byte slots per element in the C ABI's vectors (mwcg_words): the four FP32
+# words of QQF and QF are packed two to a slot; every other arithmetic has one
+# FP64 word per slot.
+SLOTS = {**WORDS, 10: 2, 11: 2}
+FP32_WORDS = {10, 11}
+STATUS = {0: "converged", 1: "not_converged", 2: "breakdown", 3: "bad_preconditioner", 4: "out_of_range"}
 PRECOND = {"none": 0, "jacobi": 1}
 ERRORS = {-1: "MWCG_ERR_ARG", -2: "MWCG_ERR_CUDA", -3: "MWCG_ERR_GUARD", -4: "MWCG_ERR_NOMEM"}
 

@@ -48,7 +48,8 @@ KernelTable table_qw();
 KernelTable table_qqw();
 KernelTable table_qqw_nn();
 KernelTable table_qqf();
-const void* qqf_init_pre();   // QQF: ||b|| and the first scale, before its init
+KernelTable table_qf();
+const void* qqf_init_pre();   // QQF and QF: ||b|| and the first scale, before the init
 BiTable bitable_fp64();
 BiTable bitable_dw();
 BiTable bitable_qdw();
@@ -83,16 +84,18 @@ int fail(int code, const char* fmt, ...) {
                   cudaGetErrorString(e_));                                                        \
   } while (0)
 
-constexpr int kNArith = 11;   // MWCG_FP64 .. MWCG_QQF
+constexpr int kNArith = 12;   // MWCG_FP64 .. MWCG_QF
+// The FP32-word arithmetics: scaled CG, packed vectors, no batched, cluster,
+// preconditioned, BiCGStab or adjoint solve.
+bool fp32_words(int arith) { return arith == MWCG_QQF || arith == MWCG_QF; }
 constexpr int kMaxG = 1024;
 
-// Dynamic shared memory of the last-block reductions: G slots of up to w
-// words + 2 FP64 + 3 one-byte flags (8 w + 19 bytes, rounded up: 44 KB at
+// Dynamic shared memory of the last-block reductions (mwk::red_smem: 44 KB at
 // G = 1024 for w = 3, 52 KB for w = 4, which is above the 48 KB available
 // without opting in, so every reduction kernel opts in once, to the largest
 // size: the attribute is a cap, and a lower one would refuse launches that
 // need the default 48 KB).
-size_t red_smem(int G, int w) { return (size_t)G * (8 * w + 20); }
+using mwk::red_smem;
 
 // Creates the CUDA context with an ordinary runtime call before the kernel
 // tables' one-time set-up.  Observed on GB300 (driver 580): when a
@@ -124,6 +127,7 @@ const mwk::KernelTable* table(int arith) {
     t[8] = mwk::table_qqw();
     t[9] = mwk::table_qqw_nn();
     t[10] = mwk::table_qqf();
+    t[11] = mwk::table_qf();
     for (auto& k : t)
       for (const void* f : {k.spmv, k.spmv_pol, k.init, k.init_pcg, k.update, k.update_pol, k.update_pcg,
                             k.update_pcg_pol, k.dot})
@@ -135,7 +139,7 @@ const mwk::KernelTable* table(int arith) {
 }
 
 // Kernel run between the x0 SpMV and the init, or null (QQF only).
-const void* init_pre(int arith) { return arith == MWCG_QQF ? mwk::qqf_init_pre() : nullptr; }
+const void* init_pre(int arith) { return fp32_words(arith) ? mwk::qqf_init_pre() : nullptr; }
 
 const mwk::BiTable* bitable(int arith) {
   static mwk::BiTable t[kNArith];
@@ -157,11 +161,14 @@ const mwk::BiTable* bitable(int arith) {
         if (f) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
     cudaGetLastError();
   });
-  if (arith < 0 || arith >= kNArith || !t[arith].init) return nullptr;   // none for QQF
+  if (arith < 0 || arith >= kNArith || !t[arith].init) return nullptr;   // none for QQF and QF
   return &t[arith];
 }
 
 constexpr int32_t kMaxIt = 1 << 30;
+// Zeroed entries past the end of the device CSR arrays: the SpMV's L2
+// prefetches widen their ranges to 16-byte boundaries.
+constexpr int64_t kRpPad = 1, kValPad = 2, kColPad = 4;
 
 
 
@@ -537,7 +544,7 @@ int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, in
   }
   const int64_t tiles = (A->n + mwk::TPB - 1) / mwk::TPB;
   const int small = mwb_host::small_cluster_size();
-  if (!eager_mode() && A->plan.G == small && tiles <= small && arith != MWCG_QQF)
+  if (!eager_mode() && A->plan.G == small && tiles <= small && !fp32_words(arith))
     return run_cluster(A, b, x, arith, tol, maxit, hist, s, iters_out, relres_out);
   const bool eager = eager_mode();
   if (!eager && (rc = ensure_graph(A, arith)) != MWCG_OK) return rc;
@@ -705,7 +712,7 @@ int check_solve_args(const mwcg_csr* A, const void* b, const void* x, int arith,
 extern "C" {
 
 int mwcg_words(int arith) {
-  static const int w[kNArith] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4, 2};   // QQF: 4 FP32 words in 2 slots
+  static const int w[kNArith] = {1, 2, 2, 3, 3, 2, 3, 4, 4, 4, 2, 2};   // QQF, QF: 4 FP32 words in 2 slots
   return (arith >= 0 && arith < kNArith) ? w[arith] : -1;
 }
 
@@ -752,9 +759,9 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
     return code;
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&A->rp, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
-      (nnz && (e = cudaMalloc(&A->col, sizeof(int32_t) * nnz)) != cudaSuccess) ||
-      (nnz && (e = cudaMalloc(&A->val, sizeof(double) * nnz)) != cudaSuccess) ||
+  if ((e = cudaMalloc(&A->rp, sizeof(int64_t) * (n + 1 + kRpPad))) != cudaSuccess ||
+      (nnz && (e = cudaMalloc(&A->col, sizeof(int32_t) * (nnz + kColPad))) != cudaSuccess) ||
+      (nnz && (e = cudaMalloc(&A->val, sizeof(double) * (nnz + kValPad))) != cudaSuccess) ||
       (e = cudaMalloc(&A->part, sizeof(double) * mwk::PART * kMaxG)) != cudaSuccess ||
       (e = cudaMalloc(&A->st, sizeof(mwk::DevState))) != cudaSuccess ||
       (e = cudaMallocHost(&A->h_st, sizeof(mwk::DevState))) != cudaSuccess)
@@ -765,6 +772,9 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
           cudaSuccess ||
       (nnz && (e = cudaMemcpyAsync(A->col, col, sizeof(int32_t) * nnz, kind, s)) != cudaSuccess) ||
       (nnz && (e = cudaMemcpyAsync(A->val, val, sizeof(double) * nnz, kind, s)) != cudaSuccess) ||
+      (e = cudaMemsetAsync(A->rp + n + 1, 0, sizeof(int64_t) * kRpPad, s)) != cudaSuccess ||
+      (nnz && (e = cudaMemsetAsync(A->col + nnz, 0, sizeof(int32_t) * kColPad, s)) != cudaSuccess) ||
+      (nnz && (e = cudaMemsetAsync(A->val + nnz, 0, sizeof(double) * kValPad, s)) != cudaSuccess) ||
       (e = cudaMemsetAsync(A->st, 0, sizeof(mwk::DevState), s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cleanup(fail(MWCG_ERR_CUDA, "copy to device: %s", cudaGetErrorString(e)));
@@ -972,7 +982,7 @@ int mwcg_spmv(mwcg_csr* A, int arith, const double* p, double* q, void* stream) 
 int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream, double* out) {
   g_err.clear();
   if (!table(arith) || n < 0 || G < 1 || G > kMaxG || !out) return fail(MWCG_ERR_ARG, "bad argument");
-  const int w = (arith == MWCG_QQF) ? 4 : mwcg_words(arith);      // one word per double
+  const int w = fp32_words(arith) ? 4 : mwcg_words(arith);      // one word per double
   if (n == 0) {
     for (int k = 0; k < w; ++k) out[k] = 0.0;
     return MWCG_OK;
@@ -1109,7 +1119,7 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
   for (int s = 0; s < nsys; ++s) {
     int rc = check_solve_args(A[s], b[s], x[s], arith[s], tol[s], maxit[s]);
     if (rc != MWCG_OK) return fail(rc, "system %d: %s", s, g_err.c_str());
-    if (arith[s] == MWCG_QQF) return fail(MWCG_ERR_ARG, "system %d: QQF is not batched", s);
+    if (fp32_words(arith[s])) return fail(MWCG_ERR_ARG, "system %d: QQF and QF are not batched", s);
     if (!seen.insert(A[s]).second) return fail(MWCG_ERR_ARG, "system %d: matrix handle repeated in the batch", s);
     if ((rc = ensure_ws(A[s])) != MWCG_OK) return rc;
   }

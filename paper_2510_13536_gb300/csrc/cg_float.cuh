@@ -44,6 +44,14 @@ __device__ __forceinline__ void st<mw::QQF>(double* __restrict__ v, int64_t n, i
   f[i] = make_float2(t.w[0], t.w[1]);
   f[n + i] = make_float2(t.w[2], t.w[3]);
 }
+template <>
+__device__ __forceinline__ mw::QF::T ld<mw::QF>(const double* __restrict__ v, int64_t n, int64_t i) {
+  return ld<mw::QQF>(v, n, i);
+}
+template <>
+__device__ __forceinline__ void st<mw::QF>(double* __restrict__ v, int64_t n, int64_t i, const mw::QF::T& t) {
+  st<mw::QQF>(v, n, i, t);
+}
 constexpr int kQqfSlots = 2;          // 8-byte slots per element
 
 __device__ __forceinline__ int qqf_E(const DevState* S) { return (int)S->omega[0]; }
@@ -169,6 +177,10 @@ __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
 
 // x += (alpha~ 2^E) p~; r~ = 2^-s normalise(r~ + (-alpha~) q~); rho~' = r~^T r~;
 // the stop test on 2^(E+s) sqrt(rho~') / ||b||; beta~; the next shift.
+// Range of x (unscaled FP32 words): the largest |leading word| of the new x is
+// reduced by an atomic maximum of its bits (an order-free reduction); a value
+// that is not finite ends the solve with ST_RANGE, and so does a solve that
+// would end converged or at maxit with every leading word below 2^-126.
 template <class A>
 __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
   using T = typename A::T;
@@ -187,18 +199,53 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
   const int64_t ntiles = (n + TPB - 1) / TPB;
   T acc = A::zero();
   bool pacc = false;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t i = t * TPB + threadIdx.x;
-    if (i < n) {
-      st<A>(x, n, i, A::muladd(ld<A>(x, n, i), cx, ld<A>(W.p, n, i)));
-      T ri = A::muladd(ld<A>(W.r, n, i), mal, ld<A>(W.q, n, i));
-      A::renorm(ri);
+  uint32_t xb = 0;                 // largest |x_i0| bits of this thread's rows (NaN and inf above finite)
+  // A::ILP tiles (t, t + G, ...) per pass, all loads first: the kernel is bound
+  // by memory latency.  Each slot still adds its leaves in increasing tile
+  // order, so the summation order is that of one tile per pass.
+  for (int64_t t = blockIdx.x; t < ntiles; t += (int64_t)A::ILP * gridDim.x) {
+    T xs[A::ILP], ps_[A::ILP], rs[A::ILP], qs[A::ILP];
+    int64_t idx[A::ILP];
+    bool valid[A::ILP];
 #pragma unroll
-      for (int j = 0; j < A::W; ++j) ri.w[j] = mw::fmul(ri.w[j], ps);
-      st<A>(W.r, n, i, ri);
-      const T leaf = A::mul(ri, ri);
-      if (pacc) acc = A::add(acc, leaf);
-      else { acc = leaf; pacc = true; }
+    for (int u = 0; u < A::ILP; ++u) {
+      const int64_t tu = t + (int64_t)u * gridDim.x;
+      idx[u] = tu * TPB + threadIdx.x;
+      valid[u] = tu < ntiles && idx[u] < n;
+      if (valid[u]) {
+        xs[u] = ld<A>(x, n, idx[u]);
+        ps_[u] = ld<A>(W.p, n, idx[u]);
+        rs[u] = ld<A>(W.r, n, idx[u]);
+        qs[u] = ld<A>(W.q, n, idx[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < A::ILP; ++u) {
+      if (valid[u]) {
+        const T xn = A::muladd(xs[u], cx, ps_[u]);
+        st<A>(x, n, idx[u], xn);
+        xb = max(xb, __float_as_uint(xn.w[0]) & 0x7FFFFFFFu);
+        T ri = A::muladd(rs[u], mal, qs[u]);
+        A::renorm(ri);
+#pragma unroll
+        for (int j = 0; j < A::W; ++j) ri.w[j] = mw::fmul(ri.w[j], ps);
+        st<A>(W.r, n, idx[u], ri);
+        const T leaf = A::mul(ri, ri);
+        if (pacc) acc = A::add(acc, leaf);
+        else { acc = leaf; pacc = true; }
+      }
+    }
+  }
+  {
+    __shared__ uint32_t sxb[NWARP];
+    xb = __reduce_max_sync(0xFFFFFFFFu, xb);
+    if ((threadIdx.x & 31) == 0) sxb[threadIdx.x >> 5] = xb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t m = 0;
+#pragma unroll
+      for (int k = 0; k < NWARP; ++k) m = max(m, sxb[k]);
+      atomicMax(&S->xmax_bits, m);     // before the block's ticket (grid_reduce fences)
     }
   }
   block_tree<A>(acc, pacc, 1);
@@ -208,6 +255,9 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
   if (threadIdx.x == 0) {
     S->counter = 0;
     if (!ptot) tot = A::zero();
+    const uint32_t xm = atomicOr(&S->xmax_bits, 0u);
+    S->xmax_bits = 0;
+    const bool x_nonfinite = xm >= 0x7F800000u, x_under = xm < 0x00800000u;
     const int En = E + s;
     const double c = A::collapse(tot);
     const double relres = __ddiv_rn(__dmul_rn(__dsqrt_rn(c), mw::pow2d(En)), S->bnorm);
@@ -215,14 +265,17 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
     const int it = S->iters;
     if (S->hist) S->hist[it - 1] = relres;
     unsigned cont = 0;
-    if (relres < S->tol) {
-      S->status = ST_CONVERGED;
+    if (x_nonfinite) {
+      S->status = ST_RANGE;
+      S->done = 1;
+    } else if (relres < S->tol) {
+      S->status = x_under ? ST_RANGE : ST_CONVERGED;
       S->done = 1;
     } else if (!isfinite(relres)) {
       S->status = ST_BREAKDOWN;
       S->done = 1;
     } else if (it >= S->maxit) {
-      S->status = ST_MAXIT;
+      S->status = x_under ? ST_RANGE : ST_MAXIT;
       S->done = 1;
     } else {
       const T rho = load_scalar_f<A>(S->rho);
@@ -245,15 +298,26 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_pupdate(Csr M, Work W) {
   const int64_t n = M.n;
   const T cp = A::scale(load_scalar_f<A>(S->beta), qqf_shift(S));
   const int64_t stride = (int64_t)gridDim.x * TPB;
-  for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += stride)
-    st<A>(W.p, n, i, A::muladd(ld<A>(W.r, n, i), cp, ld<A>(W.p, n, i)));
+  for (int64_t i0 = (int64_t)blockIdx.x * TPB + threadIdx.x; i0 < n; i0 += (int64_t)A::ILP * stride) {
+    T rr[A::ILP], pp[A::ILP];
+#pragma unroll
+    for (int u = 0; u < A::ILP; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < n) { rr[u] = ld<A>(W.r, n, i); pp[u] = ld<A>(W.p, n, i); }
+    }
+#pragma unroll
+    for (int u = 0; u < A::ILP; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < n) st<A>(W.p, n, i, A::muladd(rr[u], cp, pp[u]));
+    }
+  }
 }
 
-// The QQF kernel table: plain CG only (no normalisation policy, no
-// preconditioner, no adjoint gradient kernel); vectors of two 8-byte slots.
-// Its init is preceded by k_qqf_bnorm (qqf_init_pre in inst_qqf.cu).
+// The kernel table of QQF or QF (A): plain CG only (no normalisation policy,
+// no preconditioner, no adjoint gradient kernel); vectors of two 8-byte
+// slots.  Its init is preceded by k_qqf_bnorm (qqf_init_pre in inst_qqf.cu).
+template <class A>
 inline KernelTable make_table_qqf() {
-  using A = mw::QQF;
   KernelTable t{};
   t.words = kQqfSlots;
   t.spmv = (const void*)&k_spmv<A>;

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "mw_device.cuh"
+#include "tma.cuh"
 
 namespace mwk {
 
@@ -36,12 +37,16 @@ constexpr int TPB = 256;                  // threads per block of every kernel
 // multi-word value in [0, W), its presence at PRES, FP64 value k at FV + k
 // with its presence at FP + k.
 constexpr int PART = 12, PRES = 4, FV = 5, FP = 7;
+// Dynamic shared memory the last-block reductions need for G blocks of a
+// w-word arithmetic: grid_reduce uses G (8 w + 4) bytes, grid_reduce_mix with
+// two FP64 values G (8 w + 19); one size serves every reduction kernel.
+inline size_t red_smem(int G, int w) { return (size_t)G * (8 * w + 20); }
 // Tiles interleaved per thread (A::ILP; never changes the summation order).
 // Measured on GB300: the multi-word kernels are fastest with 1; FP64, which is
 // memory bound, needs several rows' loads in flight per thread.
 constexpr int NWARP = TPB / 32;
 
-enum { ST_CONVERGED = 0, ST_MAXIT = 1, ST_BREAKDOWN = 2, ST_GUARD = 3 };
+enum { ST_CONVERGED = 0, ST_MAXIT = 1, ST_BREAKDOWN = 2, ST_GUARD = 3, ST_RANGE = 4 };
 
 // Per-solve state in device memory.  Written by the host before a launch
 // (b, x, tol, maxit, hist) and by the kernels (everything else).
@@ -67,7 +72,7 @@ struct DevState {
   uint32_t norm_mask;       // NORM_* places
   double omega[4];          // BiCGStab: omega
   int32_t early;            // BiCGStab: ||s|| met the tolerance (x += alpha p ends the solve)
-  int32_t pad1;
+  uint32_t xmax_bits;       // QQF: largest |leading word of x| of this iteration, as FP32 bits
 };
 
 // Normalisation places (an extension of Sec. IV-D, which normalises r after
@@ -295,6 +300,38 @@ __device__ __forceinline__ bool grid_reduce_mix(const Work& W, const typename A:
 // ---------------------------------------------------------------------------
 // q = A p (mode 1, fused with p^T q and the alpha step) or q = A x0 (mode 0).
 // ---------------------------------------------------------------------------
+// The alpha step (Algorithm 1 line 6): the block's slots of p^T q by the
+// pairwise tree, the grid's block values by the last block to finish, then
+// alpha = rho / p^T q and the breakdown test, in that block's thread 0.
+template <class A>
+__device__ __forceinline__ void spmv_alpha(const Work& W, typename A::T acc, bool pacc, int V) {
+  using T = typename A::T;
+  DevState* S = W.st;
+  block_tree<A>(acc, pacc, V);
+  T tot;
+  bool ptot = false;
+  if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  if (threadIdx.x == 0) {
+    S->counter = 0;
+    if (!ptot) tot = A::zero();
+    S->iters += 1;
+    double pq = A::collapse(tot);
+    // Breakdown: collapse(p^T q) not > 0 (NaN included) or not finite.
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      S->status = ST_BREAKDOWN;
+      S->done = 1;
+      set_cond(W, 0);
+    } else {
+      T rho;
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) rho.w[k] = S->rho[k];
+      T al = A::div(rho, tot);
+#pragma unroll
+      for (int k = 0; k < A::W; ++k) S->alpha[k] = al.w[k];
+    }
+  }
+}
+
 // Entries kk[u], kk[u] + V, ... < ke[u] of the interleaved rows added into
 // sum[u] left to right; NS: normalise the running sum after every addition.
 template <class A, bool NS>
@@ -314,6 +351,9 @@ __device__ __forceinline__ void row_accumulate(const Csr& M, const double* __res
     if (!more) break;
   }
 }
+
+// Prefetch distance of the SpMV, in passes over the block's tiles.
+constexpr int kPfPasses = 2;
 
 // POL: the instantiation that follows the handle's normalisation policy
 // (DevState norm_every / norm_mask).  The default instantiation implements
@@ -352,10 +392,40 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
   const int64_t ntiles = (n + R - 1) / R;
   T acc = A::zero();
   bool pacc = false;
+  // L2 prefetch, issued by one lane of the block's last warp: on each pass,
+  // the row pointers of the tiles 2 kPfPasses passes ahead and the val / col
+  // segments of the tiles kPfPasses passes ahead (whose row pointers were
+  // prefetched earlier, so reading them hits L2).  The row's dependent loads
+  // (row pointer, then entry and column, then the gathered p) then find the
+  // CSR data in L2.
+  const bool pf_lane = threadIdx.x == TPB - 32;
+  const int64_t pass = (int64_t)A::ILP_SPMV * gridDim.x;
+  auto prefetch = [&](int64_t t0) {
+#pragma unroll
+    for (int u = 0; u < A::ILP_SPMV; ++u) {
+      const int64_t tr = t0 + 2 * kPfPasses * pass + (int64_t)u * gridDim.x;
+      if (tr < ntiles) tma::prefetch_l2_range(M.rp, tr * R, min((tr + 1) * R, n) + 1, 8);
+      const int64_t tv = t0 + kPfPasses * pass + (int64_t)u * gridDim.x;
+      if (tv < ntiles) {
+        const int64_t k0 = M.rp[tv * R], k1 = M.rp[min((tv + 1) * R, n)];
+        tma::prefetch_l2_range(M.val, k0, k1, 8);
+        tma::prefetch_l2_range(M.col, k0, k1, 4);
+      }
+    }
+  };
+  if (pf_lane && blockIdx.x < ntiles) {    // the first passes' row pointers
+    for (int64_t m = 0; m < 2 * kPfPasses; ++m)
+#pragma unroll
+      for (int u = 0; u < A::ILP_SPMV; ++u) {
+        const int64_t tr = blockIdx.x + m * pass + (int64_t)u * gridDim.x;
+        if (m >= kPfPasses && tr < ntiles) tma::prefetch_l2_range(M.rp, tr * R, min((tr + 1) * R, n) + 1, 8);
+      }
+  }
   // A::ILP_SPMV tiles (t, t+G, ...) per pass: their rows' chains are independent,
   // so interleaving them hides latency; the dot leaves are still added in
   // increasing tile order, so the summation order is unchanged.
-  for (int64_t t = blockIdx.x; t < ntiles; t += (int64_t)A::ILP_SPMV * gridDim.x) {
+  for (int64_t t = blockIdx.x; t < ntiles; t += pass) {
+    if (pf_lane) prefetch(t);
     T sum[A::ILP_SPMV];
     bool ps[A::ILP_SPMV];
     int64_t row[A::ILP_SPMV], kk[A::ILP_SPMV], ke[A::ILP_SPMV], len[A::ILP_SPMV];
@@ -446,29 +516,7 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
     }
   }
   if (mode != 1) return;
-  block_tree<A>(acc, pacc, V);
-  T tot;
-  bool ptot = false;
-  if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
-  if (threadIdx.x == 0) {
-    S->counter = 0;
-    if (!ptot) tot = A::zero();
-    S->iters += 1;
-    double pq = A::collapse(tot);
-    // Breakdown: collapse(p^T q) not > 0 (NaN included) or not finite.
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      S->status = ST_BREAKDOWN;
-      S->done = 1;
-      set_cond(W, 0);
-    } else {
-      T rho;
-#pragma unroll
-      for (int k = 0; k < A::W; ++k) rho.w[k] = S->rho[k];
-      T al = A::div(rho, tot);
-#pragma unroll
-      for (int k = 0; k < A::W; ++k) S->alpha[k] = al.w[k];
-    }
-  }
+  spmv_alpha<A>(W, acc, pacc, V);
 }
 
 // ---------------------------------------------------------------------------

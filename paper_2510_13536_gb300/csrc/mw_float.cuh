@@ -83,14 +83,35 @@ __device__ __forceinline__ void split3(double a, float& a0, float& a1, float& a2
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
 __device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
 
-#ifndef MWCG_ILP_SPMV_QQF
-#define MWCG_ILP_SPMV_QQF 1        // rows per thread in flight in the SpMV (same summation order)
-#endif
+// FP64 x QQF for a power of two a = +-2^k (2^-126 <= |a| < 2^128): split3(a) is
+// (a, +0, +0) and the fourth word is +0, so in the full product every TwoProd
+// error, every product with a zero word of a and every TwoSum partner is a
+// zero, and the sequence returns (a b0, a b1, a b2, a b3), with +0 for a zero
+// lower word of b, whenever each nonzero a b_j is an exact FP32 normal number
+// (b_j normal and the scaled exponent inside the normal range).  That case is
+// four FP32 multiplications; the path declines (returns false) otherwise.
+__device__ __forceinline__ bool pow2_dxmul_f(double a, const float (&b)[4], float (&c)[4]) {
+  const uint64_t ua = (uint64_t)__double_as_longlong(a);
+  const int ea = (int)((ua >> 52) & 0x7FFu);
+  if ((ua & 0xFFFFFFFFFFFFFULL) != 0 || ea < 897 || ea > 1150) return false;
+  const float af = __uint_as_float((uint32_t)(ua >> 32 & 0x80000000u) | ((uint32_t)(ea - 896) << 23));
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t eb = (__float_as_uint(b[j]) >> 23) & 0xFFu;
+    const float p = fmul(af, b[j]);
+    const uint32_t ep = (__float_as_uint(p) >> 23) & 0xFFu;
+    const bool zero = (__float_as_uint(b[j]) << 1) == 0u;
+    ok = ok && (zero || (eb != 0u && eb != 255u && ep != 0u && ep != 255u));
+    c[j] = (zero && j > 0) ? 0.0f : p;
+  }
+  return ok;
+}
 
 struct QQF {
-  static constexpr int ILP = 1;
+  static constexpr int ILP = 2;               // rows in flight per thread in the vector kernels (memory bound)
   static constexpr int CHUNK = 1;
-  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_QQF;
+  static constexpr int ILP_SPMV = 1;
   static constexpr int MINB = 3;
   static constexpr int W = 4;
   static constexpr bool QUASI = true;
@@ -155,7 +176,11 @@ struct QQF {
     c.w[3] = fadd(fadd(ffma(a, b.w[3], e4), e5), e6);
     return c;
   }
-  static __device__ __forceinline__ T dxmul(double a, const T& b) { return mul(from(a), b); }
+  static __device__ __forceinline__ T dxmul(double a, const T& b) {
+    T c;
+    if (pow2_dxmul_f(a, b.w, c.w)) return c;
+    return mul(from(a), b);
+  }
   static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return add(c, mul(a, b)); }
   static __device__ __forceinline__ T dxmuladd(const T& c, double a, const T& b) { return add(c, dxmul(a, b)); }
   static __device__ __forceinline__ T neg(const T& a) {
@@ -201,6 +226,42 @@ struct QQF {
     }
     return c;
   }
+};
+
+// QF: QQF with every addition and product (FP64 x QF included) followed by
+// VecSum4 -- the non-quasi counterpart of QQF, as DW relates to QDW in Sec.
+// III.  A quasi addition's error is relative to its operands, not to its
+// result, so on strongly cancelling SpMV rows QQF keeps about FP64's precision
+// in the result; renormalising every result keeps the words ordered and the
+// precision relative to the result.  Division, scaling and collapse are
+// QQF's (the quotient is renormalised by QQF's division).
+struct QF {
+  static constexpr int ILP = 2;
+  static constexpr int CHUNK = 1;
+  static constexpr int ILP_SPMV = 1;
+  static constexpr int MINB = 3;
+  static constexpr int W = 4;
+  static constexpr bool QUASI = false;
+  static constexpr bool NORMALISES = false;   // the normalisation policy does not apply
+  static constexpr bool PACKED = true;        // FP32 words, two per 8-byte slot
+  using T = MWF<4>;
+  static __device__ __forceinline__ T fix(T c) {
+    QQF::renorm(c);
+    return c;
+  }
+  static __device__ __forceinline__ T zero() { return QQF::zero(); }
+  static __device__ __forceinline__ T from(double a) { return QQF::from(a); }
+  static __device__ __forceinline__ T add(const T& a, const T& b) { return fix(QQF::add(a, b)); }
+  static __device__ __forceinline__ T mul(const T& a, const T& b) { return fix(QQF::mul(a, b)); }
+  static __device__ __forceinline__ T dxmul(double a, const T& b) { return fix(QQF::dxmul(a, b)); }
+  static __device__ __forceinline__ T muladd(const T& c, const T& a, const T& b) { return add(c, mul(a, b)); }
+  static __device__ __forceinline__ T dxmuladd(const T& c, double a, const T& b) { return add(c, dxmul(a, b)); }
+  static __device__ __forceinline__ T neg(const T& a) { return QQF::neg(a); }
+  static __device__ __forceinline__ void renorm(T& a) { QQF::renorm(a); }
+  static __device__ __forceinline__ void normalize(T& a) { QQF::renorm(a); }
+  static __device__ __forceinline__ T div(const T& a, const T& b) { return QQF::div(a, b); }
+  static __device__ __forceinline__ double collapse(const T& a) { return QQF::collapse(a); }
+  static __device__ __forceinline__ T scale(const T& a, int k) { return QQF::scale(a, k); }
 };
 
 }  // namespace mw

@@ -126,7 +126,7 @@ extern "C" int mwcg_dot_noalloc(int arith, int64_t n, const double* u, const dou
   W.V = 1;
   W.G = G;
   void* args[] = {(void*)&u, (void*)&v, (void*)&n, (void*)&W, (void*)&out};
-  e = cudaLaunchKernel(kt.dot, dim3(G), dim3(mwk::TPB), args, (size_t)G * 40, s);
+  e = cudaLaunchKernel(kt.dot, dim3(G), dim3(mwk::TPB), args, mwk::red_smem(G, kt.words), s);
   if (e != cudaSuccess) return err(MWCG_ERR_CUDA, "kernel launch", e);
   return MWCG_OK;
 }

@@ -183,7 +183,7 @@ class SolveResult:
     x: torch.Tensor          # (w, n) multi-word solution
     iters: int
     relres: float
-    status: int              # 0 converged, 1 maxit, 2 breakdown
+    status: int              # 0 converged, 1 maxit, 2 breakdown, 3 bad preconditioner, 4 x out of range (QQF)
     history: torch.Tensor | None = None
 
     @property

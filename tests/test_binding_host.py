@@ -31,8 +31,10 @@ def test_numpy_and_torch_packing_agree():
 
 def test_abi_conversion_per_arithmetic():
     n = 5
+    for name in ("qqf", "qf"):
+        a = _capi.ARITH[name]
+        assert _capi.WORDS[a] == 4 and _capi.SLOTS[a] == 2 and a in _capi.FP32_WORDS
     q = _capi.ARITH["qqf"]
-    assert _capi.WORDS[q] == 4 and _capi.SLOTS[q] == 2 and q in _capi.FP32_WORDS
     x = torch.ones((4, n), dtype=torch.float32)
     assert solver._to_abi(q, x, n).shape == (2, n)
     assert solver._from_abi(q, solver._to_abi(q, x, n), n).dtype == torch.float32

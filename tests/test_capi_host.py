@@ -37,8 +37,9 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_words_and_error_string(lib):
-    assert [lib.mwcg_words(a) for a in range(11)] == [1, 2, 2, 3, 3, 2, 3, 4, 4, 4, 2]   # QQF: 2 slots
-    assert lib.mwcg_words(11) == -1 and lib.mwcg_words(-1) == -1
+    # 8-byte slots per element: the FP64 words; QQF and QF pack four FP32 words in 2.
+    assert [lib.mwcg_words(a) for a in range(12)] == [1, 2, 2, 3, 3, 2, 3, 4, 4, 4, 2, 2]
+    assert lib.mwcg_words(12) == -1 and lib.mwcg_words(-1) == -1
     assert isinstance(lib.mwcg_last_error(), bytes)
 
 
@@ -79,3 +80,5 @@ def test_null_arguments_rejected(lib):
     out = (ctypes.c_double * 4)()
     assert lib.mwcg_dot_noalloc(10, 10, None, None, 1, None, out) == -1      # QQF has no no-alloc dot
     assert b"unknown arithmetic" in lib.mwcg_last_error()
+    assert lib.mwcg_dot_noalloc(11, 10, None, None, 1, None, out) == -1      # nor has QF
+    assert lib.mwcg_dot_noalloc(12, 10, None, None, 1, None, out) == -1

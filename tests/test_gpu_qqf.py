@@ -1,9 +1,11 @@
-"""QQF (four FP32 words, scaled CG) on the CUDA path vs the oracle, bit for bit.
+"""QQF and QF (four FP32 words, scaled CG) on the CUDA path vs the oracle, bit for bit.
 
 The word algebra (add, mul, FP64 x QQF through the exact three-word split,
 division, VecSum4, collapse), the SpMV and dot, and the solver on the CUDA
 graph and on host-launched kernels, including right-hand sides far outside
 FP32's range (the power-of-two scaling of r and p) and the special cases.
+Every test runs for QQF and for QF (QQF renormalised after every operation),
+except the QQF breakdown and its QF counterpart.
 """
 import numpy as np
 import pytest
@@ -11,6 +13,11 @@ import pytest
 from paper_2510_13536_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(params=["qqf", "qf"])
+def ar(request):
+    return request.param
 
 
 @pytest.fixture(scope="module")
@@ -48,29 +55,53 @@ def rand_qqf(rng, n, emin=-20, emax=20):
     return w.astype(np.float64)
 
 
-def test_word_ops_bit_exact(mw, orc):
+def test_word_ops_bit_exact(mw, orc, ar):
     rng = np.random.default_rng(61)
     n = 5000
     a, b = rand_qqf(rng, n), rand_qqf(rng, n)
     b[:, :7] = 0.0
     b[0, :7] = [1.0, -1.0, 2.0 ** -60, 3.0, 0.5, 2.0 ** 60, 1.5]
     for op in ("add", "mul", "div"):
-        g = mw.word_op(op, "qqf", dev(a, np.float32), dev(b, np.float32)).cpu().numpy()
+        g = mw.word_op(op, ar, dev(a, np.float32), dev(b, np.float32)).cpu().numpy()
         assert g.dtype == np.float32 and g.shape == (4, n)
-        assert same_bits(g, getattr(orc, op)("qqf", a, b)), op
-    g = mw.word_op("normalize", "qqf", dev(a, np.float32)).cpu().numpy()
-    assert same_bits(g, orc.normalize("qqf", a))
-    g = mw.word_op("collapse", "qqf", dev(a, np.float32)).cpu().numpy()
-    assert same_bits(g, orc.collapse("qqf", a))
+        assert same_bits(g, getattr(orc, op)(ar, a, b)), op
+    g = mw.word_op("normalize", ar, dev(a, np.float32)).cpu().numpy()
+    assert same_bits(g, orc.normalize(ar, a))
+    g = mw.word_op("collapse", ar, dev(a, np.float32)).cpu().numpy()
+    assert same_bits(g, orc.collapse(ar, a))
     # FP64 x QQF over the split's fast range, its edges and the rounding path.
     s = rng.uniform(1, 2, n) * rng.choice([-1, 1], n) * 2.0 ** rng.integers(-100, 128, n)
     s[:12] = [0.0, -0.0, 5e-310, -3.3e-320, 2.0 ** -97, -2.0 ** -97 * 1.75, 2.0 ** -98, 1.3 * 2.0 ** -100,
               -7.1e-35, 2.0 ** 127 * 1.999, 1.0, -1.0]
-    g = mw.word_op("dxmul", "qqf", dev(s), dev(b, np.float32)).cpu().numpy()
-    assert same_bits(g, orc.dxmul("qqf", s, b))
+    g = mw.word_op("dxmul", ar, dev(s), dev(b, np.float32)).cpu().numpy()
+    assert same_bits(g, orc.dxmul(ar, s, b))
 
 
-def test_spmv_and_dot(mw, orc):
+def test_pow2_product_bit_exact(mw, orc, ar):
+    """FP64 x QQF with power-of-two entries, which the device reduces to four
+    exact FP32 scalings when every product is a normal number: against the
+    full product of the oracle, over zero lower words of either sign,
+    subnormal words, products that leave FP32's normal range and entries at
+    and beyond the edges of that range."""
+    rng = np.random.default_rng(64)
+    n = 6000
+    b = rand_qqf(rng, n, emin=-140, emax=127)
+    z = rng.integers(0, 8, n)
+    for k in range(1, 4):                                   # zero lower words, both signs
+        m = z == k
+        b[k:, m] = 0.0
+        b[k, m & (rng.integers(0, 2, n) == 1)] = -0.0
+    b[0, z == 4] = rng.choice([0.0, -0.0], int((z == 4).sum()))
+    sub = z == 5                                            # a subnormal lower word
+    b[3, sub] = np.float32(1e-42) * rng.choice([-1, 1], int(sub.sum()))
+    e = rng.integers(-140, 140, n)
+    s = rng.choice([-1.0, 1.0], n) * 2.0 ** e.astype(np.float64)
+    s[:10] = [1.0, -1.0, 2.0 ** -126, -2.0 ** -127, 2.0 ** 127, 2.0 ** 128, -2.0 ** -97, 2.0 ** -98, 0.5, 4.0]
+    g = mw.word_op("dxmul", ar, dev(s), dev(b, np.float32)).cpu().numpy()
+    assert same_bits(g, orc.dxmul(ar, s, b))
+
+
+def test_spmv_and_dot(mw, orc, ar):
     rng = np.random.default_rng(62)
     for A, plan in ((P.power_law_laplacian(4000, seed=3, mean_deg=12, max_deg=300), None),
                     (P.laplacian_3d(16, 1e-3), (2, 256, 37))):
@@ -78,17 +109,17 @@ def test_spmv_and_dot(mw, orc):
         if plan:
             M.plan = plan
         p = rand_qqf(rng, A.n, -3, 3)
-        q = mw.spmv(M, "qqf", dev(p, np.float32)).cpu().numpy()
-        assert same_bits(q, orc.spmv("qqf", A, p, V=M.plan[0])), A.name
+        q = mw.spmv(M, ar, dev(p, np.float32)).cpu().numpy()
+        assert same_bits(q, orc.spmv(ar, A, p, V=M.plan[0])), A.name
     u, v = rand_qqf(rng, 70001, -4, 4), rand_qqf(rng, 70001, -4, 4)
     for G in (1, 37, 456):
-        g = mw.dot("qqf", dev(u, np.float32), dev(v, np.float32), G)
-        assert same_bits(g, orc.dot("qqf", u, v, R=256, G=G)), G
+        g = mw.dot(ar, dev(u, np.float32), dev(v, np.float32), G)
+        assert same_bits(g, orc.dot(ar, u, v, R=256, G=G)), G
 
 
-def _check(mw, orc, M, A, b, tol, maxit, tag, x0=None):
-    r = mw.solve(M, dev(b), "qqf", tol, maxit, history=True, x0=None if x0 is None else dev(x0, np.float32))
-    xo, ito, rro, sto, ho = orc.cg("qqf", A, b, x0=x0, tol=tol, maxit=maxit, plan=M.plan, history=True)
+def _check(mw, orc, M, A, b, tol, maxit, tag, x0=None, ar="qqf"):
+    r = mw.solve(M, dev(b), ar, tol, maxit, history=True, x0=None if x0 is None else dev(x0, np.float32))
+    xo, ito, rro, sto, ho = orc.cg(ar, A, b, x0=x0, tol=tol, maxit=maxit, plan=M.plan, history=True)
     assert (r.iters, r.status) == (ito, sto), (tag, r.iters, ito, r.status, sto)
     assert same_bits(np.array([r.relres]), np.array([rro])), (tag, r.relres, rro)
     assert r.x.dtype.is_floating_point and r.x.shape == (4, A.n)
@@ -98,102 +129,132 @@ def _check(mw, orc, M, A, b, tol, maxit, tag, x0=None):
     return r
 
 
-def test_cg_graph_path(mw, orc):
+def test_cg_graph_path(mw, orc, ar):
     for A, seed, tol, maxit in ((P.laplacian_3d(24, 1e-3), 71, 1e-22, 300),
                                 (P.diffusion_2d(90, 3), 72, 1e-20, 800),
                                 (P.power_law_laplacian(5000, seed=7, mean_deg=12, max_deg=300), 73, 1e-20, 300)):
         b = P.rhs_uniform(A.n, seed)
         M = mw.CSRMatrix.from_csr(A)
-        r = _check(mw, orc, M, A, b, tol, maxit, A.name)
+        r = _check(mw, orc, M, A, b, tol, maxit, A.name, ar=ar)
         assert r.iters > 20
         M.plan = (2, 256, 37)
-        _check(mw, orc, M, A, b, tol, maxit, A.name + " V=2")
+        _check(mw, orc, M, A, b, tol, maxit, A.name + " V=2", ar=ar)
 
 
-def test_eager_launches(mw, orc, monkeypatch):
+def test_breakdown_on_cancelling_power_law(mw, orc):
+    """QQF's known failure: on a 2000-node power-law graph Laplacian whose rows
+    cancel strongly, its ~96 bits run out and p^T q loses its sign near
+    iteration 800.  The GPU takes the breakdown path at the oracle's iteration,
+    with the oracle's residual and solution bits."""
+    A = P.power_law_laplacian(2000, seed=7, mean_deg=12, max_deg=300)
+    b = P.rhs_uniform(A.n, 32)
+    M = mw.CSRMatrix.from_csr(A)
+    r = _check(mw, orc, M, A, b, 1e-14, 2000, "power-law 2000")
+    assert r.status == 2 and r.iters > 700, (r.status, r.iters)
+
+
+def test_qf_converges_where_qqf_breaks_down(mw, orc):
+    """The same system in QF (every result renormalised): it converges, with
+    the oracle's iteration count, residual and solution bits."""
+    A = P.power_law_laplacian(2000, seed=7, mean_deg=12, max_deg=300)
+    b = P.rhs_uniform(A.n, 32)
+    M = mw.CSRMatrix.from_csr(A)
+    r = _check(mw, orc, M, A, b, 1e-14, 4000, "power-law 2000", ar="qf")
+    assert r.status == 0, (r.status, r.iters)
+
+
+def test_eager_launches(mw, orc, ar, monkeypatch):
     monkeypatch.setenv("MWCG_EAGER", "1")
     A = P.diffusion_2d(60, 4)
     b = P.rhs_uniform(A.n, 74)
     M = mw.CSRMatrix.from_csr(A)
-    _check(mw, orc, M, A, b, 1e-20, 400, "eager")
+    _check(mw, orc, M, A, b, 1e-20, 400, "eager", ar=ar)
 
 
-def test_small_systems_run_the_graph(mw, orc):
+def test_small_systems_run_the_graph(mw, orc, ar):
     """Systems small enough for the one-cluster launch of the other arithmetics."""
     for A in (P.laplacian_2d(40), P.laplacian_2d(5), P.random_spd_small(9, seed=3)):
         b = P.rhs_uniform(A.n, 75)
         M = mw.CSRMatrix.from_csr(A)
-        _check(mw, orc, M, A, b, 1e-22, 400, A.name)
+        _check(mw, orc, M, A, b, 1e-22, 400, A.name, ar=ar)
 
 
-def test_scaling_far_outside_fp32_range(mw, orc):
+def test_scaling_far_outside_fp32_range(mw, orc, ar):
     """b 2^k with |k| > 126: E0 takes the FP64 route of the word scaling;
-    the iterations, residuals and history equal the unscaled problem's."""
+    the iterations, residuals and history equal the unscaled problem's while
+    x (unscaled FP32 words) stays in FP32's range.  At k = -300 the whole
+    solution is below FP32's normal range and at k = +300 it overflows at the
+    first update: the solve then reports MWCG_OUT_OF_RANGE (4), not success."""
     A = P.laplacian_3d(20, 1e-3)
     b = P.rhs_uniform(A.n, 76)
     M = mw.CSRMatrix.from_csr(A)
-    r0 = _check(mw, orc, M, A, b, 1e-22, 300, "k=0")
-    for k in (-300, 300, -40, 90):
-        r = _check(mw, orc, M, A, b * 2.0 ** k, 1e-22, 300, f"k={k}")
+    r0 = _check(mw, orc, M, A, b, 1e-22, 300, "k=0", ar=ar)
+    assert r0.status == 0
+    for k in (-300, -40, 90):
+        r = _check(mw, orc, M, A, b * 2.0 ** k, 1e-22, 300, f"k={k}", ar=ar)
         assert (r.iters, r.relres) == (r0.iters, r0.relres), k
         assert same_bits(r.history.cpu().numpy(), r0.history.cpu().numpy()), k
+        assert r.status == (4 if k == -300 else 0), (k, r.status)
+    r = _check(mw, orc, M, A, b * 2.0 ** 300, 1e-22, 300, "k=300", ar=ar)
+    assert (r.status, r.iters) == (4, 1)
+    assert same_bits(r.history.cpu().numpy(), r0.history.cpu().numpy()[:1])
 
 
-def test_nonzero_x0_and_limits(mw, orc):
+def test_nonzero_x0_and_limits(mw, orc, ar):
     A = P.diffusion_2d(50, 6)
     b = P.rhs_uniform(A.n, 77)
     M = mw.CSRMatrix.from_csr(A)
     rng = np.random.default_rng(78)
     x0 = rand_qqf(rng, A.n, -2, 2)
-    _check(mw, orc, M, A, b, 1e-20, 500, "x0", x0=x0)
-    _check(mw, orc, M, A, b, 1e-300, 7, "maxit")
-    _check(mw, orc, M, A, b, 0.0, 3, "tol 0")
+    _check(mw, orc, M, A, b, 1e-20, 500, "x0", x0=x0, ar=ar)
+    _check(mw, orc, M, A, b, 1e-300, 7, "maxit", ar=ar)
+    _check(mw, orc, M, A, b, 0.0, 3, "tol 0", ar=ar)
 
 
-def test_special_cases(mw, orc):
+def test_special_cases(mw, orc, ar):
     A = P.laplacian_2d(30)
     M = mw.CSRMatrix.from_csr(A)
-    r = mw.solve(M, dev(np.zeros(A.n)), "qqf", 1e-10, 50, x0=dev(np.ones((4, A.n)), np.float32))
+    r = mw.solve(M, dev(np.zeros(A.n)), ar, 1e-10, 50, x0=dev(np.ones((4, A.n)), np.float32))
     assert (r.iters, r.status, r.relres) == (0, 0, 0.0) and np.all(r.x.cpu().numpy() == 0)
     b = P.matvec_exact(A, np.ones(A.n))
     x0 = np.zeros((4, A.n))
     x0[0] = 1.0
-    r = mw.solve(M, dev(b), "qqf", 1e-10, 50, x0=dev(x0, np.float32))       # r0 = 0 exactly
+    r = mw.solve(M, dev(b), ar, 1e-10, 50, x0=dev(x0, np.float32))       # r0 = 0 exactly
     assert (r.iters, r.status, r.relres) == (0, 0, 0.0) and np.array_equal(r.x.cpu().numpy(), x0)
-    r = mw.solve(M, dev(b), "qqf", 1e-10, 0)
-    xo, ito, rro, sto = orc.cg("qqf", A, b, tol=1e-10, maxit=0, plan=M.plan)
+    r = mw.solve(M, dev(b), ar, 1e-10, 0)
+    xo, ito, rro, sto = orc.cg(ar, A, b, tol=1e-10, maxit=0, plan=M.plan)
     assert (r.iters, r.status) == (ito, sto) == (0, 1) and r.relres == rro
     one = P.CSR(1, np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([3.0]))
     M1 = mw.CSRMatrix.from_csr(one)
-    _check(mw, orc, M1, one, np.array([1.0]), 1e-30, 5, "n=1")
+    _check(mw, orc, M1, one, np.array([1.0]), 1e-30, 5, "n=1", ar=ar)
     E = P.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
-    r = mw.solve(mw.CSRMatrix.from_csr(E), dev(np.zeros(0)), "qqf", 1e-10, 10)
+    r = mw.solve(mw.CSRMatrix.from_csr(E), dev(np.zeros(0)), ar, 1e-10, 10)
     assert (r.iters, r.status, r.relres) == (0, 0, 0.0) and tuple(r.x.shape) == (4, 0)
 
 
-def test_host_buffers(mw, orc):
+def test_host_buffers(mw, orc, ar):
     A = P.diffusion_2d(40, 8)
     b = P.rhs_uniform(A.n, 79)
     M = mw.CSRMatrix.from_csr(A)
-    x, it, rr, st = mw.solve_host(M, b, "qqf", 1e-20, 400)
-    xo, ito, rro, sto = orc.cg("qqf", A, b, tol=1e-20, maxit=400, plan=M.plan)
+    x, it, rr, st = mw.solve_host(M, b, ar, 1e-20, 400)
+    xo, ito, rro, sto = orc.cg(ar, A, b, tol=1e-20, maxit=400, plan=M.plan)
     assert (it, st) == (ito, sto) and x.dtype == np.float32 and same_bits(x, xo)
 
 
-def test_unsupported_paths_rejected(mw):
+def test_unsupported_paths_rejected(mw, ar):
     import torch
     from paper_2510_13536_gb300._capi import MWCGError
     A = P.laplacian_2d(20)
     M = mw.CSRMatrix.from_csr(A)
     b = dev(P.rhs_uniform(A.n, 80))
     with pytest.raises(MWCGError):
-        mw.solve_bicgstab(M, b, "qqf", 1e-10, 10)
+        mw.solve_bicgstab(M, b, ar, 1e-10, 10)
     with pytest.raises(MWCGError):
-        mw.solve_batched([M], [b], "qqf", 1e-10, 10)
+        mw.solve_batched([M], [b], ar, 1e-10, 10)
     with pytest.raises(MWCGError):
-        mw.adjoint(M, torch.zeros((2, A.n), dtype=torch.float64, device="cuda"), b, "qqf", 1e-10, 10)
+        mw.adjoint(M, torch.zeros((2, A.n), dtype=torch.float64, device="cuda"), b, ar, 1e-10, 10)
     M.preconditioner = "jacobi"
     with pytest.raises(MWCGError):
-        mw.solve(M, b, "qqf", 1e-10, 10)
+        mw.solve(M, b, ar, 1e-10, 10)
     M.preconditioner = "none"
-    assert mw.solve(M, b, "qqf", 1e-10, 200).status == 0
+    assert mw.solve(M, b, ar, 1e-10, 200).status == 0

@@ -39,11 +39,11 @@ def test_noalloc_dot_equals_allocating_dot_on_consecutive_calls(env):
     torch, L, mw = env
     rng = np.random.default_rng(21)
     for call in range(2):                                   # two calls in a row reuse the same scratch
-        for arith in ("qtw", "dw", "qdw", "tw", "fp64"):
+        for arith in ("qtw", "dw", "qdw", "tw", "fp64", "qw", "qqw", "qqw_nn"):
             a = mw.arith_id(arith)
             w = mw.words(arith)
             for n, G in ((70001, 152), (5000, 1024), (257, 3), (1, 1)):
-                scale = np.array([1.0, 1e-17, 1e-34][:w])[:, None]
+                scale = np.array([1.0, 1e-17, 1e-34, 1e-51][:w])[:, None]
                 u = torch.as_tensor(rng.standard_normal((w, n)) * scale, device="cuda")
                 v = torch.as_tensor(rng.standard_normal((w, n)) * scale, device="cuda")
                 rc, got = _noalloc_dot(torch, L, a, u, v, G)
@@ -58,3 +58,5 @@ def test_noalloc_dot_rejects_oversized_grid(env):
     rc, _ = _noalloc_dot(torch, L, 4, u, u, 1025)
     assert rc == -1
     assert b"1..1024" in L.mwcg_last_error()
+    assert L.mwcg_dot_noalloc(mw.arith_id("qqf"), 10, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                              1, None, ctypes.c_void_p(u.data_ptr())) == -1     # QQF is not supported
