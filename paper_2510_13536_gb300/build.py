@@ -24,7 +24,7 @@ SOURCES = ["capi.cu", "batched.cu", "batched_k00.cu", "batched_k01.cu", "batched
            "batched_k11.cu", "batched_k12.cu", "noalloc.cu", "probe.cu", "precond.cu", "inst_fp64.cu", "inst_dw.cu",
            "inst_qdw.cu", "inst_tw.cu", "inst_qtw.cu", "inst_qw.cu", "inst_qqw.cu", "inst_qqf.cu", "inst_qf.cu", "inst_bicg_a.cu",
            "inst_bicg_b.cu", "inst_bicg_c.cu"]
-HEADERS = ["tma.cuh", "mw_device.cuh", "mw_device4.cuh", "mw_float.cuh", "mw_int.cuh", "cg_kernels.cuh", "cg_float.cuh",
+HEADERS = ["mw_device.cuh", "mw_device4.cuh", "mw_float.cuh", "mw_int.cuh", "cg_kernels.cuh", "cg_float.cuh",
            "bicg_kernels.cuh", "batched.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -59,24 +59,6 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
-    # MWCG_EFT=0|1|2 selects the TwoSum implementation and MWCG_QTS_INT=1 the
-    # integer-pipe QuickTwoSum (same results; for A/B timing); MWCG_NATIVE_EFT=1
-    # is MWCG_EFT=0.
-    if os.environ.get("MWCG_NATIVE_EFT") == "1":
-        extra.append("-DMWCG_NATIVE_EFT")
-    if os.environ.get("MWCG_EFT") in ("0", "1", "2"):
-        extra.append("-DMWCG_EFT=" + os.environ["MWCG_EFT"])
-    if os.environ.get("MWCG_QTS_INT") == "1":
-        extra.append("-DMWCG_QTS_INT=1")
-    for key in ("MWCG_QTW_P_SPMV", "MWCG_QTW_P_VEC", "MWCG_DW_P_SPMV", "MWCG_DW_P_VEC", "MWCG_QDW_P_SPMV",
-                "MWCG_QDW_P_VEC", "MWCG_TW_P", "MWCG_ILP_FP64", "MWCG_ILP_MW", "MWCG_CHUNK_FP64", "MWCG_ILP_SPMV_MW", "MWCG_MINB_MW", "MWCG_MINB_FP64",
-                ):
-        if os.environ.get(key, "").isdigit():
-            extra.append(f"-D{key}={os.environ[key]}")
-    if os.environ.get("MWCG_ADD_FMA") in ("1", "2"):
-        extra.append("-DMWCG_ADD_FMA=" + os.environ["MWCG_ADD_FMA"])
-    if os.environ.get("MWCG_TP_INT") in ("0", "1"):
-        extra.append("-DMWCG_TP_INT=" + os.environ["MWCG_TP_INT"])
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

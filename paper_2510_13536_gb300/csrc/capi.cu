@@ -166,9 +166,6 @@ const mwk::BiTable* bitable(int arith) {
 }
 
 constexpr int32_t kMaxIt = 1 << 30;
-// Zeroed entries past the end of the device CSR arrays: the SpMV's L2
-// prefetches widen their ranges to 16-byte boundaries.
-constexpr int64_t kRpPad = 1, kValPad = 2, kColPad = 4;
 
 
 
@@ -759,9 +756,9 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
     return code;
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&A->rp, sizeof(int64_t) * (n + 1 + kRpPad))) != cudaSuccess ||
-      (nnz && (e = cudaMalloc(&A->col, sizeof(int32_t) * (nnz + kColPad))) != cudaSuccess) ||
-      (nnz && (e = cudaMalloc(&A->val, sizeof(double) * (nnz + kValPad))) != cudaSuccess) ||
+  if ((e = cudaMalloc(&A->rp, sizeof(int64_t) * (n + 1))) != cudaSuccess ||
+      (nnz && (e = cudaMalloc(&A->col, sizeof(int32_t) * nnz)) != cudaSuccess) ||
+      (nnz && (e = cudaMalloc(&A->val, sizeof(double) * nnz)) != cudaSuccess) ||
       (e = cudaMalloc(&A->part, sizeof(double) * mwk::PART * kMaxG)) != cudaSuccess ||
       (e = cudaMalloc(&A->st, sizeof(mwk::DevState))) != cudaSuccess ||
       (e = cudaMallocHost(&A->h_st, sizeof(mwk::DevState))) != cudaSuccess)
@@ -772,9 +769,6 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
           cudaSuccess ||
       (nnz && (e = cudaMemcpyAsync(A->col, col, sizeof(int32_t) * nnz, kind, s)) != cudaSuccess) ||
       (nnz && (e = cudaMemcpyAsync(A->val, val, sizeof(double) * nnz, kind, s)) != cudaSuccess) ||
-      (e = cudaMemsetAsync(A->rp + n + 1, 0, sizeof(int64_t) * kRpPad, s)) != cudaSuccess ||
-      (nnz && (e = cudaMemsetAsync(A->col + nnz, 0, sizeof(int32_t) * kColPad, s)) != cudaSuccess) ||
-      (nnz && (e = cudaMemsetAsync(A->val + nnz, 0, sizeof(double) * kValPad, s)) != cudaSuccess) ||
       (e = cudaMemsetAsync(A->st, 0, sizeof(mwk::DevState), s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cleanup(fail(MWCG_ERR_CUDA, "copy to device: %s", cudaGetErrorString(e)));

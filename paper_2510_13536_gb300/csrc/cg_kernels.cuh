@@ -28,7 +28,6 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "mw_device.cuh"
-#include "tma.cuh"
 
 namespace mwk {
 
@@ -352,9 +351,6 @@ __device__ __forceinline__ void row_accumulate(const Csr& M, const double* __res
   }
 }
 
-// Prefetch distance of the SpMV, in passes over the block's tiles.
-constexpr int kPfPasses = 2;
-
 // POL: the instantiation that follows the handle's normalisation policy
 // (DevState norm_every / norm_mask).  The default instantiation implements
 // the default policy {1, NORM_R} with no tests at all: it never normalises
@@ -392,40 +388,10 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
   const int64_t ntiles = (n + R - 1) / R;
   T acc = A::zero();
   bool pacc = false;
-  // L2 prefetch, issued by one lane of the block's last warp: on each pass,
-  // the row pointers of the tiles 2 kPfPasses passes ahead and the val / col
-  // segments of the tiles kPfPasses passes ahead (whose row pointers were
-  // prefetched earlier, so reading them hits L2).  The row's dependent loads
-  // (row pointer, then entry and column, then the gathered p) then find the
-  // CSR data in L2.
-  const bool pf_lane = threadIdx.x == TPB - 32;
-  const int64_t pass = (int64_t)A::ILP_SPMV * gridDim.x;
-  auto prefetch = [&](int64_t t0) {
-#pragma unroll
-    for (int u = 0; u < A::ILP_SPMV; ++u) {
-      const int64_t tr = t0 + 2 * kPfPasses * pass + (int64_t)u * gridDim.x;
-      if (tr < ntiles) tma::prefetch_l2_range(M.rp, tr * R, min((tr + 1) * R, n) + 1, 8);
-      const int64_t tv = t0 + kPfPasses * pass + (int64_t)u * gridDim.x;
-      if (tv < ntiles) {
-        const int64_t k0 = M.rp[tv * R], k1 = M.rp[min((tv + 1) * R, n)];
-        tma::prefetch_l2_range(M.val, k0, k1, 8);
-        tma::prefetch_l2_range(M.col, k0, k1, 4);
-      }
-    }
-  };
-  if (pf_lane && blockIdx.x < ntiles) {    // the first passes' row pointers
-    for (int64_t m = 0; m < 2 * kPfPasses; ++m)
-#pragma unroll
-      for (int u = 0; u < A::ILP_SPMV; ++u) {
-        const int64_t tr = blockIdx.x + m * pass + (int64_t)u * gridDim.x;
-        if (m >= kPfPasses && tr < ntiles) tma::prefetch_l2_range(M.rp, tr * R, min((tr + 1) * R, n) + 1, 8);
-      }
-  }
   // A::ILP_SPMV tiles (t, t+G, ...) per pass: their rows' chains are independent,
   // so interleaving them hides latency; the dot leaves are still added in
   // increasing tile order, so the summation order is unchanged.
-  for (int64_t t = blockIdx.x; t < ntiles; t += pass) {
-    if (pf_lane) prefetch(t);
+  for (int64_t t = blockIdx.x; t < ntiles; t += (int64_t)A::ILP_SPMV * gridDim.x) {
     T sum[A::ILP_SPMV];
     bool ps[A::ILP_SPMV];
     int64_t row[A::ILP_SPMV], kk[A::ILP_SPMV], ke[A::ILP_SPMV], len[A::ILP_SPMV];

@@ -22,32 +22,8 @@
 
 namespace mw {
 
-// fl(a+b) = fma(a, 1, b) and fl(a-b) = fma(b, -1, a) exactly (the products
-// are exact, the one rounding is the addition's; zero signs agree as well).
-// With MWCG_ADD_FMA=1 additions are issued that way, through inline PTX so the
-// compiler cannot fold the multiplication away, for GPUs whose FP64 FMA path
-// outruns the FP64 add path.
-#if defined(MWCG_ADD_FMA) && MWCG_ADD_FMA == 2
-// Multiplier read from constant memory, whose value the compiler cannot assume,
-// so the instruction stays an FMA.
-static __constant__ double c_pm_one[2] = {1.0, -1.0};
-__device__ __forceinline__ double dadd(double a, double b) { return __fma_rn(a, c_pm_one[0], b); }
-__device__ __forceinline__ double dsub(double a, double b) { return __fma_rn(b, c_pm_one[1], a); }
-#elif defined(MWCG_ADD_FMA) && MWCG_ADD_FMA == 1
-__device__ __forceinline__ double dadd(double a, double b) {
-  double r;
-  asm("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(r) : "d"(a), "d"(b));
-  return r;
-}
-__device__ __forceinline__ double dsub(double a, double b) {
-  double r;
-  asm("fma.rn.f64 %0, %1, 0dBFF0000000000000, %2;" : "=d"(r) : "d"(b), "d"(a));
-  return r;
-}
-#else
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
-#endif
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double dneg(double a) {
@@ -62,38 +38,13 @@ __device__ __forceinline__ bool nonzero(double a) {
   return (mwi::bits_of(a) << 1) != 0ULL;
 }
 
-// Algorithm 2, TwoSum, as printed (6 FP64 operations).  Its error term is the
-// exact rounding error of fl(a+b), so two cheaper sequences that produce the
-// same number are also provided (mw_int.cuh): the error recovered from the bit
-// patterns on the integer pipe (1 FP64 operation), and Fast2Sum after ordering
-// the operands by an integer magnitude comparison (3 FP64 operations).  Both
-// fall back to the printed sequence on the operands they do not cover.
-__device__ __forceinline__ void two_sum_printed(double a, double b, double& x, double& y) {
-  double s = dadd(a, b);
-  double z = dsub(s, a);
-  double t1 = dsub(a, dsub(s, z));
-  double t2 = dsub(b, z);
-  y = dadd(t1, t2);
-  x = s;
-}
-// Implementation of TwoSum, chosen at build time (all return the same bits):
-// MWCG_EFT = 0 the printed sequence (also -DMWCG_NATIVE_EFT), 1 the
-// integer-pipe recovery (default: fastest on GB300 for every arithmetic),
-// 2 Fast2Sum after an integer magnitude ordering.
-#ifndef MWCG_EFT
-#define MWCG_EFT 1
-#endif
-#if defined(MWCG_NATIVE_EFT)
-#undef MWCG_EFT
-#define MWCG_EFT 0
-#endif
-struct RnAdd { __device__ __forceinline__ double operator()(double a, double b) const { return __dadd_rn(a, b); } };
-struct RnSub { __device__ __forceinline__ double operator()(double a, double b) const { return __dsub_rn(a, b); } };
-
-// The printed sequences as out-of-line functions, for the rare operands the
-// cheaper paths decline.  Keeping them out of line stops the compiler from
-// executing part of them speculatively on every call (which measured as two
-// extra FP64 additions per TwoSum).
+// Algorithm 2, TwoSum.  Its error term is the exact rounding error of
+// fl(a+b), so it is recovered from the bit patterns of a, b and fl(a+b) on the
+// integer pipe (mwi::add_error, one FP64 operation instead of six), which
+// returns the same number as the printed sequence; the printed sequence runs
+// for the operands that path declines.  It is kept out of line so that the
+// compiler does not execute part of it speculatively on every call (measured
+// as two extra FP64 additions per TwoSum).
 static __device__ __noinline__ double two_sum_err_slow(double a, double b, double s) {
   const double z = dsub(s, a);
   return dadd(dsub(a, dsub(s, z)), dsub(b, z));
@@ -102,27 +53,12 @@ static __device__ __noinline__ double quick_two_sum_err_slow(double a, double b,
   return dadd(dsub(a, s), b);
 }
 
-__device__ __forceinline__ void two_sum_int(double a, double b, double& x, double& y) {
+__device__ __forceinline__ void two_sum(double a, double b, double& x, double& y) {
   const double s = dadd(a, b);
   double e;
   if (!mwi::add_error(a, b, s, e)) e = two_sum_err_slow(a, b, s);
   x = s;
   y = e;
-}
-__device__ __forceinline__ void two_sum_sorted(double a, double b, double& x, double& y) {
-  if (!mwi::sorted_two_sum(a, b, x, y, RnAdd{}, RnSub{})) {
-    x = dadd(a, b);
-    y = two_sum_err_slow(a, b, x);
-  }
-}
-__device__ __forceinline__ void two_sum(double a, double b, double& x, double& y) {
-#if MWCG_EFT == 0
-  two_sum_printed(a, b, x, y);
-#elif MWCG_EFT == 1
-  two_sum_int(a, b, x, y);
-#else
-  two_sum_sorted(a, b, x, y);
-#endif
 }
 // Fully integer-pipe variants (mwi::add_rn computes fl(a+b) itself): no FP64
 // instruction at all on the common path.  Used at call sites chosen per
@@ -141,15 +77,6 @@ __device__ __forceinline__ void two_sum_fullint(double a, double b, double& x, d
   y = e;
 }
 
-// QuickTwoSum with fl(a+b) on the FP64 pipe and the error on the integer pipe
-// where its precondition holds (the printed error otherwise).
-__device__ __forceinline__ void quick_two_sum_interr(double a, double b, double& x, double& y) {
-  const double s = dadd(a, b);
-  double e;
-  if (!(mwi::quick_exact(a, b) && mwi::add_error(a, b, s, e))) e = quick_two_sum_err_slow(a, b, s);
-  x = s;
-  y = e;
-}
 __device__ __forceinline__ void quick_two_sum_fullint(double a, double b, double& x, double& y) {
   double s, e;
   if (!mwi::add_rn(a, b, s)) s = dadd_slow(a, b);
@@ -158,79 +85,40 @@ __device__ __forceinline__ void quick_two_sum_fullint(double a, double b, double
   y = e;
 }
 
-// Algorithm 3, QuickTwoSum, as printed (3 FP64 operations; MWCG_QTS_INT=1
-// recovers the error on the integer pipe where the precondition holds).
+// Algorithm 3, QuickTwoSum, as printed (3 FP64 operations).
 __device__ __forceinline__ void quick_two_sum(double a, double b, double& x, double& y) {
-#if defined(MWCG_QTS_INT) && MWCG_QTS_INT == 1
-  const double s = dadd(a, b);
-  double e;
-  if (!(mwi::quick_exact(a, b) && mwi::add_error(a, b, s, e))) e = quick_two_sum_err_slow(a, b, s);
-  x = s;
-  y = e;
-#else
   double s = dadd(a, b);
   y = dadd(dsub(a, s), b);
   x = s;
-#endif
 }
 // Algorithm 4, TwoProdFMA.  two_prod_int recovers the error fma(a, b, -p) on
 // the integer pipe instead (mwi::mul_error, same bits), the FMA running only
 // for the operands that path declines.  Measured on GB300 it pays off where
-// the integer pipe has room: the double-word arithmetics use it, the
-// triple-word ones (whose kernels already keep the integer pipe busy) use the
-// FMA.  MWCG_TP_INT=0/1 forces one choice for every arithmetic.
+// the integer pipe has room: the double-word arithmetics use it (two_prod_w2),
+// the triple-word ones, whose kernels already keep the integer pipe busy, use
+// the FMA (two_prod).
 static __device__ __noinline__ double two_prod_err_slow(double a, double b, double p) { return dfma(a, b, -p); }
-__device__ __forceinline__ void two_prod_fma(double a, double b, double& x, double& y) {
+__device__ __forceinline__ void two_prod(double a, double b, double& x, double& y) {
   const double p = dmul(a, b);
   y = dfma(a, b, -p);
   x = p;
 }
-__device__ __forceinline__ void two_prod_int(double a, double b, double& x, double& y) {
+__device__ __forceinline__ void two_prod_w2(double a, double b, double& x, double& y) {
   const double p = dmul(a, b);
   double e;
   if (!mwi::mul_error(a, b, p, e)) e = two_prod_err_slow(a, b, p);
   y = e;
   x = p;
 }
-#if defined(MWCG_TP_INT) && MWCG_TP_INT == 1
-#define MWCG_TP_W2 two_prod_int
-#define MWCG_TP_W3 two_prod_int
-#elif defined(MWCG_TP_INT) && MWCG_TP_INT == 0
-#define MWCG_TP_W2 two_prod_fma
-#define MWCG_TP_W3 two_prod_fma
-#else
-#define MWCG_TP_W2 two_prod_int
-#define MWCG_TP_W3 two_prod_fma
-#endif
-__device__ __forceinline__ void two_prod(double a, double b, double& x, double& y) { MWCG_TP_W3(a, b, x, y); }
-__device__ __forceinline__ void two_prod_w2(double a, double b, double& x, double& y) { MWCG_TP_W2(a, b, x, y); }
 
 template <int W> struct MW { double w[W]; };
 
 // ---------------------------------------------------------------- FP64
-#ifndef MWCG_ILP_FP64
-#define MWCG_ILP_FP64 2
-#endif
-#ifndef MWCG_ILP_MW
-#define MWCG_ILP_MW 1
-#endif
-#ifndef MWCG_ILP_SPMV_MW
-#define MWCG_ILP_SPMV_MW 1
-#endif
-#ifndef MWCG_MINB_FP64
-#define MWCG_MINB_FP64 3
-#endif
-#ifndef MWCG_MINB_MW
-#define MWCG_MINB_MW 3
-#endif
-#ifndef MWCG_CHUNK_FP64
-#define MWCG_CHUNK_FP64 2
-#endif
 struct FP64 {
-  static constexpr int ILP = MWCG_ILP_FP64;   // rows in flight per thread (memory bound)
-  static constexpr int CHUNK = MWCG_CHUNK_FP64; // SpMV entries loaded ahead per row
-  static constexpr int ILP_SPMV = MWCG_ILP_FP64;
-  static constexpr int MINB = MWCG_MINB_FP64;  // blocks per SM the register budget must allow
+  static constexpr int ILP = 2;                // rows in flight per thread (memory bound)
+  static constexpr int CHUNK = 2;              // SpMV entries loaded ahead per row
+  static constexpr int ILP_SPMV = 2;
+  static constexpr int MINB = 3;               // blocks per SM the register budget must allow
   static constexpr int W = 1;
   static constexpr bool QUASI = false;
   static constexpr bool NORMALISES = false;   // A::normalize is the identity
@@ -265,18 +153,12 @@ __device__ __forceinline__ double qadd_(double a, double b) {
 // Policy P (bit mask, same results): bit 0 DWadd's TwoSum, bit 1 DWadd's two
 // plain additions, bit 2 DWadd's closing QuickTwoSum, bit 3 the closing
 // QuickTwoSum of DWmul / FP64 x DW, run entirely on the integer pipe.
-#ifndef MWCG_DW_P_SPMV
-#define MWCG_DW_P_SPMV 0
-#endif
-#ifndef MWCG_DW_P_VEC
-#define MWCG_DW_P_VEC 0
-#endif
-template <int P = MWCG_DW_P_VEC>
+template <int P = 0>
 struct DWt {
-  static constexpr int ILP = MWCG_ILP_MW;
+  static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
-  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_MW;
-  static constexpr int MINB = MWCG_MINB_MW;
+  static constexpr int ILP_SPMV = 1;
+  static constexpr int MINB = 3;
   static constexpr int W = 2;
   static constexpr bool QUASI = false;
   static constexpr bool NORMALISES = false;   // A::normalize is the identity
@@ -330,23 +212,17 @@ struct DWt {
   static __device__ __forceinline__ double collapse(const T& a) { return dadd(a.w[0], a.w[1]); }
 };
 using DW = DWt<>;
-using DW_S = DWt<MWCG_DW_P_SPMV>;
+using DW_S = DWt<0>;            // SpMV instantiation (the measured-best policy is the default)
 
 // ---------------------------------------------------------------- QDW
 // Policy P: bit 0 QDWadd's TwoSum, bit 1 its two plain additions, bit 2 the
 // normalising QuickTwoSum, run entirely on the integer pipe (same bits).
-#ifndef MWCG_QDW_P_SPMV
-#define MWCG_QDW_P_SPMV 0
-#endif
-#ifndef MWCG_QDW_P_VEC
-#define MWCG_QDW_P_VEC 0
-#endif
-template <bool NORM, int P = MWCG_QDW_P_VEC>
+template <bool NORM, int P = 0>
 struct QDWt {
-  static constexpr int ILP = MWCG_ILP_MW;
+  static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
-  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_MW;
-  static constexpr int MINB = MWCG_MINB_MW;
+  static constexpr int ILP_SPMV = 1;
+  static constexpr int MINB = 3;
   static constexpr int W = 2;
   static constexpr bool QUASI = true;
   static constexpr bool NORMALISES = NORM;   // false for the NN variants
@@ -393,8 +269,8 @@ struct QDWt {
 };
 using QDW = QDWt<true>;
 using QDW_NN = QDWt<false>;
-using QDW_S = QDWt<true, MWCG_QDW_P_SPMV>;
-using QDW_NN_S = QDWt<false, MWCG_QDW_P_SPMV>;
+using QDW_S = QDWt<true, 0>;     // SpMV instantiations (the default policy measured best)
+using QDW_NN_S = QDWt<false, 0>;
 
 // ---------------------------------------------------------------- QTW
 // Policy P (bit mask, same results for every value): which TwoSums and plain
@@ -405,18 +281,12 @@ using QDW_NN_S = QDWt<false, MWCG_QDW_P_SPMV>;
 // instructions, about 25 clocks of the 64-lane integer pipe per warp against 16
 // of the FP64 pipe for a DADD, so only the SpMV's FP64 x QTW c3 addition gains
 // (2%); every wider choice, and any choice in the vector kernels, is slower.
-#ifndef MWCG_QTW_P_SPMV
-#define MWCG_QTW_P_SPMV 8
-#endif
-#ifndef MWCG_QTW_P_VEC
-#define MWCG_QTW_P_VEC 0
-#endif
-template <bool NORM, int P = MWCG_QTW_P_VEC>
+template <bool NORM, int P = 0>
 struct QTWt {
-  static constexpr int ILP = MWCG_ILP_MW;
+  static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
-  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_MW;
-  static constexpr int MINB = MWCG_MINB_MW;
+  static constexpr int ILP_SPMV = 1;
+  static constexpr int MINB = 3;
   static constexpr int W = 3;
   static constexpr bool QUASI = true;
   static constexpr bool NORMALISES = NORM;   // false for the NN variants
@@ -487,21 +357,16 @@ struct QTWt {
 };
 using QTW = QTWt<true>;
 using QTW_NN = QTWt<false>;
-// SpMV-kernel instantiations (their own policy).
-using QTW_S = QTWt<true, MWCG_QTW_P_SPMV>;
-using QTW_NN_S = QTWt<false, MWCG_QTW_P_SPMV>;
+// SpMV-kernel instantiations: the FP64 x QTW c3 addition on the integer pipe.
+using QTW_S = QTWt<true, 8>;
+using QTW_NN_S = QTWt<false, 8>;
 
 // ---------------------------------------------------------------- TW
-// Policy MWCG_TW_P (same results): bit 0 the renormalisation's QuickTwoSums
-// take their error term from the integer pipe.
-#ifndef MWCG_TW_P
-#define MWCG_TW_P 0
-#endif
 struct TW {
-  static constexpr int ILP = MWCG_ILP_MW;
+  static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
-  static constexpr int ILP_SPMV = MWCG_ILP_SPMV_MW;
-  static constexpr int MINB = MWCG_MINB_MW;
+  static constexpr int ILP_SPMV = 1;
+  static constexpr int MINB = 3;
   static constexpr int W = 3;
   static constexpr bool QUASI = false;
   static constexpr bool NORMALISES = false;   // A::normalize is the identity
@@ -536,8 +401,7 @@ struct TW {
     for (int i = 0; i + 1 < N; ++i) {
       if (!stop) {
         double hi, lo;
-        if constexpr ((MWCG_TW_P & 1) != 0) quick_two_sum_interr(eps, e[i + 1], hi, lo);
-        else quick_two_sum(eps, e[i + 1], hi, lo);
+        quick_two_sum(eps, e[i + 1], hi, lo);
         if (j == 0) r0 = hi; else if (j == 1) r1 = hi; else r2 = hi;
         if (nonzero(lo)) {
           if (j >= 2) stop = true;

@@ -18,16 +18,13 @@
 
 namespace mw {
 
-#ifndef MWCG_MINB_MW4
-#define MWCG_MINB_MW4 3
-#endif
 
 template <bool NORM>
 struct QQWt {
   static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
   static constexpr int ILP_SPMV = 1;
-  static constexpr int MINB = MWCG_MINB_MW4;
+  static constexpr int MINB = 3;
   static constexpr int W = 4;
   static constexpr bool QUASI = true;
   static constexpr bool NORMALISES = NORM;   // false for the NN variant
@@ -129,7 +126,7 @@ struct QW {
   static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
   static constexpr int ILP_SPMV = 1;
-  static constexpr int MINB = MWCG_MINB_MW4;
+  static constexpr int MINB = 3;
   static constexpr int W = 4;
   static constexpr bool QUASI = false;
   static constexpr bool NORMALISES = false;   // results are always normalised

@@ -111,31 +111,6 @@ MWI_HD bool add_error(double a, double b, double x, double& y) {
   return true;
 }
 
-// TwoSum by ordering: with |h| >= |l| the three-operation Fast2Sum
-// (s = h + l, z = s - h, y = l - z) returns the exact error, the same number as
-// the printed six-operation TwoSum.  Ordering the operands costs one integer
-// comparison of the magnitude bits instead of three FP64 operations.  Two
-// cases are patched to keep the bits identical to the printed sequence: a zero
-// l gives y = +0 (Fast2Sum would return -0 for h = +0, l = -0), and an
-// overflow-prone or non-finite h declines (returns false) so the caller runs
-// the printed sequence.  FP64 operations are passed in as the caller's
-// round-to-nearest primitives.
-template <class Add, class Sub>
-MWI_HD bool sorted_two_sum(double a, double b, double& x, double& y, Add add, Sub sub) {
-  const uint64_t ua = bits_of(a), ub = bits_of(b);
-  const bool swap = (ua & kAbs) < (ub & kAbs);
-  const uint64_t hb = swap ? ub : ua;
-  if (((hb >> 52) & 0x7ff) >= 2046) return false;
-  const double h = swap ? b : a;
-  const double l = swap ? a : b;
-  const double s = add(h, l);
-  const double z = sub(s, h);
-  const double e = sub(l, z);
-  x = s;
-  y = (((swap ? ua : ub) & kAbs) == 0) ? 0.0 : e;
-  return true;
-}
-
 // x = fl(a + b) (IEEE binary64, round to nearest, ties to even) on the integer
 // pipe.  Operands ordered by magnitude, |h| >= |l|; significands extended by
 // three guard bits; l aligned to h with the bits shifted out folded into a

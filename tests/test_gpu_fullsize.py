@@ -37,7 +37,7 @@ def c2(mw):
     return A, M, torch.as_tensor(b, device="cuda"), tol, maxit
 
 
-@pytest.mark.parametrize("arith", ["fp64", "dw", "qtw", "qqf"])
+@pytest.mark.parametrize("arith", ["fp64", "dw", "qtw", "qqf", "qf"])
 def test_c2_solution_bits_match_oracle_full_solve(mw, c2, arith):
     g = json.load(open(GOLD))
     if arith not in g:
@@ -49,14 +49,14 @@ def test_c2_solution_bits_match_oracle_full_solve(mw, c2, arith):
     e = g[arith]
     assert (r.iters, r.status) == (e["iters"], e["status"])
     assert float(r.relres).hex() == e["relres_hex"]
-    x = r.x.cpu().numpy().astype(np.float64)      # QQF's FP32 words as the oracle stores them
+    x = r.x.cpu().numpy().astype(np.float64)      # QQF's / QF's FP32 words as the oracle stores them
     for i, words in e["samples"].items():
         assert [float(x[k, int(i)]).hex() for k in range(x.shape[0])] == words
     assert hashlib.sha256(np.ascontiguousarray(x).view(np.uint64).tobytes()).hexdigest() == e["x_sha256"]
 
 
 @pytest.mark.parametrize("arith,bound", [("fp64", 1e-9), ("dw", 1e-10), ("qdw", 1e-10), ("qtw", 1e-10),
-                                         ("qqf", 1e-10)])
+                                         ("qqf", 1e-10), ("qf", 1e-10)])
 def test_c2_twin_forward_error(mw, arith, bound):
     import torch
     A, b, tol, maxit = P.workload("c2_twin")

@@ -23,15 +23,6 @@ SHIM = r"""
 extern "C" void add_error_batch(long n, const double* a, const double* b, const double* x, double* y, int* ok) {
   for (long i = 0; i < n; ++i) { double t = 0.0; ok[i] = mwi::add_error(a[i], b[i], x[i], t) ? 1 : 0; y[i] = t; }
 }
-static double add_(double a, double b) { return a + b; }
-static double sub_(double a, double b) { return a - b; }
-extern "C" void sorted_two_sum_batch(long n, const double* a, const double* b, double* x, double* y, int* ok) {
-  for (long i = 0; i < n; ++i) {
-    double s = 0.0, t = 0.0;
-    ok[i] = mwi::sorted_two_sum(a[i], b[i], s, t, add_, sub_) ? 1 : 0;
-    x[i] = s; y[i] = t;
-  }
-}
 #include <cmath>
 extern "C" void mul_error_batch(long n, const double* a, const double* b, double* e, double* ref, int* ok) {
   for (long i = 0; i < n; ++i) {
@@ -79,7 +70,6 @@ def shim(tmp_path_factory):
     P = ctypes.c_void_p
     L.add_error_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.quick_exact_batch.argtypes = [ctypes.c_long, P, P, P]
-    L.sorted_two_sum_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.mul_error_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.add_rn_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.pow2_dx_batch.argtypes = [ctypes.c_long, ctypes.c_int, P, P, P, P]
@@ -182,22 +172,6 @@ def test_exact_rational_error(shim):
     for i in idx[::7]:
         assert Fraction(float(y[i])) == Fraction(float(a[i])) + Fraction(float(b[i])) - Fraction(float(x[i]))
         assert not (y[i] == 0 and np.signbit(y[i]))        # zero error is +0, as the printed sequence gives
-
-
-@pytest.mark.parametrize("seed", [4, 5])
-def test_sorted_fast2sum_matches_printed_two_sum(shim, seed):
-    a, b = inputs(seed, 400_000)
-    for (u, v) in ((a, b), (b, a)):
-        xr, yr = printed_two_sum(u, v)
-        x = np.zeros_like(u)
-        y = np.zeros_like(u)
-        ok = np.zeros(u.size, dtype=np.int32)
-        shim.sorted_two_sum_batch(u.size, _p(u), _p(v), _p(x), _p(y), _p(ok))
-        ok = ok.astype(bool)
-        big = np.maximum(np.abs(u), np.abs(v))
-        assert np.array_equal(~ok, ~(big < 2.0 ** 1023))       # declines only for overflow-prone / non-finite
-        assert np.array_equal(x[ok].view(np.uint64), xr[ok].view(np.uint64))
-        assert np.array_equal(y[ok].view(np.uint64), yr[ok].view(np.uint64))
 
 
 def test_mul_error_matches_two_prod_fma(shim):
