@@ -969,6 +969,13 @@ def run_gpu(args):
         grad = run_c5(torch, mw, P, False, args.fd_bench)
         grad["qtw_over_dw"] = qtw_over_dw_general(torch, mw, P)
 
+    # The automatic plan each arithmetic of this line ran with, and the SpMV
+    # timings (ms per lane count V) the autotuner measured to choose it.
+    autotune = {}
+    for ar in dict.fromkeys((arith, "dw")):
+        pl, tm = M.tuning(ar)
+        autotune[ar] = {"plan": list(pl), "spmv_ms_by_V": {str(v): t for v, t in tm.items()}}
+
     alg_bytes_iter = 12 * A.nnz + 8 * (A.n + 1) + 11 * elem * A.n
     out = {
         "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
@@ -982,6 +989,7 @@ def run_gpu(args):
         "dw": {"time_s": min(dw_ms) / 1e3, "iters": dw_it},
         "qtw_over_dw_time": (ms / min(dw_ms)) if arith == "qtw" else None,
         "kernel_ms": {"spmv_dot": kms[0], "update_dot": kms[1], "p_update": kms[2]},
+        "autotune": autotune,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": args.steps * (3 + 3 * it),

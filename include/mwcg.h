@@ -105,8 +105,17 @@ enum {
  *      kernels) rows, tile t belongs to block t mod G, each block slot sums
  *      its rows across the block's tiles in increasing order, then slots and
  *      blocks are combined by pairwise trees.
- * mwcg_create_csr picks the plan from the row-length distribution; tests
- * read it with mwcg_get_plan and may pin one with mwcg_set_plan. */
+ * Automatic plans (the autotuner; the paper fixes no order, Sec. IV-B):
+ * mwcg_create_csr derives, per arithmetic, a plan from the row-length
+ * distribution with an FP64-instruction cost model (V; G = one resident wave
+ * of 3 blocks per SM, or the one-cluster size for small systems).  At the
+ * first call in an arithmetic the SpMV is timed under the model's best lane
+ * counts (at most three, each within twice the best model cost) on a
+ * synthetic vector with every word populated; another lane count replaces
+ * the model's only when it is at least 4% faster.  The result is cached per
+ * handle and arithmetic.  Because a measurement can decide V, and V the
+ * summation order, pin a plan with mwcg_set_plan where results must be
+ * reproducible bit for bit across processes or GPUs. */
 typedef struct {
   int32_t V;
   int32_t T;
@@ -147,9 +156,19 @@ int mwcg_update_values(mwcg_csr* A, const double* val, int on_device, void* stre
 
 int64_t mwcg_n(const mwcg_csr* A);
 int64_t mwcg_nnz(const mwcg_csr* A);
+/* The plan of the handle's last call (before any call: the pinned plan, or
+ * the automatic QTW plan). */
 int mwcg_get_plan(const mwcg_csr* A, mwcg_plan* out);
-/* Pin a plan (V power of two in 1..32, T = 256, G in 1..1024); MWCG_ERR_ARG otherwise. */
+/* Pin a plan for every arithmetic (V power of two in 1..32, T = 256, G in
+ * 1..1024; MWCG_ERR_ARG otherwise).  plan = NULL returns to the automatic
+ * plans. */
 int mwcg_set_plan(mwcg_csr* A, const mwcg_plan* plan);
+/* The plan a call in `arith` uses: the pinned plan, or the arithmetic's
+ * automatic plan, timed first (on `stream`, synchronised) if this is the
+ * handle's first call in that arithmetic.  spmv_ms (optional, double[6]):
+ * the measured SpMV time in ms for V = 1, 2, 4, ..., 32, 0 where not timed
+ * (all 0 for a pinned plan or a system too small to time). */
+int mwcg_get_plan_for(mwcg_csr* A, int arith, void* stream, mwcg_plan* out, double* spmv_ms);
 
 /* Normalisation policy of the quasi arithmetics (QDW, QTW), per matrix handle.
  * Sec. IV-D normalises the residual r once per iteration, right after its

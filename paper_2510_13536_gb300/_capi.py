@@ -27,7 +27,7 @@ ERRORS = {-1: "MWCG_ERR_ARG", -2: "MWCG_ERR_CUDA", -3: "MWCG_ERR_GUARD", -4: "MW
 # Every symbol declared in include/mwcg.h.
 EXPORTS = [
     "mwcg_words", "mwcg_last_error", "mwcg_create_csr", "mwcg_destroy_csr", "mwcg_update_values",
-    "mwcg_n", "mwcg_nnz", "mwcg_get_plan", "mwcg_set_plan", "mwcg_solve", "mwcg_solve_host",
+    "mwcg_n", "mwcg_nnz", "mwcg_get_plan", "mwcg_set_plan", "mwcg_get_plan_for", "mwcg_solve", "mwcg_solve_host",
     "mwcg_solve_history", "mwcg_solve_batched", "mwcg_adjoint", "mwcg_spmv", "mwcg_dot",
     "mwcg_word_op", "mwcg_collapse", "mwcg_profile_kernels", "mwcg_batched_cluster_size",
     "mwcg_dot_noalloc", "mwcg_probe_peak", "mwcg_set_normalization", "mwcg_get_normalization",
@@ -73,6 +73,7 @@ def load(path: str | None = None):
         "mwcg_nnz": (i64, [P]),
         "mwcg_get_plan": (ctypes.c_int, [P, ctypes.POINTER(Plan)]),
         "mwcg_set_plan": (ctypes.c_int, [P, ctypes.POINTER(Plan)]),
+        "mwcg_get_plan_for": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.POINTER(Plan), P]),
         "mwcg_set_normalization": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_uint32]),
         "mwcg_set_preconditioner": (ctypes.c_int, [P, ctypes.c_int]),
         "mwcg_get_preconditioner": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int)]),

@@ -211,12 +211,23 @@ struct mwcg_csr {
   GraphCache graphs[kNArith];
   GraphCache bigraphs[kNArith];  // BiCGStab
   double* bws = nullptr;         // BiCGStab: rh, s, t (four words each), lazily allocated
-  std::vector<int64_t> rowlen;  // host copy of row lengths (plan selection)
+  // Plans.  `plan` is the plan of the current call.  A plan set with
+  // mwcg_set_plan is pinned for every arithmetic; otherwise each arithmetic
+  // has its own automatic plan: the cost model's choice at creation, checked
+  // by timing the SpMV under the model's best candidates at the first call in
+  // that arithmetic (tune_plan).
+  bool pinned = false;
+  mwcg_plan pinned_plan{1, 256, 1};
+  mwcg_plan auto_plan[kNArith];
+  bool tuned[kNArith] = {};
+  double tune_ms[kNArith][6] = {};   // SpMV ms per candidate V = 2^j (0: not timed)
+  double passes[6] = {}, warps[6] = {};   // row-length statistics of the cost model
   int32_t norm_every = 1;       // normalisation policy of the quasi arithmetics
   uint32_t norm_mask = mwk::NORM_R;
   int prec = MWCG_PREC_NONE;    // preconditioner
   double* w = nullptr;          // Jacobi weights, rebuilt after a value update
   int* w_bad = nullptr;         // device flag of the weights kernel
+  int64_t* vbad = nullptr;      // device word of mwcg_update_values' check
   bool w_valid = false;
   bool w_undefined = false;     // a diagonal entry missing, not positive or not finite
 };
@@ -247,39 +258,62 @@ void op_costs(int arith, double& mac, double& add) {
   }
 }
 
-// Plan selection from the row-length sequence.  The multi-word SpMV is bound
-// by the FP64 pipe, and a warp instruction costs the same whatever its
+// Plan model from the row-length sequence.  The multi-word SpMV is bound by
+// the FP64 pipe, and a warp instruction costs the same whatever its
 // active-lane count, so the cost of V lanes per row is, per warp (32/V
 // consecutive rows), the longest row's ceil(len/V) multiply-adds plus
 // log2(V) tree adds.  FP64 arithmetic is memory bound: there the cost adds the
-// number of 32-lane load rounds, which favours wider rows.
-mwcg_plan choose_plan(const std::vector<int64_t>& len, int sms, int arith, int small_cluster) {
-  double mac, add;
-  op_costs(arith, mac, add);
+// number of 32-lane load rounds, which favours wider rows.  row_stats keeps,
+// for V = 2^j, the sum over warps of ceil(max len / V) and the warp count.
+void row_stats(const std::vector<int64_t>& len, double* passes, double* warps) {
   const int64_t n = (int64_t)len.size();
-  int bestV = 1;
-  double best = -1;
-  for (int V = 1; V <= 32; V <<= 1) {
-    const int rows_per_warp = 32 / V;
-    int lg = 0;
-    while ((1 << lg) < V) ++lg;
-    double cost = 0;
+  for (int j = 0; j < 6; ++j) {
+    const int V = 1 << j, rows_per_warp = 32 / V;
+    double ps = 0, ws = 0;
     for (int64_t r0 = 0; r0 < n; r0 += rows_per_warp) {
       int64_t mx = 0;
       for (int64_t r = r0; r < std::min(n, r0 + rows_per_warp); ++r) mx = std::max(mx, len[r]);
-      const double passes = (double)((mx + V - 1) / V);
-      cost += passes * mac + lg * add;
-      if (arith == MWCG_FP64) cost += passes * 2.0;
+      ps += (double)((mx + V - 1) / V);
+      ws += 1;
     }
-    if (best < 0 || cost < best * 0.98) { best = cost; bestV = V; }
+    passes[j] = ps;
+    warps[j] = ws;
   }
+}
+double plan_cost(const double* passes, const double* warps, int j, int arith) {
+  double mac, add;
+  op_costs(arith, mac, add);
+  double c = passes[j] * mac + j * add * warps[j];
+  if (arith == MWCG_FP64) c += passes[j] * 2.0;
+  return c;
+}
+// Lane counts 2^j ranked by model cost: the best first (a lane count is
+// preferred to a narrower one only when it is 2% cheaper).
+std::vector<int> ranked_lanes(const double* passes, const double* warps, int arith) {
+  int best = 0;
+  double bc = plan_cost(passes, warps, 0, arith);
+  for (int j = 1; j < 6; ++j) {
+    const double c = plan_cost(passes, warps, j, arith);
+    if (c < bc * 0.98) { bc = c; best = j; }
+  }
+  std::vector<int> order{best};
+  std::vector<std::pair<double, int>> rest;
+  for (int j = 0; j < 6; ++j)
+    if (j != best) rest.push_back({plan_cost(passes, warps, j, arith), j});
+  std::sort(rest.begin(), rest.end());
+  for (auto& r : rest) order.push_back(r.second);
+  return order;
+}
+mwcg_plan choose_plan(const double* passes, const double* warps, int64_t n, int sms, int arith, int small_cluster,
+                      int minb) {
   mwcg_plan p;
-  p.V = bestV;
+  p.V = 1 << ranked_lanes(passes, warps, arith)[0];
   p.T = mwk::TPB;
   const int64_t tiles = (n + mwk::TPB - 1) / mwk::TPB;
-  // One resident wave: the kernels' launch bounds keep A::MINB = 3 blocks of
-  // 256 threads per SM within the register file.
-  p.G = (int)std::max<int64_t>(1, std::min<int64_t>(3 * (int64_t)sms, std::min<int64_t>(tiles, kMaxG)));
+  // One resident wave: the kernels' launch bounds keep `minb` blocks of 256
+  // threads per SM within the register file (3 for the FP64-word
+  // arithmetics, 4 for the FP32-word ones).
+  p.G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)minb * sms, std::min<int64_t>(tiles, kMaxG)));
   // A system of at most `small_cluster` tiles is solved by one thread-block
   // cluster in a single launch (see run_solve).  With G >= tiles every tile is
   // its own block, so G = small_cluster gives the same summation order as
@@ -433,6 +467,115 @@ int ensure_ws(mwcg_csr* A) {
   return MWCG_OK;
 }
 
+// Smallest k with val[k] not finite, by an atomic minimum (*first starts
+// above any index).
+__global__ void k_first_nonfinite(const double* __restrict__ val, int64_t nnz, int64_t* first) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(val[k])) atomicMin(reinterpret_cast<unsigned long long*>(first), (unsigned long long)k);
+}
+
+// Synthetic SpMV input for plan timing: every word of p populated (a vector
+// whose lower words are zero runs faster than the iterates do).  FP64 words:
+// word k of element i is +-(1 + h_i 2^-32) 2^(-53 k); FP32 words (packed two
+// to a slot): word j is +-(1 + h_i 2^-32) 2^(-24 j); h_i a 32-bit hash of i.
+__global__ void k_fill_probe(double* v, int64_t n, int slots, int fp32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ULL;
+    h ^= h >> 29;
+    const double m = (1.0 + (double)(uint32_t)(h >> 16) * 0x1p-32) * ((h & 1) ? -1.0 : 1.0);
+    for (int k = 0; k < slots; ++k) {
+      if (fp32) {
+        float2 f = make_float2((float)(m * ldexp(1.0, -48 * k)), (float)(m * ldexp(1.0, -48 * k - 24)));
+        reinterpret_cast<float2*>(v)[k * n + i] = f;
+      } else {
+        v[k * n + i] = m * ldexp(1.0, -53 * k);
+      }
+    }
+  }
+}
+
+// The plan check of an arithmetic, once per handle: the SpMV (q = A p, the
+// kernel that depends on the lane count V) is timed with CUDA events under
+// the cost model's candidates (the best and those within twice its cost, at
+// most three; same G), two warm launches then three timed; the model's choice
+// is kept unless another candidate is at least 4% faster.  Systems small
+// enough for the one-cluster solve keep the model's plan.
+int tune_plan(mwcg_csr* A, int arith, cudaStream_t s) {
+  A->tuned[arith] = true;
+  const int64_t n = A->n;
+  const int64_t tiles = (n + mwk::TPB - 1) / mwk::TPB;
+  const mwcg_plan model = A->auto_plan[arith];
+  if (n == 0 || tiles <= mwb_host::small_cluster_size()) return MWCG_OK;
+  const std::vector<int> rank = ranked_lanes(A->passes, A->warps, arith);
+  const double c0 = plan_cost(A->passes, A->warps, rank[0], arith);
+  std::vector<int> cand;
+  for (int j : rank)
+    if (cand.size() < 3 && plan_cost(A->passes, A->warps, j, arith) <= 2.0 * c0) cand.push_back(j);
+  if (cand.size() < 2) return MWCG_OK;
+  int rc;
+  if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
+  const mwk::KernelTable* kt = table(arith);
+  double* p = A->ws + 4 * n;
+  const bool fp32 = fp32_words(arith);
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_fill_probe<<<grid, 256, 0, s>>>(p, n, mwcg_words(arith), fp32 ? 1 : 0);
+  CK(cudaGetLastError());
+  mwk::DevState* h = A->h_st;
+  std::memset(h, 0, sizeof *h);
+  h->x = p;                                   // the mode-0 SpMV reads its input from x
+  CK(cudaMemcpyAsync(A->st, h, sizeof *h, cudaMemcpyHostToDevice, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const mwcg_plan saved = A->plan;
+  double best_ms = -1;
+  int best_j = cand[0];
+  cudaError_t ce = cudaSuccess;
+  for (size_t c = 0; c < cand.size() && ce == cudaSuccess; ++c) {
+    A->plan = mwcg_plan{1 << cand[c], mwk::TPB, model.G};
+    mwk::Csr M = csr_view(A);
+    mwk::Work W = work_view(A, 0, 0);
+    int mode0 = 0;
+    void* args[] = {(void*)&M, (void*)&W, (void*)&mode0};
+    const size_t smem = red_smem(model.G, kt->words);
+    for (int r = 0; r < 5 && ce == cudaSuccess; ++r) {
+      if (r == 2) ce = cudaEventRecord(e0, s);
+      if (ce == cudaSuccess) ce = cudaLaunchKernel(kt->spmv, dim3(model.G), dim3(mwk::TPB), args, smem, s);
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    const double t = ms / 3.0;
+    A->tune_ms[arith][cand[c]] = t;
+    if (c == 0 || t < 0.96 * best_ms) {      // the model's choice unless beaten by 4%
+      best_ms = t;
+      best_j = cand[c];
+    }
+  }
+  A->plan = saved;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return fail(MWCG_ERR_CUDA, "plan timing: %s", cudaGetErrorString(ce));
+  A->auto_plan[arith].V = 1 << best_j;
+  return MWCG_OK;
+}
+
+// Set A->plan for a call in `arith`: the pinned plan, or the arithmetic's
+// automatic plan (checked by timing at its first call).
+int select_plan(mwcg_csr* A, int arith, cudaStream_t s) {
+  if (A->pinned) {
+    A->plan = A->pinned_plan;
+    return MWCG_OK;
+  }
+  if (!A->tuned[arith]) {
+    const int rc = tune_plan(A, arith, s);
+    if (rc != MWCG_OK) return rc;
+  }
+  A->plan = A->auto_plan[arith];
+  return MWCG_OK;
+}
+
 // Jacobi weights for a preconditioned solve, built on first use after the
 // preconditioner was set or the values changed.  *undefined: a diagonal
 // entry is missing, not positive or not finite.
@@ -529,6 +672,7 @@ int run_cluster(mwcg_csr* A, const double* b, double* x, int arith, double tol, 
 int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
               cudaStream_t s, int32_t* iters_out, double* relres_out) {
   int rc;
+  if ((rc = select_plan(A, arith, s)) != MWCG_OK) return rc;
   if (A->prec == MWCG_PREC_JACOBI && !table(arith)->init_pcg)
     return fail(MWCG_ERR_ARG, "arithmetic %d has no preconditioned solver", arith);
   if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
@@ -648,6 +792,7 @@ int ensure_bigraph(mwcg_csr* A, int arith) {
 int run_bicg(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
              cudaStream_t s, int32_t* iters_out, double* relres_out) {
   int rc;
+  if ((rc = select_plan(A, arith, s)) != MWCG_OK) return rc;
   if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
   if (!A->bws) CK(cudaMalloc(&A->bws, sizeof(double) * 12 * (size_t)A->n));
   const bool eager = eager_mode();
@@ -772,9 +917,15 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
       (e = cudaMemsetAsync(A->st, 0, sizeof(mwk::DevState), s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cleanup(fail(MWCG_ERR_CUDA, "copy to device: %s", cudaGetErrorString(e)));
-  A->rowlen.resize(n);
-  for (int64_t i = 0; i < n; ++i) A->rowlen[i] = hrp[i + 1] - hrp[i];
-  A->plan = choose_plan(A->rowlen, sm_count_of(A->device), MWCG_QTW, mwb_host::small_cluster_size());
+  {
+    std::vector<int64_t> rowlen(n);
+    for (int64_t i = 0; i < n; ++i) rowlen[i] = hrp[i + 1] - hrp[i];
+    row_stats(rowlen, A->passes, A->warps);
+  }
+  const int sms = sm_count_of(A->device), small = mwb_host::small_cluster_size();
+  for (int a = 0; a < kNArith; ++a)
+    A->auto_plan[a] = choose_plan(A->passes, A->warps, n, sms, a, small, table(a)->minb);
+  A->plan = A->auto_plan[MWCG_QTW];
   *out = A;
   return MWCG_OK;
 }
@@ -793,6 +944,7 @@ void mwcg_destroy_csr(mwcg_csr* A) {
   cudaFree(A->hx);
   cudaFree(A->w);
   cudaFree(A->w_bad);
+  cudaFree(A->vbad);
   cudaFree(A->bws);
   if (A->h_st) cudaFreeHost(A->h_st);
   delete A;
@@ -803,13 +955,29 @@ int mwcg_update_values(mwcg_csr* A, const double* val, int on_device, void* stre
   if (!A) return fail(MWCG_ERR_ARG, "null matrix handle");
   if (A->nnz == 0) return MWCG_OK;
   if (!val) return fail(MWCG_ERR_ARG, "null val");
-  std::vector<double> hv(A->nnz);
-  if (on_device) CK(cudaMemcpy(hv.data(), val, sizeof(double) * A->nnz, cudaMemcpyDeviceToHost));
-  else std::memcpy(hv.data(), val, sizeof(double) * A->nnz);
-  for (int64_t k = 0; k < A->nnz; ++k)
-    if (!std::isfinite(hv[k])) return fail(MWCG_ERR_ARG, "val[%lld] is not finite", (long long)k);
-  CK(cudaMemcpyAsync(A->val, hv.data(), sizeof(double) * A->nnz, cudaMemcpyHostToDevice, S(stream)));
-  CK(cudaStreamSynchronize(S(stream)));
+  cudaStream_t s = S(stream);
+  if (on_device) {
+    // Validated on the device (the first non-finite index, if any, comes back
+    // as one 8-byte word), then copied device to device: no host round trip
+    // of the values, which autograd updates on every step.
+    if (!A->vbad) CK(cudaMalloc(&A->vbad, sizeof(int64_t)));
+    int64_t* first = A->vbad;
+    CK(cudaMemsetAsync(first, 0x7f, sizeof(int64_t), s));
+    const int grid = (int)std::min<int64_t>((A->nnz + 255) / 256, 4096);
+    k_first_nonfinite<<<grid, 256, 0, s>>>(val, A->nnz, first);
+    int64_t bad = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, first, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(MWCG_ERR_CUDA, "value check: %s", cudaGetErrorString(e));
+    if (bad < A->nnz) return fail(MWCG_ERR_ARG, "val[%lld] is not finite", (long long)bad);
+    CK(cudaMemcpyAsync(A->val, val, sizeof(double) * A->nnz, cudaMemcpyDeviceToDevice, s));
+  } else {
+    for (int64_t k = 0; k < A->nnz; ++k)
+      if (!std::isfinite(val[k])) return fail(MWCG_ERR_ARG, "val[%lld] is not finite", (long long)k);
+    CK(cudaMemcpyAsync(A->val, val, sizeof(double) * A->nnz, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaStreamSynchronize(s));
   A->w_valid = false;                  // Jacobi weights follow the new diagonal
   return MWCG_OK;
 }
@@ -824,10 +992,28 @@ int mwcg_get_plan(const mwcg_csr* A, mwcg_plan* out) {
 }
 
 int mwcg_set_plan(mwcg_csr* A, const mwcg_plan* p) {
-  if (!A || !p) return fail(MWCG_ERR_ARG, "null argument");
+  if (!A) return fail(MWCG_ERR_ARG, "null argument");
+  if (!p) {                            // back to the automatic plans
+    A->pinned = false;
+    A->plan = A->auto_plan[MWCG_QTW];
+    return MWCG_OK;
+  }
   if (!is_pow2_le32(p->V) || p->T != mwk::TPB || p->G < 1 || p->G > kMaxG)
     return fail(MWCG_ERR_ARG, "invalid plan V=%d T=%d G=%d", p->V, p->T, p->G);
+  A->pinned = true;
+  A->pinned_plan = *p;
   A->plan = *p;
+  return MWCG_OK;
+}
+
+int mwcg_get_plan_for(mwcg_csr* A, int arith, void* stream, mwcg_plan* out, double* spmv_ms) {
+  g_err.clear();
+  if (!A || !out || !table(arith)) return fail(MWCG_ERR_ARG, "bad handle, arithmetic or output");
+  const int rc = select_plan(A, arith, S(stream));
+  if (rc != MWCG_OK) return rc;
+  *out = A->plan;
+  if (spmv_ms)
+    for (int j = 0; j < 6; ++j) spmv_ms[j] = A->pinned ? 0.0 : A->tune_ms[arith][j];
   return MWCG_OK;
 }
 
@@ -957,6 +1143,7 @@ int mwcg_spmv(mwcg_csr* A, int arith, const double* p, double* q, void* stream) 
   if (!p || !q) return fail(MWCG_ERR_ARG, "null p or q");
   cudaStream_t s = S(stream);
   int rc;
+  if ((rc = select_plan(A, arith, s)) != MWCG_OK) return rc;
   if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
   mwk::DevState* h = A->h_st;
   std::memset(h, 0, sizeof *h);
@@ -1040,8 +1227,9 @@ int mwcg_profile_kernels(mwcg_csr* A, const double* b, double* x, int arith, int
   int rc = check_solve_args(A, b, x, arith, 0.0, niters);
   if (rc != MWCG_OK) return rc;
   if (niters < 2 || niters > 100000 || !ms_out || A->n == 0) return fail(MWCG_ERR_ARG, "bad profile arguments");
-  if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
   cudaStream_t s = S(stream);
+  if ((rc = select_plan(A, arith, s)) != MWCG_OK) return rc;
+  if ((rc = ensure_ws(A)) != MWCG_OK) return rc;
   const mwk::KernelTable* kt = table(arith);
   if (A->prec == MWCG_PREC_JACOBI && !kt->init_pcg)
     return fail(MWCG_ERR_ARG, "arithmetic %d has no preconditioned solver", arith);
@@ -1116,6 +1304,7 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
     if (fp32_words(arith[s])) return fail(MWCG_ERR_ARG, "system %d: QQF and QF are not batched", s);
     if (!seen.insert(A[s]).second) return fail(MWCG_ERR_ARG, "system %d: matrix handle repeated in the batch", s);
     if ((rc = ensure_ws(A[s])) != MWCG_OK) return rc;
+    if ((rc = select_plan(A[s], arith[s], S(stream))) != MWCG_OK) return rc;
   }
   std::vector<mwb::Sys> hs;
   std::vector<int> idx;

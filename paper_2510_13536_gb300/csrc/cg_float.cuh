@@ -320,6 +320,7 @@ template <class A>
 inline KernelTable make_table_qqf() {
   KernelTable t{};
   t.words = kQqfSlots;
+  t.minb = A::MINB;
   t.spmv = (const void*)&k_spmv<A>;
   t.spmv_pol = t.spmv;
   t.init = (const void*)&k_qqf_init<A>;

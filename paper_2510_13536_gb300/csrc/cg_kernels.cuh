@@ -882,6 +882,7 @@ __global__ void __launch_bounds__(TPB) k_word_op(int op, int64_t n, const double
 // Kernel table of one arithmetic, used by the host runtime.
 struct KernelTable {
   int words;
+  int minb;                 // blocks per SM the loop kernels are compiled for (the plan's G = minb x SMs)
   const void* spmv;
   const void* spmv_pol;     // the three loop kernels under a non-default normalisation policy
   const void* update_pol;
@@ -907,6 +908,7 @@ template <class A, class AS = A>
 KernelTable make_table() {
   KernelTable t;
   t.words = A::W;
+  t.minb = A::MINB;
   t.spmv = (const void*)&k_spmv<AS>;
   t.init_pcg = (const void*)&k_init<A, true>;
   t.update_pcg = (const void*)&k_update<A, false, true>;

@@ -112,7 +112,7 @@ struct QQF {
   static constexpr int ILP = 2;               // rows in flight per thread in the vector kernels (memory bound)
   static constexpr int CHUNK = 1;
   static constexpr int ILP_SPMV = 1;
-  static constexpr int MINB = 3;
+  static constexpr int MINB = 4;               // blocks per SM (the plan's G = 4 x SMs)
   static constexpr int W = 4;
   static constexpr bool QUASI = true;
   static constexpr bool NORMALISES = false;   // the normalisation policy does not apply
@@ -239,7 +239,7 @@ struct QF {
   static constexpr int ILP = 2;
   static constexpr int CHUNK = 1;
   static constexpr int ILP_SPMV = 1;
-  static constexpr int MINB = 3;
+  static constexpr int MINB = 4;               // blocks per SM (the plan's G = 4 x SMs)
   static constexpr int W = 4;
   static constexpr bool QUASI = false;
   static constexpr bool NORMALISES = false;   // the normalisation policy does not apply

@@ -126,8 +126,23 @@ class CSRMatrix:
 
     @plan.setter
     def plan(self, vtg):
+        """Pin (V, T, G) for every arithmetic; None returns to the automatic plans."""
+        if vtg is None:
+            check(_capi.load().mwcg_set_plan(self._h, None))
+            return
         p = Plan(*[int(v) for v in vtg])
         check(_capi.load().mwcg_set_plan(self._h, ctypes.byref(p)))
+
+    def plan_for(self, arith) -> tuple[int, int, int]:
+        """The plan a solve in `arith` uses (timed at the first call in it)."""
+        return self.tuning(arith)[0]
+
+    def tuning(self, arith):
+        """(plan, {V: measured SpMV ms}) of an arithmetic's automatic plan."""
+        p = Plan()
+        ms = (ctypes.c_double * 6)()
+        check(_capi.load().mwcg_get_plan_for(self._h, arith_id(arith), _stream(), ctypes.byref(p), ms))
+        return (p.V, p.T, p.G), {1 << j: ms[j] for j in range(6) if ms[j] > 0}
 
     @property
     def normalization(self) -> tuple[int, int]:

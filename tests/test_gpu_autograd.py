@@ -53,6 +53,17 @@ def test_values_update_changes_the_solve(mw):
     assert float(torch.max(torch.abs(x1 - 2 * x2))) < 1e-14
     with pytest.raises(RuntimeError):
         M.update_values(np.full(A.nnz, np.nan))
+    # Device values are checked on the device; a rejected update leaves A as it was.
+    v = torch.as_tensor(A.val, device="cuda") * 2.0
+    v[123] = float("inf")
+    v[400] = float("nan")
+    with pytest.raises(RuntimeError, match=r"val\[123\]"):
+        M.update_values(v)
+    r3 = mw.solve(M, b, "dw", 1e-20, 1000)
+    assert torch.equal(r3.x, r2.x)
+    M.update_values(torch.as_tensor(A.val, device="cuda"))
+    r4 = mw.solve(M, b, "dw", 1e-20, 1000)
+    assert torch.equal(r4.x, r1.x)
 
 
 def test_pipe_probe_reports_rates(mw):

@@ -141,7 +141,7 @@ def test_cg_bit_exact_against_mirrored_oracle(mw, orc, arith, case):
     A, seed = make()
     b = P.rhs_ones_exact(A) if seed is None else P.rhs_uniform(A.n, seed)
     M = mw.CSRMatrix.from_csr(A)
-    V, T, G = M.plan
+    V, T, G = M.plan_for(arith)                 # the automatic (timed) plan of this arithmetic
     r = mw.solve(M, dev(b), arith, tol, maxit)
     xo, ito, rro, sto = orc.cg(arith, A, b, tol=tol, maxit=maxit, plan=(V, T, G))
     assert (r.iters, r.status) == (ito, sto), (name, arith)
@@ -167,8 +167,8 @@ def test_cg_special_cases(mw, orc):
     A = P.laplacian_2d(16)
     b = P.rhs_ones_exact(A)
     M = mw.CSRMatrix.from_csr(A)
-    plan = M.plan
     for arith in ARITHS:
+        plan = M.plan_for(arith)
         w = W[arith]
         # b = 0 -> x = 0, zero iterations
         r = mw.solve(M, dev(np.zeros(A.n)), arith, 1e-10, 100, x0=dev(np.ones((w, A.n))))
