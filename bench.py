@@ -301,6 +301,39 @@ def cpu_baseline(torch, mw, M, A, b_np, b_dev, arith, tol, gpu_iters, k=CPU_SAMP
             "history_bits_match_gpu": same}
 
 
+# FP64 instructions (DADD, DFMA, DMUL) per element of the vector kernels:
+# k_update = x += alpha p and r += (-alpha) q (two muladds: MW product + MW
+# add), the normalisation of r (QTW VecSum3: two TwoSums; QDW QuickTwoSum),
+# the dot leaf r r and its accumulation; k_pupdate = p = r + beta p (one
+# muladd).  The same sequences as the SpMV model's table (SPMV_INSTR), less
+# one DMUL in QTW's leaf r r, whose two cross products a1 b2 and a2 b1 are the
+# same product (computed once; ncu counts 8 DMUL per element).
+VEC_INSTR = {
+    "qtw": {"update": (35, 18, 8), "p_update": (11, 6, 3)},
+    "dw": {"update": (27, 6, 3), "p_update": (9, 2, 1)},
+    "qdw": {"update": (12, 6, 3), "p_update": (3, 2, 1)},
+    "fp64": {"update": (1, 2, 1), "p_update": (0, 1, 0)},
+}
+
+
+def vector_rooflines(arith, n, kms, probe, elem):
+    """FP64-pipe and HBM fractions of k_update and k_pupdate (as spmv_roofline)."""
+    m = VEC_INSTR.get(arith)
+    r_add, r_fma, r_mul = probe["dadd_ops_per_s"], probe["dfma_ops_per_s"], probe["dmul_ops_per_s"]
+    hbm = _measured_hbm_gbs() * 1e9
+    out = {}
+    for name, ms, passes in (("update_dot", kms[1], 6), ("p_update", kms[2], 3)):
+        t = ms * 1e-3
+        d = {"kernel_ms": ms, "alg_bytes_per_launch": passes * elem * n,
+             "hbm_frac_of_measured": passes * elem * n / t / hbm}
+        if m is not None:
+            a, f, mu = m["update" if name == "update_dot" else "p_update"]
+            d["fp64_instr_per_launch"] = {"dadd": a * n, "dfma": f * n, "dmul": mu * n}
+            d["fp64_pipe_frac"] = (a * n / r_add + f * n / r_fma + mu * n / r_mul) / t
+        out[name] = d
+    return out
+
+
 def spmv_roofline(arith, A, plan, spmv_ms, probe, elem):
     """Roofline of the dominant kernel, k_spmv (SpMV + p^T q + alpha), from its
     mean duration over 30 launches (CUDA events on the launching stream).
@@ -943,6 +976,7 @@ def run_gpu(args):
                                                  ctypes.c_void_p(stream.cuda_stream), ctypes.byref(v)))
         probe[name] = v.value
     roofline = spmv_roofline(arith, A, M.plan, spmv_ms, probe, elem)
+    roofline["vector_kernels"] = vector_rooflines(arith, A.n, kms, probe, elem)
 
     # End to end through the C ABI with host buffers (pinned), copies included.
     bh = torch.empty(A.n, dtype=torch.float64, pin_memory=True)

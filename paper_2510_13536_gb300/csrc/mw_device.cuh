@@ -115,10 +115,14 @@ template <int W> struct MW { double w[W]; };
 
 // ---------------------------------------------------------------- FP64
 struct FP64 {
-  static constexpr int ILP = 2;                // rows in flight per thread (memory bound)
+  // Memory bound: 5 blocks per SM (40 registers a thread, the plan's G = 5 x
+  // SMs) with one row per thread and 2 SpMV entries loaded ahead per row
+  // measured fastest on GB300 (c2 SpMV 63.6 us; 3 blocks with 2 rows x 2
+  // entries: 69.8 us; 4 or 6 blocks, 4 entries or 2 rows: 65.7-76.3 us).
+  static constexpr int ILP = 1;                // rows in flight per thread
   static constexpr int CHUNK = 2;              // SpMV entries loaded ahead per row
-  static constexpr int ILP_SPMV = 2;
-  static constexpr int MINB = 3;               // blocks per SM the register budget must allow
+  static constexpr int ILP_SPMV = 1;
+  static constexpr int MINB = 5;               // blocks per SM the register budget must allow
   static constexpr int W = 1;
   static constexpr bool QUASI = false;
   static constexpr bool NORMALISES = false;   // A::normalize is the identity
