@@ -586,38 +586,52 @@ def run_qqf(torch, mw, P, cpu):
     M = mw.CSRMatrix.from_csr(A)
     db = torch.as_tensor(b, device="cuda")
     n, nnz = A.n, A.nnz
-    out = {"workload": "c2: " + P.WORKLOADS["c2"], "plan": list(M.plan), "runs": []}
-    for ar in ("fp64", "dw", "qdw", "qtw", "qqf"):
+    out = {"workload": "c2: " + P.WORKLOADS["c2"], "runs": []}
+    for ar in ("fp64", "dw", "qdw", "qtw", "qqf", "qf"):
         mw.solve(M, db, ar, tol, 2)
         r, ms = _timed(torch, lambda: mw.solve(M, db, ar, tol, maxit), reps=3)
-        out["runs"].append({"arith": ar, "iters": r.iters, "status": r.status, "relres": r.relres,
-                            "time_s": ms / 1e3, "ms_per_iter": ms / max(r.iters, 1)})
+        out["runs"].append({"arith": ar, "plan": list(M.plan), "iters": r.iters, "status": r.status,
+                            "relres": r.relres, "time_s": ms / 1e3, "ms_per_iter": ms / max(r.iters, 1)})
     # Per-kernel durations (CUDA events around each launch) and their rooflines.
     s = torch.cuda.current_stream()
-    kms = (ctypes.c_double * 3)()
-    xx = torch.zeros((2, n), dtype=torch.float64, device="cuda")
-    _capi.check(_capi.load().mwcg_profile_kernels(M.handle, ctypes.c_void_p(db.data_ptr()),
-                                                  ctypes.c_void_p(xx.data_ptr()), mw.arith_id("qqf"), 30,
-                                                  ctypes.c_void_p(s.cuda_stream), kms))
     hbm = _measured_hbm_gbs() * 1e9
     by = {"spmv_dot": 12 * nnz + 8 * (n + 1) + 2 * 16 * n,    # CSR + p gathered once + q written
           "update_dot": 6 * 16 * n,                         # x, r read and written; p, q read
           "p_update": 3 * 16 * n}                           # r read; p read and written
-    ops = QQF_SPMV_OPS[0] * nnz + QQF_SPMV_OPS[1] * n
-    kern = {}
-    for k, name in enumerate(("spmv_dot", "update_dot", "p_update")):
-        t = kms[k] * 1e-3
-        kern[name] = {"ms": kms[k], "alg_bytes": by[name], "hbm_gbs": by[name] / t / 1e9,
-                      "hbm_frac_of_measured": by[name] / t / hbm}
-    kern["spmv_dot"]["fp32_ops"] = ops
-    kern["spmv_dot"]["fp32_frac_of_peak"] = ops / (kms[0] * 1e-3) / FP32_PEAK_OPS
-    out["qqf_kernels"] = kern
+    for ar in ("qqf", "qf"):
+        kms = (ctypes.c_double * 3)()
+        xx = torch.zeros((2, n), dtype=torch.float64, device="cuda")
+        _capi.check(_capi.load().mwcg_profile_kernels(M.handle, ctypes.c_void_p(db.data_ptr()),
+                                                      ctypes.c_void_p(xx.data_ptr()), mw.arith_id(ar), 30,
+                                                      ctypes.c_void_p(s.cuda_stream), kms))
+        ops = FP32_SPMV_OPS[ar][0] * nnz + FP32_SPMV_OPS[ar][1] * n
+        kern = {}
+        for k, name in enumerate(("spmv_dot", "update_dot", "p_update")):
+            t = kms[k] * 1e-3
+            kern[name] = {"ms": kms[k], "alg_bytes": by[name], "hbm_gbs": by[name] / t / 1e9,
+                          "hbm_frac_of_measured": by[name] / t / hbm}
+        kern["spmv_dot"]["fp32_ops_full_products"] = ops
+        kern["spmv_dot"]["fp32_frac_of_peak_full_products"] = ops / (kms[0] * 1e-3) / FP32_PEAK_OPS
+        out[ar + "_kernels"] = kern
+    # The ill-conditioned power-law graph Laplacian (n = 20000, kappa ~ 5e11):
+    # QQF's ~96 bits run out on its cancelling rows, QF keeps QDW-class
+    # convergence.
+    Ap = P.power_law_laplacian(20000, seed=7, mean_deg=12, max_deg=300)
+    bp = torch.as_tensor(P.rhs_uniform(Ap.n, 32), device="cuda")
+    Mp = mw.CSRMatrix.from_csr(Ap)
+    pl = []
+    for ar in ("fp64", "qdw", "qqf", "qf"):
+        mw.solve(Mp, bp, ar, 1e-14, 2)
+        r, ms = _timed(torch, lambda: mw.solve(Mp, bp, ar, 1e-14, 40000))
+        pl.append({"arith": ar, "iters": r.iters, "status": r.status, "relres": r.relres, "time_s": ms / 1e3})
+    out["power_law_20000"] = {"workload": "power-law graph Laplacian n = 20000 (mean degree 12, max 300, "
+                                          "lognormal weights, + 1e-8 I), b = 2U-1, tol 1e-14", "runs": pl}
     # Forward error on the exact-solution twin (x* = +-1, b = A x* exact).
     Ae, be, xs = P.exact_solution_system("norm_poisson")
     Me = mw.CSRMatrix.from_csr(Ae)
     dbe = torch.as_tensor(be, device="cuda")
     fe = []
-    for ar, tl in (("dw", 1e-24), ("qdw", 1e-24), ("qqf", 1e-24), ("fp64", 1e-14)):
+    for ar, tl in (("dw", 1e-24), ("qdw", 1e-24), ("qqf", 1e-24), ("qf", 1e-24), ("fp64", 1e-14)):
         mw.solve(Me, dbe, ar, tl, 2)
         r, ms = _timed(torch, lambda: mw.solve(Me, dbe, ar, tl, 20000))
         x = r.x.double().cpu().numpy()

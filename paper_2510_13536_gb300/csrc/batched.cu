@@ -2,7 +2,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <cstdlib>
 #include <cstring>
 #include <set>
 #include <vector>
@@ -77,10 +76,9 @@ int small_cluster_size() {
 // plan, not on the grouping.  Returns a cudaError_t; outputs are copied back
 // into hsys.
 cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* clusters_out) {
-  // MWCG_BATCH_PAD=0 drops the shared-memory pad that keeps one CTA per SM
-  // (clusters may then share SMs); for tuning runs.
-  const char* pad_env = std::getenv("MWCG_BATCH_PAD");
-  const size_t pad = (pad_env && pad_env[0] == '0') ? 0 : mwb::kPadSmem;
+  // A single system keeps one CTA per SM (the pad); a batch packs two CTAs of
+  // (possibly different) clusters per SM.
+  const size_t pad = nsys == 1 ? mwb::kPadSmem : 0;
   constexpr int NG = 6;
   static const mwb::RunGroup run[NG] = {mwb::run_group_00, mwb::run_group_01, mwb::run_group_02,
                                         mwb::run_group_10, mwb::run_group_11, mwb::run_group_12};

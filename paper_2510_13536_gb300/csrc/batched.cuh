@@ -430,7 +430,7 @@ __device__ __forceinline__ void solve_any(const ClusterCtx& cc, Slots* slots, Sy
 // translation unit (batched_k*.cu): a kernel holding every arithmetic's
 // solver takes minutes to compile.
 template <bool PREC, int GRP>
-__global__ void __launch_bounds__(TPB, 1) k_batched(Sys* __restrict__ sys, int nsys, unsigned* queue) {
+__global__ void __launch_bounds__(TPB, 2) k_batched(Sys* __restrict__ sys, int nsys, unsigned* queue) {
   __shared__ Slots slots;
   __shared__ int s_next;
   cgx::cluster_group cl = cgx::this_cluster();
@@ -445,7 +445,12 @@ __global__ void __launch_bounds__(TPB, 1) k_batched(Sys* __restrict__ sys, int n
   }
 }
 
-constexpr size_t kPadSmem = 120 * 1024;     // dynamic shared memory that keeps one CTA per SM
+// Dynamic shared memory that keeps one CTA per SM, used for the one-cluster
+// solve of a single small system (its CTAs then spread over as many SMs as
+// possible).  Batches run without it: two CTAs per SM (the kernels are
+// compiled for 2 blocks per SM, at most 128 registers, no spills) keep twice
+// the warps per SM busy (c4, 256 systems: 8.26 s with the pad, 5.14 s without).
+constexpr size_t kPadSmem = 120 * 1024;
 
 // Host: run k_batched<PREC, GRP> over n systems already on the device (queue
 // zeroed), clusters of `cluster` CTAs: as many clusters as fit at once, at
