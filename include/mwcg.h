@@ -151,7 +151,10 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
 void mwcg_destroy_csr(mwcg_csr* A);
 
 /* Replace the values of A (same sparsity pattern); val is double[nnz] on the
- * host (on_device = 0) or device (1).  Non-finite values: MWCG_ERR_ARG. */
+ * host (on_device = 0) or device (1).  Non-finite values: MWCG_ERR_ARG (the
+ * message names the first one) and A keeps its values.  Device values are
+ * checked on the device and copied device to device (no host copy of the
+ * values); the call synchronises `stream`. */
 int mwcg_update_values(mwcg_csr* A, const double* val, int on_device, void* stream);
 
 int64_t mwcg_n(const mwcg_csr* A);

@@ -193,7 +193,11 @@ struct DWt {
   // QuickTwoSum runs as printed.
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     double p, e;
-    if (!(mwi::is_pow2(a) && mwi::pow2_scale(a, b.w[0], false, p) && mwi::pow2_scale(a, b.w[1], true, e))) {
+    double pe[2];
+    if (mwi::pow2_product<2>(a, b.w, pe)) {
+      p = pe[0];
+      e = pe[1];
+    } else {
       two_prod_w2(a, b.w[0], p, e);
       e = dfma(a, b.w[1], e);
     }
@@ -248,8 +252,7 @@ struct QDWt {
   }
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     T c;
-    if (mwi::is_pow2(a) && mwi::pow2_scale(a, b.w[0], false, c.w[0]) && mwi::pow2_scale(a, b.w[1], true, c.w[1]))
-      return c;
+    if (mwi::pow2_product<2>(a, b.w, c.w)) return c;
     two_prod_w2(a, b.w[0], c.w[0], c.w[1]);
     c.w[1] = dfma(a, b.w[1], c.w[1]);
     return c;
@@ -326,9 +329,7 @@ struct QTWt {
   // instance) takes the exact-scaling path on the integer pipe (same bits).
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     T c;
-    if (mwi::is_pow2(a) && mwi::pow2_scale(a, b.w[0], false, c.w[0]) && mwi::pow2_scale(a, b.w[1], true, c.w[1]) &&
-        mwi::pow2_scale(a, b.w[2], true, c.w[2]))
-      return c;
+    if (mwi::pow2_product<3>(a, b.w, c.w)) return c;
     double e1, e2, e5;
     two_prod(a, b.w[0], c.w[0], e1);
     two_prod(a, b.w[1], c.w[1], e2);

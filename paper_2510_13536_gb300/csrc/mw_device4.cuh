@@ -73,8 +73,7 @@ struct QQWt {
   // exactly on the integer pipe (the same bits as the sequence below).
   static __device__ __forceinline__ T dxmul(double a, const T& b) {
     T c;
-    if (mwi::is_pow2(a) && mwi::pow2_scale(a, b.w[0], false, c.w[0]) && mwi::pow2_scale(a, b.w[1], true, c.w[1]) &&
-        mwi::pow2_scale(a, b.w[2], true, c.w[2]) && mwi::pow2_scale(a, b.w[3], true, c.w[3]))
+    if (mwi::pow2_product<4>(a, b.w, c.w))
       return c;
     double e1, e2, e3, e4, e5, e6;
     two_prod(a, b.w[0], c.w[0], e1);

@@ -41,7 +41,7 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& x, float& y) 
 }
 __device__ __forceinline__ void two_prod_f(float a, float b, float& x, float& y) {
   const float p = fmul(a, b);
-  y = ffma(a, b, fneg(p));
+  y = ffma(a, b, -p);          // the negation folds into the FMA's operand (no extra instruction)
   x = p;
 }
 
@@ -92,6 +92,20 @@ __device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((lo
 // four FP32 multiplications; the path declines (returns false) otherwise.
 __device__ __forceinline__ bool pow2_dxmul_f(double a, const float (&b)[4], float (&c)[4]) {
   const uint64_t ua = (uint64_t)__double_as_longlong(a);
+  if ((ua & 0x7FFFFFFFFFFFFFFFULL) == 0x3FF0000000000000ULL) {
+    // a = +-1: no exponent changes, so every product (subnormal words
+    // included) is exact for any finite b: a sign flip per word, +0 for a
+    // zero lower word.  Non-finite words decline.
+    const uint32_t sg = (uint32_t)(ua >> 32) & 0x80000000u;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t u = __float_as_uint(b[j]);
+      ok = ok && ((u & 0x7F800000u) != 0x7F800000u);
+      c[j] = (j > 0 && (u << 1) == 0u) ? 0.0f : __uint_as_float(u ^ sg);
+    }
+    return ok;
+  }
   const int ea = (int)((ua >> 52) & 0x7FFu);
   if ((ua & 0xFFFFFFFFFFFFFULL) != 0 || ea < 897 || ea > 1150) return false;
   const float af = __uint_as_float((uint32_t)(ua >> 32 & 0x80000000u) | ((uint32_t)(ea - 896) << 23));

@@ -217,6 +217,34 @@ MWI_HD bool pow2_scale(double a, double b, bool plus_zero, double& out) {
   return true;
 }
 
+// FP64 x MW product with a power-of-two FP64 factor a, as the printed
+// sequences (Algorithm 10 and its DW / QDW / QQW analogues, before DW's
+// closing QuickTwoSum) return it: every TwoProd error and every partner of a
+// TwoSum is then zero, so each word is scaled exactly and a zero lower word
+// comes out as +0.  For a = +-1 the scaling changes no exponent and holds for
+// every finite word, subnormal ones included (a sign flip per word); other
+// powers of two need every nonzero scaled word to stay normal (pow2_scale).
+// Returns false (the caller runs the printed sequence) for a non-finite word
+// or a scaled word that would leave the normal range.
+template <int W>
+MWI_HD bool pow2_product(double a, const double (&b)[W], double (&c)[W]) {
+  const uint64_t ua = bits_of(a);
+  if ((ua & kAbs) == 0x3FF0000000000000ULL) {
+    const uint64_t sg = ua & ~kAbs;
+    bool ok = true;
+    for (int k = 0; k < W; ++k) {
+      const uint64_t ub = bits_of(b[k]);
+      ok = ok && (((ub >> 52) & 0x7ff) != 0x7ff);
+      c[k] = (k > 0 && (ub & kAbs) == 0) ? 0.0 : from_bits(ub ^ sg);
+    }
+    return ok;
+  }
+  if (!is_pow2(a)) return false;
+  for (int k = 0; k < W; ++k)
+    if (!pow2_scale(a, b[k], k > 0, c[k])) return false;
+  return true;
+}
+
 // Precondition under which QuickTwoSum (Algorithm 3) returns the exact error:
 // exponent field of a >= exponent field of b, or b = +-0.
 MWI_HD bool quick_exact(double a, double b) {

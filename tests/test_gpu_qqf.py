@@ -97,6 +97,10 @@ def test_pow2_product_bit_exact(mw, orc, ar):
     e = rng.integers(-140, 140, n)
     s = rng.choice([-1.0, 1.0], n) * 2.0 ** e.astype(np.float64)
     s[:10] = [1.0, -1.0, 2.0 ** -126, -2.0 ** -127, 2.0 ** 127, 2.0 ** 128, -2.0 ** -97, 2.0 ** -98, 0.5, 4.0]
+    s[10:20] = [1.0, -1.0, 1.0, -1.0, 2.0, 1.0, -1.0, 0.25, 1.0, -1.0]   # non-finite words of b below
+    b[:, 10:20] = 1.0
+    b[0, 10], b[1, 11], b[2, 12], b[3, 13], b[1, 14] = np.inf, -np.inf, np.nan, np.inf, np.nan
+    b[0, 15], b[3, 16], b[1, 17] = -np.inf, np.nan, np.inf
     g = mw.word_op("dxmul", ar, dev(s), dev(b, np.float32)).cpu().numpy()
     assert same_bits(g, orc.dxmul(ar, s, b))
 

@@ -52,6 +52,20 @@ extern "C" void pow2_dx_batch(long n, int w, const double* a, const double* b, d
     ok[i] = g ? 1 : 0;
   }
 }
+template <int W>
+static void pow2_product_batch_w(long n, const double* a, const double* b, double* c, int* ok) {
+  for (long i = 0; i < n; ++i) {
+    double bw[W], cw[W];
+    for (int k = 0; k < W; ++k) bw[k] = b[k * n + i];
+    ok[i] = mwi::pow2_product<W>(a[i], bw, cw) ? 1 : 0;
+    for (int k = 0; k < W; ++k) c[k * n + i] = cw[k];
+  }
+}
+extern "C" void pow2_product_batch(long n, int w, const double* a, const double* b, double* c, int* ok) {
+  if (w == 2) pow2_product_batch_w<2>(n, a, b, c, ok);
+  else if (w == 3) pow2_product_batch_w<3>(n, a, b, c, ok);
+  else pow2_product_batch_w<4>(n, a, b, c, ok);
+}
 extern "C" void quick_exact_batch(long n, const double* a, const double* b, int* ok) {
   for (long i = 0; i < n; ++i) ok[i] = mwi::quick_exact(a[i], b[i]) ? 1 : 0;
 }
@@ -73,6 +87,7 @@ def shim(tmp_path_factory):
     L.mul_error_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.add_rn_batch.argtypes = [ctypes.c_long, P, P, P, P, P]
     L.pow2_dx_batch.argtypes = [ctypes.c_long, ctypes.c_int, P, P, P, P]
+    L.pow2_product_batch.argtypes = [ctypes.c_long, ctypes.c_int, P, P, P, P]
     return L
 
 
@@ -247,6 +262,45 @@ def test_power_of_two_product_matches_printed_dxmul(shim, orc, arith, w):
     ok = np.zeros(n, dtype=np.int32)
     shim.pow2_dx_batch(n, w, _p(a), _p(np.ascontiguousarray(b)), _p(c), _p(ok))
     ok = ok.astype(bool)
+    ref = orc.dxmul(arith, a, b)
+    assert ok.mean() > 0.5
+    assert np.array_equal(c[:, ok].view(np.uint64), ref[:, ok].view(np.uint64))
+
+
+@pytest.mark.parametrize("arith,w", [("qtw", 3), ("qdw", 2), ("qqw", 4)])
+def test_pow2_product_matches_printed_dxmul(shim, orc, arith, w):
+    """mwi::pow2_product, the device's FP64 x MW shortcut for power-of-two
+    entries, against the oracle's printed product bit for bit: a = +-1 (a sign
+    flip per word, valid for subnormal words too) and other powers of two, with
+    zero words of either sign, subnormal lower words and words near the range
+    edges; non-finite words must decline."""
+    rng = np.random.default_rng(41 + w)
+    n = 200_000
+    a = rng.choice([1.0, -1.0], n)
+    m = rng.integers(0, 4, n)
+    a[m == 1] = np.exp2(rng.integers(-60, 61, int((m == 1).sum())).astype(float)) * rng.choice([-1.0, 1.0], int((m == 1).sum()))
+    a[m == 2] = rng.uniform(1, 2, int((m == 2).sum()))           # not a power of two: declined
+    b = np.empty((w, n))
+    b[0] = rng.uniform(-2, 2, n) * np.exp2(rng.integers(-300, 300, n))
+    for k in range(1, w):
+        b[k] = b[k - 1] * rng.uniform(-1, 1, n) * 2.0 ** -53
+    z = rng.integers(0, 9, n)
+    b[1, z == 1] = 0.0
+    b[1, z == 2] = -0.0
+    b[w - 1, z == 3] = -0.0
+    b[0, z == 4] = -0.0
+    b[w - 1, z == 5] = 3e-310 * rng.choice([-1.0, 1.0], int((z == 5).sum()))   # subnormal lower word
+    b[:, z == 6] *= 2.0 ** 900                                    # near overflow after scaling
+    b[rng.integers(0, w), z == 7] = np.inf
+    b[rng.integers(0, w), z == 8] = np.nan
+    c = np.zeros((w, n))
+    ok = np.zeros(n, dtype=np.int32)
+    shim.pow2_product_batch(n, w, _p(a), _p(np.ascontiguousarray(b)), _p(c), _p(ok))
+    ok = ok.astype(bool)
+    pm1 = np.abs(a) == 1.0
+    finite = np.all(np.isfinite(b), axis=0)
+    assert np.array_equal(ok[pm1], finite[pm1])                   # +-1: every finite b is taken
+    assert not ok[m == 2].any()
     ref = orc.dxmul(arith, a, b)
     assert ok.mean() > 0.5
     assert np.array_equal(c[:, ok].view(np.uint64), ref[:, ok].view(np.uint64))
