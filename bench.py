@@ -59,13 +59,14 @@ SPMV_OPS["qtw_nn"] = SPMV_OPS["qtw"]
 # DADD, DFMA, DMUL), from the device sequences: TwoSum errors (and the
 # double-word TwoProd errors) come from the integer pipe, a power-of-two
 # matrix entry scales the words exactly on the integer pipe, and the QTW SpMV
-# adds the product's last word on the integer pipe.  Keys: FP64 x MW product
+# adds the product's last word on the integer pipe and the DW SpMV the closing
+# QuickTwoSum of its products.  Keys: FP64 x MW product
 # with a general entry ("dx") and with a power-of-two entry ("dx2"), MW add,
 # MW product.  These counts reproduce ncu's executed-instruction counters
 # (profiles/k_spmv_*_c2.md).
 SPMV_INSTR = {
     "qtw": {"dx": (1, 3, 2), "dx2": (0, 0, 0), "add": (6, 0, 0), "mul": (5, 6, 3)},
-    "dw": {"dx": (3, 1, 1), "dx2": (3, 0, 0), "add": (6, 0, 0), "mul": (3, 2, 1)},
+    "dw": {"dx": (0, 1, 1), "dx2": (0, 0, 0), "add": (6, 0, 0), "mul": (0, 2, 1)},   # QuickTwoSum on the integer pipe
     "qdw": {"dx": (0, 1, 1), "dx2": (0, 0, 0), "add": (3, 0, 0), "mul": (0, 2, 1)},
 }
 SPMV_INSTR["qtw_nn"] = SPMV_INSTR["qtw"]
@@ -310,8 +311,8 @@ def cpu_baseline(torch, mw, M, A, b_np, b_dev, arith, tol, gpu_iters, k=CPU_SAMP
 # same product (computed once; ncu counts 8 DMUL per element).
 VEC_INSTR = {
     "qtw": {"update": (35, 18, 8), "p_update": (11, 6, 3)},
-    "dw": {"update": (27, 6, 3), "p_update": (9, 2, 1)},
-    "qdw": {"update": (12, 6, 3), "p_update": (3, 2, 1)},
+    "dw": {"update": (18, 6, 3), "p_update": (6, 2, 1)},     # products' QuickTwoSum on the integer pipe
+    "qdw": {"update": (9, 6, 3), "p_update": (3, 2, 1)},      # r's QuickTwoSum on the integer pipe
     "fp64": {"update": (1, 2, 1), "p_update": (0, 1, 0)},
 }
 

@@ -157,7 +157,7 @@ __device__ __forceinline__ double qadd_(double a, double b) {
 // Policy P (bit mask, same results): bit 0 DWadd's TwoSum, bit 1 DWadd's two
 // plain additions, bit 2 DWadd's closing QuickTwoSum, bit 3 the closing
 // QuickTwoSum of DWmul / FP64 x DW, run entirely on the integer pipe.
-template <int P = 0>
+template <int P = 8>
 struct DWt {
   static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
@@ -219,13 +219,18 @@ struct DWt {
   static __device__ __forceinline__ void normalize(T&) {}
   static __device__ __forceinline__ double collapse(const T& a) { return dadd(a.w[0], a.w[1]); }
 };
+// Every DW kernel runs the closing QuickTwoSum of its products on the integer
+// pipe (policy bit 3; DW's TwoProd error is there already).  Measured on c2:
+// SpMV 311.5 -> 289.5 us, update 165.9 -> 141.4 us, p update 54.4 -> 47.4 us;
+// bits 0-2 (the addition's operations), alone or with bit 3, make the SpMV
+// slower (342-426 us).
 using DW = DWt<>;
-using DW_S = DWt<0>;            // SpMV instantiation (the measured-best policy is the default)
+using DW_S = DWt<8>;
 
 // ---------------------------------------------------------------- QDW
 // Policy P: bit 0 QDWadd's TwoSum, bit 1 its two plain additions, bit 2 the
 // normalising QuickTwoSum, run entirely on the integer pipe (same bits).
-template <bool NORM, int P = 0>
+template <bool NORM, int P = 4>
 struct QDWt {
   static constexpr int ILP = 1;
   static constexpr int CHUNK = 1;
@@ -276,7 +281,11 @@ struct QDWt {
 };
 using QDW = QDWt<true>;
 using QDW_NN = QDWt<false>;
-using QDW_S = QDWt<true, 0>;     // SpMV instantiations (the default policy measured best)
+// The vector kernels normalise r with QuickTwoSum on the integer pipe (policy
+// bit 2; c2 update 102.5 -> 95.9 us); bit 1 (the addition's plain additions)
+// is slower (140.3 us).  The SpMV instantiations keep every FP64 operation on
+// the FP64 pipe (bits 0 / 1 there: 206 / 285 us against 155 us).
+using QDW_S = QDWt<true, 0>;
 using QDW_NN_S = QDWt<false, 0>;
 
 // ---------------------------------------------------------------- QTW
