@@ -60,7 +60,7 @@ static __device__ __noinline__ float3 split3_slow(double a) {
 // exponent k + 23 and fraction m minus the one with fraction 0, an exact
 // subtraction.  No FP64 instruction on this path.
 __device__ __forceinline__ void split3(double a, float& a0, float& a1, float& a2) {
-  const uint64_t u = (uint64_t)__double_as_longlong(a);
+  const uint64_t u = mwi::bits_of(a);      // opaque: keeps the range test off the FP64 pipe
   const uint32_t hi = (uint32_t)(u >> 32);
   const uint32_t sg = hi & 0x80000000u;
   const int e = (int)((hi >> 20) & 0x7FFu);
@@ -91,7 +91,10 @@ __device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((lo
 // (b_j normal and the scaled exponent inside the normal range).  That case is
 // four FP32 multiplications; the path declines (returns false) otherwise.
 __device__ __forceinline__ bool pow2_dxmul_f(double a, const float (&b)[4], float (&c)[4]) {
-  const uint64_t ua = (uint64_t)__double_as_longlong(a);
+  // The bits through an opaque move: a plain reinterpretation lets the
+  // compiler turn the tests below into FP64 comparisons (ncu counted one
+  // FP64-pipe instruction per stored entry).
+  const uint64_t ua = mwi::bits_of(a);
   if ((ua & 0x7FFFFFFFFFFFFFFFULL) == 0x3FF0000000000000ULL) {
     // a = +-1: no exponent changes, so every product (subnormal words
     // included) is exact for any finite b: a sign flip per word, +0 for a
