@@ -97,17 +97,18 @@ __device__ __forceinline__ bool pow2_dxmul_f(double a, const float (&b)[4], floa
   const uint64_t ua = mwi::bits_of(a);
   if ((ua & 0x7FFFFFFFFFFFFFFFULL) == 0x3FF0000000000000ULL) {
     // a = +-1: no exponent changes, so every product (subnormal words
-    // included) is exact for any finite b: a sign flip per word, +0 for a
-    // zero lower word.  Non-finite words decline.
-    const uint32_t sg = (uint32_t)(ua >> 32) & 0x80000000u;
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t u = __float_as_uint(b[j]);
-      ok = ok && ((u & 0x7F800000u) != 0x7F800000u);
-      c[j] = (j > 0 && (u << 1) == 0u) ? 0.0f : __uint_as_float(u ^ sg);
-    }
-    return ok;
+    // included) is exact for any finite b: a b0 (a zero keeps the product's
+    // sign), and a b_j + 0 for the lower words, which is a b_j when b_j is
+    // nonzero and +0 when it is zero, as the printed sequence returns them.
+    // Four FP32 instructions; the finite test is one more chain of four:
+    // x * 0 is NaN exactly when x is infinite or NaN.
+    const float af = __uint_as_float(((uint32_t)(ua >> 32) & 0x80000000u) | 0x3F800000u);
+    c[0] = fmul(af, b[0]);
+    c[1] = ffma(af, b[1], 0.0f);
+    c[2] = ffma(af, b[2], 0.0f);
+    c[3] = ffma(af, b[3], 0.0f);
+    const float t = ffma(b[3], 0.0f, ffma(b[2], 0.0f, ffma(b[1], 0.0f, fmul(b[0], 0.0f))));
+    return t == t;
   }
   const int ea = (int)((ua >> 52) & 0x7FFu);
   if ((ua & 0xFFFFFFFFFFFFFULL) != 0 || ea < 897 || ea > 1150) return false;

@@ -98,7 +98,20 @@ def _matrices():
     rp2 = np.zeros(A.n + 1, dtype=np.int64)
     np.cumsum(cnt, out=rp2[1:])
     out.append(P.CSR(A.n, rp2, A.col[keep], A.val[keep], "with_empty_rows"))
+    out.append(_drop_rows(P.laplacian_2d(45), (0, 33, 700, 2024), "stencil_with_empty_rows"))
     return out
+
+
+def _drop_rows(A, rows, name):
+    """A with the entries of `rows` removed (empty rows, same n)."""
+    rp = A.row_ptr
+    keep = np.ones(A.nnz, dtype=bool)
+    for i in rows:
+        keep[rp[i]:rp[i + 1]] = False
+    cnt = np.array([keep[rp[i]:rp[i + 1]].sum() for i in range(A.n)])
+    rp2 = np.zeros(A.n + 1, dtype=np.int64)
+    np.cumsum(cnt, out=rp2[1:])
+    return P.CSR(A.n, rp2, A.col[keep], A.val[keep], name)
 
 
 @pytest.mark.parametrize("arith", ARITHS)
@@ -147,6 +160,37 @@ def test_cg_bit_exact_against_mirrored_oracle(mw, orc, arith, case):
     assert (r.iters, r.status) == (ito, sto), (name, arith)
     assert same_bits(np.array([r.relres]), np.array([rro]))
     assert same_bits(host(r.x), xo)
+
+
+@pytest.mark.parametrize("arith", ["fp64", "dw", "qtw", "qqw", "qqf"])
+def test_value_updates_then_solve(mw, orc, arith):
+    """New values from the host, then from the device, on a stencil with empty
+    rows and a ragged tail: the solve and the SpMV equal the oracle's on the
+    new matrix, bit for bit."""
+    import torch
+    A = _drop_rows(P.laplacian_3d(13, 1e-2), (7, 2196), "lap3d_13_holes")   # 2197 rows
+    ln = np.diff(A.row_ptr)
+    dt = np.float32 if arith == "qqf" else np.float64      # FP32 words travel as float32
+    b = P.rhs_uniform(A.n, 21)
+    b[ln == 0] = 0.0                               # an empty row's equation is 0 = 0
+    M = mw.CSRMatrix.from_csr(A)
+    M.plan = (1, 256, 11)
+    rng = np.random.default_rng(22)
+    rows = np.repeat(np.arange(A.n), ln)
+    diag = A.col == rows
+    for step, on_device in ((0, False), (1, False), (2, True)):
+        val = A.val.copy()
+        if step:
+            val[diag] += rng.uniform(0.5, 1.0, diag.sum())       # still diagonally dominant
+        A2 = A.with_values(val)
+        if step:
+            M.update_values(torch.as_tensor(val, device="cuda") if on_device else val)
+        r = mw.solve(M, dev(b), arith, 1e-13, 3000)
+        xo, ito, rro, sto = orc.cg(arith, A2, b, tol=1e-13, maxit=3000, plan=(1, 256, 11))
+        assert (r.iters, r.status) == (ito, sto), (arith, step)
+        assert same_bits(host(r.x), xo), (arith, step)
+        q = host(mw.spmv(M, arith, torch.as_tensor(xo.astype(dt), device="cuda")))
+        assert same_bits(q, orc.spmv(arith, A2, xo, 1)), (arith, step)
 
 
 @pytest.mark.parametrize("arith", ["dw", "qtw", "fp64"])
