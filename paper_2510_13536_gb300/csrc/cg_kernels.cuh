@@ -333,21 +333,55 @@ __device__ __forceinline__ void spmv_alpha(const Work& W, typename A::T acc, boo
 
 // Entries kk[u], kk[u] + V, ... < ke[u] of the interleaved rows added into
 // sum[u] left to right; NS: normalise the running sum after every addition.
+// With A::CHUNK > 1 the loads of A::CHUNK entries of every interleaved row are
+// issued before the first multiply-add (more loads in flight per thread); the
+// products are still added in entry order.
 template <class A, bool NS>
 __device__ __forceinline__ void row_accumulate(const Csr& M, const double* __restrict__ p, int64_t n, int V,
                                                typename A::T* sum, int64_t* kk, const int64_t* ke) {
-  for (;;) {
-    bool more = false;
+  using T = typename A::T;
+  if constexpr (A::CHUNK == 1) {
+    for (;;) {
+      bool more = false;
 #pragma unroll
-    for (int u = 0; u < A::ILP_SPMV; ++u) {
-      if (kk[u] < ke[u]) {
-        sum[u] = A::dxmuladd(sum[u], M.val[kk[u]], ld<A>(p, n, M.col[kk[u]]));
-        if constexpr (NS) A::normalize(sum[u]);
-        kk[u] += V;
+      for (int u = 0; u < A::ILP_SPMV; ++u) {
+        if (kk[u] < ke[u]) {
+          sum[u] = A::dxmuladd(sum[u], M.val[kk[u]], ld<A>(p, n, M.col[kk[u]]));
+          if constexpr (NS) A::normalize(sum[u]);
+          kk[u] += V;
+        }
+        more = more || (kk[u] < ke[u]);
       }
-      more = more || (kk[u] < ke[u]);
+      if (!more) break;
     }
-    if (!more) break;
+  } else {
+    for (;;) {
+      bool more = false;
+      double va[A::ILP_SPMV][A::CHUNK];
+      T pv[A::ILP_SPMV][A::CHUNK];
+#pragma unroll
+      for (int u = 0; u < A::ILP_SPMV; ++u) {
+#pragma unroll
+        for (int c = 0; c < A::CHUNK; ++c) {
+          const int64_t k = kk[u] + (int64_t)c * V;
+          va[u][c] = 0.0;
+          if (k < ke[u]) { va[u][c] = M.val[k]; pv[u][c] = ld<A>(p, n, M.col[k]); }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < A::ILP_SPMV; ++u) {
+#pragma unroll
+        for (int c = 0; c < A::CHUNK; ++c) {
+          if (kk[u] < ke[u]) {
+            sum[u] = A::dxmuladd(sum[u], va[u][c], pv[u][c]);
+            if constexpr (NS) A::normalize(sum[u]);
+            kk[u] += V;
+          }
+        }
+        more = more || (kk[u] < ke[u]);
+      }
+      if (!more) break;
+    }
   }
 }
 
@@ -412,42 +446,10 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_spmv(Csr M, Work W, int mode) 
         kk[u] += V;
       }
     }
-    if constexpr (A::CHUNK == 1) {
-      // The normalising loop is a separate copy (a test inside the loop would
-      // be if-converted and cost every entry the normalisation's issue slots).
-      if (nsum) row_accumulate<A, true>(M, p, n, V, sum, kk, ke);
-      else row_accumulate<A, false>(M, p, n, V, sum, kk, ke);
-    } else {
-      // Memory-bound arithmetic: issue the loads of A::CHUNK entries of every
-      // interleaved row before the first multiply-add; the products are still
-      // added in entry order.
-      for (;;) {
-        bool more = false;
-        double va[A::ILP_SPMV][A::CHUNK];
-        T pv[A::ILP_SPMV][A::CHUNK];
-#pragma unroll
-        for (int u = 0; u < A::ILP_SPMV; ++u) {
-#pragma unroll
-          for (int c = 0; c < A::CHUNK; ++c) {
-            const int64_t k = kk[u] + (int64_t)c * V;
-            va[u][c] = 0.0;
-            if (k < ke[u]) { va[u][c] = M.val[k]; pv[u][c] = ld<A>(p, n, M.col[k]); }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < A::ILP_SPMV; ++u) {
-#pragma unroll
-          for (int c = 0; c < A::CHUNK; ++c) {
-            if (kk[u] < ke[u]) {
-              sum[u] = A::dxmuladd(sum[u], va[u][c], pv[u][c]);
-              kk[u] += V;
-            }
-          }
-          more = more || (kk[u] < ke[u]);
-        }
-        if (!more) break;
-      }
-    }
+    // The normalising loop is a separate copy (a test inside the loop would be
+    // if-converted and cost every entry the normalisation's issue slots).
+    if (nsum) row_accumulate<A, true>(M, p, n, V, sum, kk, ke);
+    else row_accumulate<A, false>(M, p, n, V, sum, kk, ke);
 #pragma unroll
     for (int u = 0; u < A::ILP_SPMV; ++u) {
       // Pairwise tree over the V lanes of the row (groups are aligned in the warp).
