@@ -140,8 +140,12 @@ const char* mwcg_last_error(void);
  *   val      double[nnz], finite;
  *   ptrs_on_device  0: the three arrays are host memory, 1: device memory;
  *   out      receives the handle (caller frees it with mwcg_destroy_csr).
- * The structure is validated on the host (device arrays are copied back for
- * that); violations return MWCG_ERR_ARG.  Symmetry is not checked: the paper
+ * The structure is validated; violations return MWCG_ERR_ARG, the message
+ * naming the first bad row_ptr entry, or the first entry k whose column or
+ * value is invalid (the column reported first).  row_ptr is checked on the
+ * host (device row_ptr is copied back, 8 (n+1) bytes); device col / val are
+ * checked on the device after the copy, with no host copy of the entries.
+ * Symmetry is not checked: the paper
  * stores symmetric matrices in general form (Sec. IV-B) and so does the
  * caller.  The arrays are copied; the caller keeps ownership of them. */
 int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,

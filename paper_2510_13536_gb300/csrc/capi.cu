@@ -324,17 +324,34 @@ mwcg_plan choose_plan(const double* passes, const double* warps, int64_t n, int 
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-int validate_csr(int64_t n, const int64_t* rp, const int32_t* col, const double* val) {
+int validate_row_ptr(int64_t n, const int64_t* rp) {
   if (rp[0] != 0) return fail(MWCG_ERR_ARG, "row_ptr[0] = %lld, expected 0", (long long)rp[0]);
   for (int64_t i = 0; i < n; ++i)
     if (rp[i + 1] < rp[i]) return fail(MWCG_ERR_ARG, "row_ptr decreases at row %lld", (long long)i);
-  const int64_t nnz = rp[n];
-  for (int64_t k = 0; k < nnz; ++k) {
-    if (col[k] < 0 || (int64_t)col[k] >= n)
-      return fail(MWCG_ERR_ARG, "col[%lld] = %d out of range [0, %lld)", (long long)k, col[k], (long long)n);
-    if (!std::isfinite(val[k])) return fail(MWCG_ERR_ARG, "val[%lld] is not finite", (long long)k);
-  }
   return MWCG_OK;
+}
+
+// The first invalid entry k (column outside [0, n) or value not finite), with
+// the column reported before the value.
+int entry_error(int64_t k, int32_t c, double v, int64_t n) {
+  if (c < 0 || (int64_t)c >= n)
+    return fail(MWCG_ERR_ARG, "col[%lld] = %d out of range [0, %lld)", (long long)k, c, (long long)n);
+  return fail(MWCG_ERR_ARG, "val[%lld] is not finite", (long long)k);
+}
+
+int validate_entries(int64_t n, int64_t nnz, const int32_t* col, const double* val) {
+  for (int64_t k = 0; k < nnz; ++k)
+    if (col[k] < 0 || (int64_t)col[k] >= n || !std::isfinite(val[k])) return entry_error(k, col[k], val[k], n);
+  return MWCG_OK;
+}
+
+// Smallest k with col[k] outside [0, n) or val[k] not finite, by an atomic
+// minimum (*first starts above any index).
+__global__ void k_first_bad_entry(const int32_t* __restrict__ col, const double* __restrict__ val, int64_t nnz,
+                                  int64_t n, int64_t* first) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+    if (col[k] < 0 || (int64_t)col[k] >= n || !isfinite(val[k]))
+      atomicMin(reinterpret_cast<unsigned long long*>(first), (unsigned long long)k);
 }
 
 template <class... Args>
@@ -875,22 +892,11 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
   const int64_t nnz = hrp[n];
   if (nnz < 0 || nnz > ((int64_t)1 << 40)) return fail(MWCG_ERR_ARG, "nnz = %lld out of range", (long long)nnz);
   if (nnz > 0 && (!col || !val)) return fail(MWCG_ERR_ARG, "null col or val");
-  std::vector<int32_t> hcol;
-  std::vector<double> hval;
-  const int32_t* vc = col;
-  const double* vv = val;
-  if (ptrs_on_device) {
-    hcol.resize(nnz);
-    hval.resize(nnz);
-    if (nnz) {
-      CK(cudaMemcpy(hcol.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(hval.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
-    }
-    vc = hcol.data();
-    vv = hval.data();
-  }
-  int rc = validate_csr(n, hrp.data(), vc, vv);
+  int rc = validate_row_ptr(n, hrp.data());
   if (rc != MWCG_OK) return rc;
+  // Host entries are checked here; device entries are checked on the device
+  // once copied (no host copy of the nnz entries).
+  if (!ptrs_on_device && (rc = validate_entries(n, nnz, col, val)) != MWCG_OK) return rc;
 
   mwcg_csr* A = new mwcg_csr();
   CK(cudaGetDevice(&A->device));
@@ -917,6 +923,28 @@ int mwcg_create_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const
       (e = cudaMemsetAsync(A->st, 0, sizeof(mwk::DevState), s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cleanup(fail(MWCG_ERR_CUDA, "copy to device: %s", cudaGetErrorString(e)));
+  if (ptrs_on_device && nnz) {
+    int64_t* first = nullptr;
+    int64_t bad = 0;
+    if ((e = cudaMalloc(&first, sizeof(int64_t))) == cudaSuccess &&
+        (e = cudaMemsetAsync(first, 0x7f, sizeof(int64_t), s)) == cudaSuccess) {
+      const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 4096);
+      k_first_bad_entry<<<grid, 256, 0, s>>>(A->col, A->val, nnz, n, first);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, first, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    cudaFree(first);
+    if (e != cudaSuccess) return cleanup(fail(MWCG_ERR_CUDA, "entry check: %s", cudaGetErrorString(e)));
+    if (bad < nnz) {
+      int32_t c = 0;
+      double v = 0.0;
+      if ((e = cudaMemcpy(&c, A->col + bad, sizeof c, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+          (e = cudaMemcpy(&v, A->val + bad, sizeof v, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cleanup(fail(MWCG_ERR_CUDA, "entry check: %s", cudaGetErrorString(e)));
+      return cleanup(entry_error(bad, c, v, n));
+    }
+  }
   {
     std::vector<int64_t> rowlen(n);
     for (int64_t i = 0; i < n; ++i) rowlen[i] = hrp[i + 1] - hrp[i];
