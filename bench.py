@@ -201,10 +201,15 @@ class ClockSampler:
                 "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None], default=None)}
 
 
+# The headers the CG kernels are built from: a committed ncu summary carries
+# their digest, and its counters are used only while the digest still matches.
+KERNEL_SOURCES = ("mw_int.cuh", "mw_device.cuh", "mw_float.cuh", "cg_kernels.cuh", "cg_float.cuh")
+
+
 def _kernel_source_digest() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("mw_device.cuh", "cg_kernels.cuh"):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2510_13536_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
