@@ -59,9 +59,9 @@ extern "C" {
  * mwcg_solve, mwcg_solve_history, mwcg_solve_host, mwcg_spmv, mwcg_dot,
  * mwcg_word_op (op 5 collapses its words to FP64) and mwcg_profile_kernels;
  * the normalisation policy does not apply to it (r is normalised every
- * iteration), and the preconditioner, BiCGStab, the adjoint, the batched
- * solve and mwcg_dot_noalloc return MWCG_ERR_ARG.  A solve whose x leaves
- * FP32's range returns MWCG_OUT_OF_RANGE.
+ * iteration).  It has CG, Jacobi PCG (mwcg_set_preconditioner), the adjoint
+ * and mwcg_dot_noalloc; BiCGStab and the batched solve return MWCG_ERR_ARG.
+ * A solve whose x leaves FP32's range returns MWCG_OUT_OF_RANGE.
  * QF is QQF with every addition and product (FP64 x QF included) followed
  * by VecSum4, the non-quasi counterpart of QQF as DW is of QDW: on strongly
  * cancelling rows its precision stays relative to the result.  It has QQF's
@@ -219,6 +219,10 @@ int mwcg_get_normalization(const mwcg_csr* A, int32_t* every, uint32_t* mask);
  *                     after this call or after mwcg_update_values; a diagonal
  *                     entry that is missing, not positive or not finite makes
  *                     the solve return MWCG_BAD_PRECONDITIONER with x0 untouched.
+ *                     MWCG_QQF / MWCG_QF run it with the scaled iteration of
+ *                     their CG (r~ = 2^-E r, z~ = w (x) r~, p~ = z~ + (beta~ 2^s) p~),
+ *                     the shift taken from the FP64 residual sum; the
+ *                     batched solve has no preconditioned QQF / QF.
  * Errors: unknown kind -> MWCG_ERR_ARG. */
 #define MWCG_PREC_NONE 0
 #define MWCG_PREC_JACOBI 1
@@ -300,8 +304,11 @@ int mwcg_batched_cluster_size(void);
  *   g_b[i]   = collapse(lambda_i)                (device double[n], may be NULL);
  *   g_val[k] = -collapse(lambda_row(k) * x_col(k)) (device double[nnz], may be NULL),
  *              the product taken in the arithmetic;
- *   x        device double[w*n], the forward solution (only it is needed).
- * Returns the status of the adjoint solve (as mwcg_solve) or an error. */
+ *   x        device double[w*n], the forward solution (only it is needed;
+ *            MWCG_QQF / MWCG_QF: its packed FP32 words, as mwcg_solve returns
+ *            them, and lambda is solved with the same scaled CG).
+ * Every arithmetic has an adjoint.  Returns the status of the adjoint solve
+ * (as mwcg_solve) or an error. */
 int mwcg_adjoint(mwcg_csr* A, const double* x, const double* gx, int arith, double tol, int32_t maxit, void* stream,
                  double* g_b, double* g_val, int32_t* iters_out, double* relres_out);
 
@@ -327,10 +334,12 @@ int mwcg_dot(int arith, int64_t n, const double* u, const double* v, int32_t G, 
  * one counter block, about 99 KB, held by every GPU that loads the library
  * until the process exits).  The function calls no cudaMalloc, cudaFree or
  * allocating library routine.
- *   arith    0..9 (MWCG_FP64 .. MWCG_QQW_NN); MWCG_QQF and MWCG_QF return MWCG_ERR_ARG;
- *   n, u, v, G  as in mwcg_dot (u, v device double[w*n]); G in
+ *   arith    0..11 (MWCG_FP64 .. MWCG_QF); any other value returns MWCG_ERR_ARG;
+ *   n, u, v, G  as in mwcg_dot (u, v device double[w*n], w = mwcg_words; for
+ *            MWCG_QQF / MWCG_QF the packed FP32 layout); G in
  *            1..MWCG_DOT_NOALLOC_MAX_G, larger G returns MWCG_ERR_ARG;
- *   out      device double[w] (caller-owned), written in stream order; the
+ *   out      device double[w] (caller-owned; double[4], one FP32 word per
+ *            double, for MWCG_QQF / MWCG_QF), written in stream order; the
  *            function does not synchronise the stream.
  * The result bits equal mwcg_dot's for the same arguments.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with

@@ -1122,6 +1122,20 @@ CGResult cg_qqf(int64_t n, const int64_t* rp, const int32_t* col, const double* 
 // ---------------------------------------------------------------------------
 enum { ST_BADPREC = 3 };
 
+// w_i = fl(1 / a_ii); false when a diagonal entry is missing, not positive or
+// not finite (the preconditioner is undefined).
+inline bool jacobi_weights(int64_t n, const int64_t* rp, const int32_t* col, const double* val, double* w) {
+  for (int64_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    bool found = false;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (col[k] == i) { d = val[k]; found = true; break; }
+    if (!found || !(d > 0.0) || !std::isfinite(d)) return false;
+    w[i] = fdiv(1.0, d);
+  }
+  return true;
+}
+
 template <class A>
 CGResult pcg_jacobi(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
                     const double* b, double* x, double tol, int maxit, Plan plan, double* hist,
@@ -1136,14 +1150,7 @@ CGResult pcg_jacobi(int64_t n, const int64_t* rp, const int32_t* col, const doub
   CGResult res{ST_CONVERGED, 0, 0.0};
 
   std::vector<double> w(n);
-  for (int64_t i = 0; i < n; ++i) {
-    double d = 0.0;
-    bool found = false;
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
-      if (col[k] == i) { d = val[k]; found = true; break; }
-    if (!found || !(d > 0.0) || !std::isfinite(d)) { res.status = ST_BADPREC; return res; }
-    w[i] = fdiv(1.0, d);
-  }
+  if (!jacobi_weights(n, rp, col, val, w.data())) { res.status = ST_BADPREC; return res; }
   double bn = fsqrt(bnorm2(b, n, Rv, G, plain));
   if (bn == 0.0) {
     for (int64_t i = 0; i < W * n; ++i) x[i] = 0.0;
@@ -1199,6 +1206,105 @@ CGResult pcg_jacobi(int64_t n, const int64_t* rp, const int32_t* col, const doub
       store<A>(p.data(), n, i, pi);
     }
     rho = rho1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi-preconditioned CG in QQF / QF: pcg_jacobi()'s recurrence with the
+// scaling of cg_qqf().  With r = 2^E r~, z~ = w (x) r~ (so z = 2^E z~), p = 2^E p~
+// and rho = 2^2E rho~, rho~ = r~^T z~:
+//   alpha = rho~ / p~^T q~;  x = x + (alpha 2^E) p~;
+//   r~' = 2^-s normalise(r~ + (-alpha) q~), E' = E + s;  z~' = w (x) r~';
+//   beta = 2^2s beta~, beta~ = rho~' / rho~;  p~' = z~' + (beta~ 2^s) p~.
+// Readings (this project's; the paper has no preconditioned solver):
+//  * z~ = w (x) r~ is the definition (the FP64 x QQF product of the scaled r~;
+//    w (x) r would be its 2^E multiple wherever neither underflows).
+//  * The stopping residual is pcg_jacobi()'s: 2^E sqrt(sum_i fl(c_i c_i)) /
+//    ||b||_2, c_i = collapse(r~_i), the sum an FP64 dot in the plan's order;
+//    and the shift s is taken from that sum (the norm of r~, which the scaling
+//    keeps near 1) in place of cg_qqf()'s rho~, which is not r~'s norm here.
+//  * Everything else (weights, ST_BADPREC, zero b / r0, breakdown, maxit, the
+//    range of x, the fixed normalisation policy) as pcg_jacobi() and cg_qqf().
+// ---------------------------------------------------------------------------
+template <class A>
+CGResult pcg_qqf(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, Plan plan, double* hist) {
+  using T = typename A::T;
+  const int W = A::W;
+  const bool plain = plan.V <= 0;
+  const int V = plain ? 1 : plan.V;
+  const int64_t Rs = plain ? 1 : std::max(1, plan.T / V);
+  const int64_t Rv = plain ? 1 : plan.T;
+  const int G = plain ? 1 : plan.G;
+  CGResult res{ST_CONVERGED, 0, 0.0};
+
+  std::vector<double> w(n);
+  if (!jacobi_weights(n, rp, col, val, w.data())) { res.status = ST_BADPREC; return res; }
+  const double bb = bnorm2(b, n, Rv, G, plain);
+  const double bn = fsqrt(bb);
+  if (bn == 0.0) {
+    for (int64_t i = 0; i < W * n; ++i) x[i] = 0.0;
+    return res;
+  }
+  int E = scale_exp(bb, n);
+  std::vector<double> r(W * n), z(W * n), p(W * n), q(W * n), c(n);
+  spmv<A>(rp, col, val, x, q.data(), n, V);                   // A x0, unscaled
+  for (int64_t i = 0; i < n; ++i) {
+    T ri = A::add(A::from(std::ldexp(b[i], -E)), scale_words(neg<A>(load<A>(q.data(), n, i)), -E));
+    store<A>(r.data(), n, i, ri);
+    store<A>(z.data(), n, i, A::dxmul(w[i], ri));
+    c[i] = A::collapse(ri);
+  }
+  p = z;
+  T rho = dot<A>(r.data(), z.data(), n, Rv, G, plain);
+  bool rzero = true;
+  for (int k = 0; k < W; ++k) rzero = rzero && (rho.w[k] == 0.0f);
+  if (rzero) return res;
+  double rr = dot<FP64>(c.data(), c.data(), n, Rv, G, plain).w[0];
+  res.relres = fdiv(std::ldexp(fsqrt(rr), E), bn);
+  if (maxit <= 0) { res.status = ST_MAXIT; return res; }
+  int s = clamp_shift(scale_exp(rr, n), E);
+
+  for (;;) {
+    spmv<A>(rp, col, val, p.data(), q.data(), n, V);
+    T pq = dot<A>(p.data(), q.data(), n, Rs, G, plain);
+    res.iters += 1;
+    double pqc = A::collapse(pq);
+    if (!(pqc > 0.0) || !std::isfinite(pqc)) { res.status = ST_BREAKDOWN; return res; }
+    T alpha = A::div(rho, pq);
+    T cx = scale_words(alpha, E);
+    T malpha = neg<A>(alpha);
+    double xmax = 0.0;
+    bool xfinite = true;
+    for (int64_t i = 0; i < n; ++i) {
+      T xi = A::muladd(load<A>(x, n, i), cx, load<A>(p.data(), n, i));
+      store<A>(x, n, i, xi);
+      if (!std::isfinite(xi.w[0])) xfinite = false;
+      else xmax = std::max(xmax, (double)std::fabs(xi.w[0]));
+      T ri = A::muladd(load<A>(r.data(), n, i), malpha, load<A>(q.data(), n, i));
+      A::normalize(ri);
+      ri = scale_words(ri, -s);
+      store<A>(r.data(), n, i, ri);
+      store<A>(z.data(), n, i, A::dxmul(w[i], ri));
+      c[i] = A::collapse(ri);
+    }
+    E += s;
+    T rho1 = dot<A>(r.data(), z.data(), n, Rv, G, plain);
+    rr = dot<FP64>(c.data(), c.data(), n, Rv, G, plain).w[0];
+    const double relres = fdiv(std::ldexp(fsqrt(rr), E), bn);
+    res.relres = relres;
+    if (hist) hist[res.iters - 1] = relres;
+    const bool x_under = xmax < std::ldexp(1.0, -126);
+    if (!xfinite) { res.status = ST_RANGE; return res; }
+    if (relres < tol) { res.status = x_under ? (int)ST_RANGE : (int)ST_CONVERGED; return res; }
+    if (!std::isfinite(relres)) { res.status = ST_BREAKDOWN; return res; }
+    if (res.iters >= maxit) { res.status = x_under ? (int)ST_RANGE : (int)ST_MAXIT; return res; }
+    T beta = A::div(rho1, rho);
+    T cp = scale_words(beta, s);
+    for (int64_t i = 0; i < n; ++i)
+      store<A>(p.data(), n, i, A::muladd(load<A>(z.data(), n, i), cp, load<A>(p.data(), n, i)));
+    rho = rho1;
+    s = clamp_shift(scale_exp(rr, n), E);
   }
 }
 
@@ -1463,9 +1569,11 @@ template <class A> struct OpGrad {
   }
 };
 
-// QQF and QF run Algorithm 1 with the scaling of cg_qqf(); the policy, the
-// preconditioned solver, BiCGStab and the adjoint's gradient are not defined
-// for them (status -2).
+// QQF and QF run Algorithm 1 with the scaling of cg_qqf() and the Jacobi PCG
+// with that of pcg_qqf(); the policy and BiCGStab are not defined for them
+// (status -2).
+// The adjoint's gradient is grad_values above: lambda and x are the unscaled
+// solutions cg_qqf() returns, multiplied in the arithmetic and collapsed.
 template <class A> struct OpCGScaled {
   static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
                  const double* b, double* x, double tol, int maxit, int V, int T, int G,
@@ -1482,13 +1590,22 @@ struct Unsupported {
   template <class... Args> static int run(Args...) { return -2; }
 };
 template <> struct OpCGNorm<QQF> : Unsupported {};
-template <> struct OpPCG<QQF> : Unsupported {};
+template <class A> struct OpPCGScaled {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                 int every, unsigned mask, int* iters, double* relres, double* hist) {
+    if (every != 1 || mask != NORM_R) return -2;     // the policy is fixed, as in cg_qqf()
+    CGResult r = pcg_qqf<A>(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist);
+    *iters = r.iters;
+    *relres = r.relres;
+    return r.status;
+  }
+};
+template <> struct OpPCG<QQF> : OpPCGScaled<QQF> {};
 template <> struct OpBiCG<QQF> : Unsupported {};
-template <> struct OpGrad<QQF> : Unsupported {};
 template <> struct OpCGNorm<QF> : Unsupported {};
-template <> struct OpPCG<QF> : Unsupported {};
+template <> struct OpPCG<QF> : OpPCGScaled<QF> {};
 template <> struct OpBiCG<QF> : Unsupported {};
-template <> struct OpGrad<QF> : Unsupported {};
 
 }  // namespace
 

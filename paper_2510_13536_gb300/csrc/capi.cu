@@ -86,7 +86,7 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr int kNArith = 12;   // MWCG_FP64 .. MWCG_QF
 // The FP32-word arithmetics: scaled CG, packed vectors, no batched, cluster,
-// preconditioned, BiCGStab or adjoint solve.
+// preconditioned or BiCGStab solve (the adjoint is the scaled CG too).
 bool fp32_words(int arith) { return arith == MWCG_QQF || arith == MWCG_QF; }
 constexpr int kMaxG = 1024;
 

@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(TPB) k_qqf_bnorm(Csr M, Work W) {
 
 // r~0 = split3(b 2^-E0) (+) 2^-E0 (-(A x0)) with A x0 in q, p~0 = r~0,
 // rho~0 = r~0^T r~0; the last block sets the scalars and the stop flags.
-template <class A>
+// PREC (Jacobi-preconditioned CG): z~0 = w (x) r~0 into q, p~0 = z~0,
+// rho~0 = r~0^T z~0, and the residual norm and the shift from the FP64 sum
+// of collapse(r~_i)^2.
+template <class A, bool PREC = false>
 __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
@@ -129,13 +132,27 @@ __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
   const int64_t ntiles = (n + TPB - 1) / TPB;
   T acc = A::zero();
   bool pacc = false;
+  mw::MW<1> rr{{0.0}};
+  bool prr = false;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t i = t * TPB + threadIdx.x;
     if (i < n) {
       const T ri = A::add(A::from(__dmul_rn(b[i], sb)), A::scale(A::neg(ld<A>(W.q, n, i)), -E));
       st<A>(W.r, n, i, ri);
-      st<A>(W.p, n, i, ri);
-      const T leaf = A::mul(ri, ri);
+      T leaf;
+      if constexpr (PREC) {
+        const T zi = A::dxmul(W.w[i], ri);
+        st<A>(W.q, n, i, zi);
+        st<A>(W.p, n, i, zi);
+        leaf = A::mul(ri, zi);
+        const double c = A::collapse(ri);
+        const mw::MW<1> lc{{mw::dmul(c, c)}};
+        if (prr) rr = mw::FP64::add(rr, lc);
+        else { rr = lc; prr = true; }
+      } else {
+        st<A>(W.p, n, i, ri);
+        leaf = A::mul(ri, ri);
+      }
       if (pacc) acc = A::add(acc, leaf);
       else { acc = leaf; pacc = true; }
     }
@@ -143,7 +160,16 @@ __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
   block_tree<A>(acc, pacc, 1);
   T rho;
   bool prho = false;
-  if (!grid_reduce<A, 0>(W, acc, pacc, rho, prho)) return;
+  double rrt = 0.0;
+  if constexpr (PREC) {
+    block_tree<mw::FP64>(rr, prr, 1);
+    double fo[1];
+    bool pfo[1];
+    if (!grid_reduce_mix<A, 1>(W, acc, pacc, &rr.w[0], &prr, rho, prho, fo, pfo)) return;
+    if (threadIdx.x == 0) rrt = pfo[0] ? fo[0] : 0.0;
+  } else {
+    if (!grid_reduce<A, 0>(W, acc, pacc, rho, prho)) return;
+  }
   if (threadIdx.x == 0) {
     S->counter = 0;
     if (!prho) rho = A::zero();
@@ -162,7 +188,8 @@ __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
       bool rzero = true;
 #pragma unroll
       for (int k = 0; k < A::W; ++k) rzero = rzero && (rho.w[k] == 0.0f);
-      S->relres = __ddiv_rn(__dmul_rn(__dsqrt_rn(A::collapse(rho)), mw::pow2d(E)), bnorm);
+      const double c = PREC ? rrt : A::collapse(rho);
+      S->relres = __ddiv_rn(__dmul_rn(__dsqrt_rn(c), mw::pow2d(E)), bnorm);
       if (rzero) {
         S->relres = 0.0;
         S->done = 1;
@@ -171,7 +198,7 @@ __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
         S->done = 1;
       }
     }
-    qqf_set_scale(S, E, 0, clamp_shift(scale_exp(A::collapse(rho), n), E));
+    qqf_set_scale(S, E, 0, clamp_shift(scale_exp(PREC ? rrt : A::collapse(rho), n), E));
   }
 }
 
@@ -181,7 +208,9 @@ __global__ void __launch_bounds__(TPB) k_qqf_init(Csr M, Work W) {
 // reduced by an atomic maximum of its bits (an order-free reduction); a value
 // that is not finite ends the solve with ST_RANGE, and so does a solve that
 // would end converged or at maxit with every leading word below 2^-126.
-template <class A>
+// PREC: z~ = w (x) r~ into q, rho~' = r~^T z~, and the stop test and the next
+// shift on the FP64 sum of collapse(r~_i)^2 (the order of pcg_jacobi's).
+template <class A, bool PREC = false>
 __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
@@ -199,6 +228,8 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
   const int64_t ntiles = (n + TPB - 1) / TPB;
   T acc = A::zero();
   bool pacc = false;
+  mw::MW<1> rr{{0.0}};
+  bool prr = false;
   uint32_t xb = 0;                 // largest |x_i0| bits of this thread's rows (NaN and inf above finite)
   // A::ILP tiles (t, t + G, ...) per pass, all loads first: the kernel is bound
   // by memory latency.  Each slot still adds its leaves in increasing tile
@@ -230,7 +261,18 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
 #pragma unroll
         for (int j = 0; j < A::W; ++j) ri.w[j] = mw::fmul(ri.w[j], ps);
         st<A>(W.r, n, idx[u], ri);
-        const T leaf = A::mul(ri, ri);
+        T leaf;
+        if constexpr (PREC) {
+          const T zi = A::dxmul(W.w[idx[u]], ri);
+          st<A>(W.q, n, idx[u], zi);
+          leaf = A::mul(ri, zi);
+          const double c = A::collapse(ri);
+          const mw::MW<1> lc{{mw::dmul(c, c)}};
+          if (prr) rr = mw::FP64::add(rr, lc);
+          else { rr = lc; prr = true; }
+        } else {
+          leaf = A::mul(ri, ri);
+        }
         if (pacc) acc = A::add(acc, leaf);
         else { acc = leaf; pacc = true; }
       }
@@ -251,7 +293,16 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
   block_tree<A>(acc, pacc, 1);
   T tot;
   bool ptot = false;
-  if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  double rrt = 0.0;
+  if constexpr (PREC) {
+    block_tree<mw::FP64>(rr, prr, 1);
+    double fo[1];
+    bool pfo[1];
+    if (!grid_reduce_mix<A, 1>(W, acc, pacc, &rr.w[0], &prr, tot, ptot, fo, pfo)) return;
+    if (threadIdx.x == 0) rrt = pfo[0] ? fo[0] : 0.0;
+  } else {
+    if (!grid_reduce<A, 0>(W, acc, pacc, tot, ptot)) return;
+  }
   if (threadIdx.x == 0) {
     S->counter = 0;
     if (!ptot) tot = A::zero();
@@ -259,7 +310,7 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
     S->xmax_bits = 0;
     const bool x_nonfinite = xm >= 0x7F800000u, x_under = xm < 0x00800000u;
     const int En = E + s;
-    const double c = A::collapse(tot);
+    const double c = PREC ? rrt : A::collapse(tot);
     const double relres = __ddiv_rn(__dmul_rn(__dsqrt_rn(c), mw::pow2d(En)), S->bnorm);
     S->relres = relres;
     const int it = S->iters;
@@ -289,13 +340,14 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_update(Csr M, Work W) {
   }
 }
 
-// p~ = r~ + (beta~ 2^s) p~.
-template <class A>
+// p~ = r~ + (beta~ 2^s) p~ (PREC: p~ = z~ + (beta~ 2^s) p~, z~ in q).
+template <class A, bool PREC = false>
 __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_pupdate(Csr M, Work W) {
   using T = typename A::T;
   DevState* S = W.st;
   if (S->done) return;
   const int64_t n = M.n;
+  const double* __restrict__ src = PREC ? W.q : W.r;
   const T cp = A::scale(load_scalar_f<A>(S->beta), qqf_shift(S));
   const int64_t stride = (int64_t)gridDim.x * TPB;
   for (int64_t i0 = (int64_t)blockIdx.x * TPB + threadIdx.x; i0 < n; i0 += (int64_t)A::ILP * stride) {
@@ -303,7 +355,7 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_pupdate(Csr M, Work W) {
 #pragma unroll
     for (int u = 0; u < A::ILP; ++u) {
       const int64_t i = i0 + u * stride;
-      if (i < n) { rr[u] = ld<A>(W.r, n, i); pp[u] = ld<A>(W.p, n, i); }
+      if (i < n) { rr[u] = ld<A>(src, n, i); pp[u] = ld<A>(W.p, n, i); }
     }
 #pragma unroll
     for (int u = 0; u < A::ILP; ++u) {
@@ -313,9 +365,10 @@ __global__ void __launch_bounds__(TPB, A::MINB) k_qqf_pupdate(Csr M, Work W) {
   }
 }
 
-// The kernel table of QQF or QF (A): plain CG only (no normalisation policy,
-// no preconditioner, no adjoint gradient kernel); vectors of two 8-byte
-// slots.  Its init is preceded by k_qqf_bnorm (qqf_init_pre in inst_qqf.cu).
+// The kernel table of QQF or QF (A): CG and Jacobi PCG with the fixed
+// normalisation policy (r every iteration), and the adjoint's gradient;
+// vectors of two 8-byte slots.  Its init is preceded by k_qqf_bnorm
+// (qqf_init_pre in inst_qqf.cu).
 template <class A>
 inline KernelTable make_table_qqf() {
   KernelTable t{};
@@ -328,9 +381,13 @@ inline KernelTable make_table_qqf() {
   t.pupdate = (const void*)&k_qqf_pupdate<A>;
   t.update_pol = t.update;
   t.pupdate_pol = t.pupdate;
-  t.init_pcg = t.update_pcg = t.pupdate_pcg = t.update_pcg_pol = t.pupdate_pcg_pol = nullptr;
+  t.init_pcg = (const void*)&k_qqf_init<A, true>;
+  t.update_pcg = (const void*)&k_qqf_update<A, true>;
+  t.pupdate_pcg = (const void*)&k_qqf_pupdate<A, true>;
+  t.update_pcg_pol = t.update_pcg;
+  t.pupdate_pcg_pol = t.pupdate_pcg;
   t.zero_x = (const void*)&k_zero_x<kQqfSlots>;
-  t.grad_values = nullptr;
+  t.grad_values = (const void*)&k_grad_values<A>;
   t.collapse = (const void*)&k_collapse<A>;
   t.dot = (const void*)&k_dot<A>;
   t.word_op = (const void*)&k_word_op<A>;

@@ -28,6 +28,8 @@ KernelTable table_qtw_nn();
 KernelTable table_qw();
 KernelTable table_qqw();
 KernelTable table_qqw_nn();
+KernelTable table_qqf();
+KernelTable table_qf();
 }  // namespace mwk
 
 namespace mwcg_detail {
@@ -50,7 +52,7 @@ std::mutex g_mu;
 double* g_scratch_dev[kMaxDevices] = {};    // device address of g_dot_scratch, per device
 
 const mwk::KernelTable& table_of(int arith) {
-  static mwk::KernelTable t[10];
+  static mwk::KernelTable t[12];
   static std::once_flag once;
   std::call_once(once, [] {
     t[0] = mwk::table_fp64();
@@ -63,6 +65,8 @@ const mwk::KernelTable& table_of(int arith) {
     t[7] = mwk::table_qw();
     t[8] = mwk::table_qqw();
     t[9] = mwk::table_qqw_nn();
+    t[10] = mwk::table_qqf();
+    t[11] = mwk::table_qf();
   });
   return t[arith];
 }
@@ -97,7 +101,7 @@ int scratch_on_current_device(double** out) {
 extern "C" int mwcg_dot_noalloc(int arith, int64_t n, const double* u, const double* v, int32_t G, void* stream,
                                 double* out) {
   mwcg_detail::set_error(MWCG_OK, "");
-  if (arith < 0 || arith > 9) return mwcg_detail::set_error(MWCG_ERR_ARG, "mwcg_dot_noalloc: unknown arithmetic");
+  if (arith < 0 || arith > 11) return mwcg_detail::set_error(MWCG_ERR_ARG, "mwcg_dot_noalloc: unknown arithmetic");
   if (n < 0) return mwcg_detail::set_error(MWCG_ERR_ARG, "mwcg_dot_noalloc: n < 0");
   if (G < 1 || G > kNoallocMaxG) {
     char buf[160];
@@ -110,7 +114,8 @@ extern "C" int mwcg_dot_noalloc(int arith, int64_t n, const double* u, const dou
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const mwk::KernelTable& kt = table_of(arith);
   if (n == 0) {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * kt.words, s);
+    const int outw = arith >= MWCG_QQF ? 4 : kt.words;   // FP32 words: one per double
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * outw, s);
     return e == cudaSuccess ? MWCG_OK : err(MWCG_ERR_CUDA, "cudaMemsetAsync", e);
   }
   double* base = nullptr;

@@ -39,8 +39,8 @@ def _pack(x: torch.Tensor, n: int) -> torch.Tensor:
     """(4, n) FP32 words -> the C ABI's (2, n) slots (words 2k, 2k+1 in slot k)."""
     if n == 0:
         return torch.empty((2, 0), dtype=torch.float64, device=x.device)
-    f = x.to(torch.float32).reshape(2, 2, n).permute(0, 2, 1).contiguous()
-    return f.view(torch.float64).reshape(2, n).contiguous()
+    f = x.to(torch.float32).reshape(2, 2, n).permute(0, 2, 1).reshape(2, 2 * n).contiguous()
+    return f.view(torch.float64)             # (2, n); the flat last axis views at any n
 
 
 def _unpack(x: torch.Tensor, n: int) -> torch.Tensor:
@@ -303,7 +303,7 @@ def adjoint(A: CSRMatrix, x: torch.Tensor, gx: torch.Tensor, arith="qtw", tol: f
     g_b = torch.empty(A.n, dtype=torch.float64, device=gx.device)
     g_val = torch.empty(A.nnz, dtype=torch.float64, device=gx.device)
     it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
-    xc, gc = x.contiguous(), gx.contiguous()           # held until the call returns
+    xc, gc = _to_abi(a, x, A.n), gx.to(torch.float64).contiguous()   # held until the call returns
     st = check(_capi.load().mwcg_adjoint(A.handle, _ptr(xc), _ptr(gc), a, float(tol), int(maxit), _stream(),
                                          _ptr(g_b), _ptr(g_val), ctypes.byref(it), ctypes.byref(rr)))
     return g_b, g_val, it.value, rr.value, st

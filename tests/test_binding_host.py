@@ -7,8 +7,11 @@ import torch
 from paper_2510_13536_gb300 import _capi, solver
 
 
-def test_qqf_slot_layout_and_round_trip():
-    n = 7
+import pytest
+
+
+@pytest.mark.parametrize("n", [1, 2, 7])
+def test_qqf_slot_layout_and_round_trip(n):
     x = torch.arange(4 * n, dtype=torch.float32).reshape(4, n) * 0.5 - 3.0
     p = solver._pack(x, n)
     assert p.dtype == torch.float64 and p.shape == (2, n) and p.is_contiguous()
@@ -19,9 +22,9 @@ def test_qqf_slot_layout_and_round_trip():
     assert torch.equal(solver._unpack(p, n), x)
 
 
-def test_numpy_and_torch_packing_agree():
+@pytest.mark.parametrize("n", [1, 11])
+def test_numpy_and_torch_packing_agree(n):
     rng = np.random.default_rng(3)
-    n = 11
     x = rng.standard_normal((4, n)).astype(np.float32)
     pt = solver._pack(torch.as_tensor(x), n).numpy()
     pn = solver._pack_np(x, n)

@@ -78,7 +78,7 @@ def test_null_arguments_rejected(lib):
     assert lib.mwcg_dot(4, 10, None, None, 0, None, None) == -1
     assert lib.mwcg_collapse(None, 4, 10, None, None) == -1
     out = (ctypes.c_double * 4)()
-    assert lib.mwcg_dot_noalloc(10, 10, None, None, 1, None, out) == -1      # QQF has no no-alloc dot
+    assert lib.mwcg_dot_noalloc(10, 10, None, None, 1, None, out) == -1      # QQF: null inputs
+    assert b"null u or v" in lib.mwcg_last_error()
+    assert lib.mwcg_dot_noalloc(12, 10, None, None, 1, None, out) == -1      # no arithmetic 12
     assert b"unknown arithmetic" in lib.mwcg_last_error()
-    assert lib.mwcg_dot_noalloc(11, 10, None, None, 1, None, out) == -1      # nor has QF
-    assert lib.mwcg_dot_noalloc(12, 10, None, None, 1, None, out) == -1

@@ -245,6 +245,85 @@ def test_host_buffers(mw, orc, ar):
     assert (it, st) == (ito, sto) and x.dtype == np.float32 and same_bits(x, xo)
 
 
+def test_adjoint_bit_exact(mw, orc, ar):
+    """lambda (the scaled CG on dL/dx), g_b = collapse(lambda) and
+    g_val = -collapse(lambda_i x_j) equal the oracle's bit for bit, through the
+    C ABI and through autograd."""
+    import torch
+    A = P.diffusion_2d(48, 9)
+    b = P.rhs_uniform(A.n, 81)
+    w = np.random.default_rng(82).standard_normal(A.n)
+    M = mw.CSRMatrix.from_csr(A)
+    r = mw.solve(M, dev(b), ar, 1e-20, 2000)
+    xo, ito, _, sto = orc.cg(ar, A, b, tol=1e-20, maxit=2000, plan=M.plan)
+    assert (r.iters, r.status) == (ito, sto) == (ito, 0) and same_bits(r.x.cpu().numpy(), xo)
+    g_b, g_val, it, rr, st = mw.adjoint(M, r.x, dev(w), ar, 1e-20, 2000)
+    ob, ov, lam, oit, orr, ost = orc.adjoint(ar, A, xo, w, 1e-20, 2000, plan=M.plan)
+    assert (it, st) == (oit, ost) and st == 0
+    assert same_bits(np.array([rr]), np.array([orr]))
+    assert same_bits(g_b.cpu().numpy(), ob) and same_bits(g_val.cpu().numpy(), ov)
+    vals = torch.tensor(A.val, dtype=torch.float64, device="cuda", requires_grad=True)
+    bb = torch.tensor(b, dtype=torch.float64, device="cuda", requires_grad=True)
+    x = mw.solve_differentiable(M, vals, bb, ar, 1e-20, 2000)
+    (x * dev(w)).sum().backward()
+    assert same_bits(vals.grad.cpu().numpy(), ov) and same_bits(bb.grad.cpu().numpy(), ob)
+
+
+def _check_pcg(mw, orc, M, A, b, tol, maxit, tag, ar):
+    r = mw.solve(M, dev(b), ar, tol, maxit, history=True)
+    xo, ito, rro, sto, ho = orc.cg(ar, A, b, tol=tol, maxit=maxit, plan=M.plan, precond="jacobi", history=True)
+    assert (r.iters, r.status) == (ito, sto), (tag, r.iters, ito, r.status, sto)
+    assert same_bits(np.array([r.relres]), np.array([rro])), tag
+    assert same_bits(r.x.cpu().numpy(), xo), tag
+    if r.iters:
+        assert same_bits(r.history.cpu().numpy(), ho), tag
+    return r
+
+
+def test_jacobi_pcg_bit_exact(mw, orc, ar, monkeypatch):
+    """Jacobi PCG in FP32 words (the scaled iteration, z~ = w (x) r~ into q,
+    the shift and the stop test from the FP64 residual sum) equals the
+    oracle's bit for bit: iterations, status, residual history and x, on the
+    graph and on host-launched kernels; a bad diagonal gives status 3."""
+    cases = ((P.diffusion_2d(48, 9), 83, 1e-20, 2000),
+             (P.power_law_laplacian(3000, seed=7, mean_deg=12, max_deg=300), 84, 1e-14, 3000),
+             (P.laplacian_3d(24, 1e-3), 85, 1e-22, 300))
+    for A, seed, tol, maxit in cases:
+        b = P.rhs_uniform(A.n, seed)
+        M = mw.CSRMatrix.from_csr(A)
+        M.preconditioner = "jacobi"
+        r = _check_pcg(mw, orc, M, A, b, tol, maxit, A.name, ar)
+        assert r.iters > 10
+    A, seed, tol, maxit = cases[0]
+    b = P.rhs_uniform(A.n, seed)
+    monkeypatch.setenv("MWCG_EAGER", "1")
+    M = mw.CSRMatrix.from_csr(A)
+    M.preconditioner = "jacobi"
+    _check_pcg(mw, orc, M, A, b, tol, maxit, "eager", ar)
+    monkeypatch.delenv("MWCG_EAGER")
+    B = P.CSR(A.n, A.row_ptr.copy(), A.col.copy(), A.val.copy())
+    B.val[[k for k in range(B.row_ptr[7], B.row_ptr[8]) if B.col[k] == 7][0]] = -1.0
+    MB = mw.CSRMatrix.from_csr(B)
+    MB.preconditioner = "jacobi"
+    r = mw.solve(MB, dev(b), ar, tol, maxit)
+    assert (r.status, r.iters) == (3, 0)
+
+
+def test_jacobi_pcg_adjoint_bit_exact(mw, orc, ar):
+    A = P.diffusion_2d(40, 10)
+    b = P.rhs_uniform(A.n, 86)
+    w = np.random.default_rng(87).standard_normal(A.n)
+    M = mw.CSRMatrix.from_csr(A)
+    M.preconditioner = "jacobi"
+    r = mw.solve(M, dev(b), ar, 1e-20, 2000)
+    assert r.status == 0
+    g_b, g_val, it, rr, st = mw.adjoint(M, r.x, dev(w), ar, 1e-20, 2000)
+    ob, ov, lam, oit, orr, ost = orc.adjoint(ar, A, r.x.cpu().numpy().astype(np.float64), w, 1e-20, 2000,
+                                             plan=M.plan, precond="jacobi")
+    assert (it, st) == (oit, ost) == (oit, 0)
+    assert same_bits(g_b.cpu().numpy(), ob) and same_bits(g_val.cpu().numpy(), ov)
+
+
 def test_unsupported_paths_rejected(mw, ar):
     import torch
     from paper_2510_13536_gb300._capi import MWCGError
@@ -255,10 +334,4 @@ def test_unsupported_paths_rejected(mw, ar):
         mw.solve_bicgstab(M, b, ar, 1e-10, 10)
     with pytest.raises(MWCGError):
         mw.solve_batched([M], [b], ar, 1e-10, 10)
-    with pytest.raises(MWCGError):
-        mw.adjoint(M, torch.zeros((2, A.n), dtype=torch.float64, device="cuda"), b, ar, 1e-10, 10)
-    M.preconditioner = "jacobi"
-    with pytest.raises(MWCGError):
-        mw.solve(M, b, ar, 1e-10, 10)
-    M.preconditioner = "none"
     assert mw.solve(M, b, ar, 1e-10, 200).status == 0

@@ -211,6 +211,30 @@ def test_tracks_double_word_cg(orc):
     assert np.max(np.abs(xq64 - xd64)) <= 1e-20 * np.max(np.abs(xd64))
 
 
+@pytest.mark.parametrize("ar", ["qqf", "qf"])
+def test_adjoint_gradient_equals_triple_word(orc, ar):
+    """The adjoint in FP32 words (lambda by the scaled CG, g_val = -lambda_i x_j
+    in the arithmetic, collapsed) against TW's, whose adjoint is pinned to exact
+    rational gradients and central differences: solved to 1e-24 both are
+    exact to FP64, so the collapsed gradients agree to a few ulps."""
+    for A in (P.laplacian_3d(8, 1e-2), P.diffusion_2d(20, seed=5)):
+        b = P.rhs_uniform(A.n, 5)
+        w = np.random.default_rng(3).standard_normal(A.n)
+        x, it, _, st = orc.cg(ar, A, b, tol=1e-24, maxit=5000)
+        xt, itt, _, stt = orc.cg("tw", A, b, tol=1e-24, maxit=5000)
+        assert st == stt == 0
+        g_b, g_val, lam, it2, _, st2 = orc.adjoint(ar, A, x, w, 1e-24, 5000)
+        t_b, t_val, _, _, _, _ = orc.adjoint("tw", A, xt, w, 1e-24, 5000)
+        assert st2 == 0 and is_f32(lam) and g_val.shape == (A.nnz,)
+        assert np.max(np.abs(g_b - t_b)) <= 4e-16 * np.max(np.abs(t_b))
+        assert np.max(np.abs(g_val - t_val)) <= 4e-16 * np.max(np.abs(t_val))
+        # A mutation of the formula (the sign, or lambda and x swapped on a
+        # nonsymmetric pattern of values) would fail: g_val is -lambda_row x_col.
+        rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+        lam64, x64 = orc.collapse(ar, lam), orc.collapse(ar, x)
+        assert np.allclose(g_val, -lam64[rows] * x64[A.col], rtol=1e-12, atol=0)
+
+
 def test_special_cases(orc):
     A = P.laplacian_2d(10)
     x, it, rr, st = orc.cg("qqf", A, np.zeros(A.n), x0=np.ones((4, A.n)), tol=1e-10, maxit=20)
@@ -224,7 +248,7 @@ def test_special_cases(orc):
     assert (it, st) == (0, 1) and rr == 1.0
     with pytest.raises(ValueError):
         orc.cg("qqf", A, b, norm=(2, 1))
-    with pytest.raises(ValueError):
-        orc.cg("qqf", A, b, precond="jacobi")
+    with pytest.raises(ValueError):                 # Jacobi PCG keeps the fixed policy too
+        orc.cg("qqf", A, b, precond="jacobi", norm=(2, 1))
     with pytest.raises(ValueError):
         orc.bicgstab("qqf", A, b)
