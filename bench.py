@@ -544,7 +544,8 @@ def run_pcg(torch, mw, P, cpu):
     """Jacobi-preconditioned CG against Algorithm 1 on three workloads: the
     3-D Poisson system (constant diagonal: the preconditioner only rescales),
     the variable-coefficient diffusion system and the power-law graph
-    Laplacian (degrees 5..1000: the diagonal spans three orders of magnitude)."""
+    Laplacian (degrees 5..1000: the diagonal spans three orders of magnitude);
+    FP64-word (FP64, DW, QTW) and FP32-word (QQF, QF) arithmetics."""
     out = {}
     for name in ("c2", "c5", "c3"):
         A, b, tol, maxit = P.workload(name)
@@ -552,7 +553,7 @@ def run_pcg(torch, mw, P, cpu):
         M = mw.CSRMatrix.from_csr(A)
         db = torch.as_tensor(b, device="cuda")
         res = {"workload": name + ": " + P.WORKLOADS[name], "tol": tol, "maxit": maxit, "plan": list(M.plan)}
-        for ar in ("fp64", "dw", "qtw"):
+        for ar in ("fp64", "dw", "qtw", "qqf", "qf"):
             for pc in ("none", "jacobi"):
                 M.preconditioner = pc
                 mw.solve(M, db, ar, tol, 2)                  # graph build, weights

@@ -59,8 +59,8 @@ extern "C" {
  * mwcg_solve, mwcg_solve_history, mwcg_solve_host, mwcg_spmv, mwcg_dot,
  * mwcg_word_op (op 5 collapses its words to FP64) and mwcg_profile_kernels;
  * the normalisation policy does not apply to it (r is normalised every
- * iteration).  It has CG, Jacobi PCG (mwcg_set_preconditioner), the adjoint
- * and mwcg_dot_noalloc; BiCGStab and the batched solve return MWCG_ERR_ARG.
+ * iteration).  It has CG, Jacobi PCG (mwcg_set_preconditioner), the batched
+ * solve, the adjoint and mwcg_dot_noalloc; BiCGStab returns MWCG_ERR_ARG.
  * A solve whose x leaves FP32's range returns MWCG_OUT_OF_RANGE.
  * QF is QQF with every addition and product (FP64 x QF included) followed
  * by VecSum4, the non-quasi counterpart of QQF as DW is of QDW: on strongly
@@ -221,8 +221,7 @@ int mwcg_get_normalization(const mwcg_csr* A, int32_t* every, uint32_t* mask);
  *                     the solve return MWCG_BAD_PRECONDITIONER with x0 untouched.
  *                     MWCG_QQF / MWCG_QF run it with the scaled iteration of
  *                     their CG (r~ = 2^-E r, z~ = w (x) r~, p~ = z~ + (beta~ 2^s) p~),
- *                     the shift taken from the FP64 residual sum; the
- *                     batched solve has no preconditioned QQF / QF.
+ *                     the shift taken from the FP64 residual sum.
  * Errors: unknown kind -> MWCG_ERR_ARG. */
 #define MWCG_PREC_NONE 0
 #define MWCG_PREC_JACOBI 1
@@ -289,6 +288,9 @@ int mwcg_solve_history(mwcg_csr* A, const double* b, double* x, int arith, doubl
  * take systems from a device queue (largest first) and run each solve to its
  * end; a system's summation order, and so its result bits, equal those of
  * mwcg_solve with plan {V of its handle, 256, mwcg_batched_cluster_size()}.
+ * Every arithmetic is accepted, QQF and QF with their scaled iteration (x[s]
+ * in the packed FP32 layout; status MWCG_OUT_OF_RANGE as in mwcg_solve), and
+ * a handle's Jacobi preconditioner applies to its system.
  * Returns MWCG_OK when the launch succeeded (per-system outcomes are in
  * status_out), or an error. */
 int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b, double* const* x,

@@ -20,6 +20,8 @@ cudaError_t run_group_02(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, 
 cudaError_t run_group_10(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
 cudaError_t run_group_11(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
 cudaError_t run_group_12(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
+cudaError_t run_group_03(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
+cudaError_t run_group_13(Sys*, int, unsigned*, cudaStream_t, int, size_t, int*, int);
 const void* kernel_00();
 
 }  // namespace mwb
@@ -79,13 +81,14 @@ cudaError_t launch(mwb::Sys* hsys, int nsys, cudaStream_t s, int cluster, int* c
   // A single system keeps one CTA per SM (the pad); a batch packs two CTAs of
   // (possibly different) clusters per SM.
   const size_t pad = nsys == 1 ? mwb::kPadSmem : 0;
-  constexpr int NG = 6;
+  constexpr int NG = 8;                      // (preconditioned or not) x four word groups
   static const mwb::RunGroup run[NG] = {mwb::run_group_00, mwb::run_group_01, mwb::run_group_02,
-                                        mwb::run_group_10, mwb::run_group_11, mwb::run_group_12};
+                                        mwb::run_group_03, mwb::run_group_10, mwb::run_group_11,
+                                        mwb::run_group_12, mwb::run_group_13};
   std::vector<mwb::Sys> grp[NG];
   std::vector<int> where[NG];
   for (int i = 0; i < nsys; ++i) {
-    const int g = (hsys[i].w ? 3 : 0) + mwb::word_group(hsys[i].arith);
+    const int g = (hsys[i].w ? 4 : 0) + mwb::word_group(hsys[i].arith);
     grp[g].push_back(hsys[i]);
     where[g].push_back(i);
   }

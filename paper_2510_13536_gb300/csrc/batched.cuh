@@ -416,10 +416,11 @@ __device__ void solve_cluster(const ClusterCtx& cc, Slots* slots, Sys& S) {
 }
 
 // Word groups of the persistent kernel: GRP 0 = FP64, DW, QDW, QDW-NN;
-// GRP 1 = TW, QTW, QTW-NN; GRP 2 = QW, QQW, QQW-NN (the last needs the
-// four-word arithmetics of mw_device4.cuh, included by its translation units).
+// GRP 1 = TW, QTW, QTW-NN; GRP 2 = QW, QQW, QQW-NN (the four-word
+// arithmetics of mw_device4.cuh, included by its translation units); GRP 3 =
+// QQF, QF (four FP32 words, the scaled iteration of batched_float.cuh).
 inline int word_group(int arith) {
-  return (arith == 3 || arith == 4 || arith == 6) ? 1 : (arith >= 7) ? 2 : 0;
+  return (arith == 3 || arith == 4 || arith == 6) ? 1 : (arith >= 10) ? 3 : (arith >= 7) ? 2 : 0;
 }
 
 template <bool PREC, int GRP>

@@ -85,8 +85,8 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr int kNArith = 12;   // MWCG_FP64 .. MWCG_QF
-// The FP32-word arithmetics: scaled CG, packed vectors, no batched, cluster,
-// preconditioned or BiCGStab solve (the adjoint is the scaled CG too).
+// The FP32-word arithmetics: scaled CG, packed vectors; no BiCGStab, and a
+// single small system runs the graph, not the one-cluster launch.
 bool fp32_words(int arith) { return arith == MWCG_QQF || arith == MWCG_QF; }
 constexpr int kMaxG = 1024;
 
@@ -1329,7 +1329,6 @@ int mwcg_solve_batched(int32_t nsys, mwcg_csr* const* A, const double* const* b,
   for (int s = 0; s < nsys; ++s) {
     int rc = check_solve_args(A[s], b[s], x[s], arith[s], tol[s], maxit[s]);
     if (rc != MWCG_OK) return fail(rc, "system %d: %s", s, g_err.c_str());
-    if (fp32_words(arith[s])) return fail(MWCG_ERR_ARG, "system %d: QQF and QF are not batched", s);
     if (!seen.insert(A[s]).second) return fail(MWCG_ERR_ARG, "system %d: matrix handle repeated in the batch", s);
     if ((rc = ensure_ws(A[s])) != MWCG_OK) return rc;
     if ((rc = select_plan(A[s], arith[s], S(stream))) != MWCG_OK) return rc;

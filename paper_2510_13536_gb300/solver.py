@@ -271,11 +271,11 @@ def solve_batched(As, bs, arith, tol, maxit, x0s=None):
     mi = list(maxit) if isinstance(maxit, (list, tuple)) else [int(maxit)] * ns
     xs = []
     for s in range(ns):
-        w = WORDS[ar[s]]
+        n = As[s].n
         if x0s is None or x0s[s] is None:
-            xs.append(torch.zeros((w, As[s].n), dtype=torch.float64, device=bs[s].device))
-        else:
-            xs.append(x0s[s].to(torch.float64).reshape(w, As[s].n).clone().contiguous())
+            xs.append(torch.zeros((SLOTS[ar[s]], n), dtype=torch.float64, device=bs[s].device))
+        else:                                   # the ABI layout (QQF / QF: packed FP32 words), a copy
+            xs.append(_to_abi(ar[s], x0s[s], n).clone())
     P = ctypes.c_void_p
     hA = (P * ns)(*[A.handle.value for A in As])
     hb = (P * ns)(*[b.data_ptr() for b in bs])
@@ -289,7 +289,7 @@ def solve_batched(As, bs, arith, tol, maxit, x0s=None):
     for b in bs:
         _ptr(b)
     check(_capi.load().mwcg_solve_batched(ns, hA, hb, hx, har, htl, hmi, _stream(), it, rr, stt))
-    return [SolveResult(xs[s], it[s], rr[s], stt[s]) for s in range(ns)]
+    return [SolveResult(_from_abi(ar[s], xs[s], As[s].n), it[s], rr[s], stt[s]) for s in range(ns)]
 
 
 def batched_cluster_size() -> int:

@@ -324,14 +324,55 @@ def test_jacobi_pcg_adjoint_bit_exact(mw, orc, ar):
     assert same_bits(g_b.cpu().numpy(), ob) and same_bits(g_val.cpu().numpy(), ov)
 
 
-def test_unsupported_paths_rejected(mw, ar):
+def test_batched_bit_exact(mw, orc, ar):
+    """The persistent batched kernel runs QQF / QF with the scaled iteration:
+    every system equals the oracle's solve in plan {V, 256, cluster size}, bit
+    for bit, beside a DW system of the same batch (another word group, launched
+    concurrently): CG and Jacobi PCG, b = 0, a maxit stop, a breakdown (QQF on
+    the cancelling power-law graph) and x leaving FP32's range (status 4)."""
     import torch
+    rng = np.random.default_rng(91)
+    specs = []                        # (A, b, arith, tol, maxit, preconditioner)
+    for k in range(10):
+        kind = k % 3
+        if kind == 0:
+            A = P.laplacian_2d(int(rng.integers(5, 60)), float(10 ** rng.uniform(-6, -2)))
+        elif kind == 1:
+            A = P.laplacian_3d(int(rng.integers(3, 22)), float(10 ** rng.uniform(-6, -2)))
+        else:
+            A = P.diffusion_2d(int(rng.integers(5, 40)), seed=k)
+        specs.append((A, P.rhs_uniform(A.n, 200 + k), ar, 1e-20, 3000, "jacobi" if k % 2 else None))
+    specs.append((P.laplacian_2d(30), P.rhs_uniform(900, 5), "dw", 1e-20, 3000, None))
+    specs.append((P.laplacian_2d(10), np.zeros(100), ar, 1e-12, 100, None))
+    specs.append((P.laplacian_2d(12), P.rhs_uniform(144, 7), ar, 1e-30, 4, None))
+    specs.append((P.power_law_laplacian(3000, seed=7, mean_deg=12, max_deg=300), P.rhs_uniform(3000, 84), ar,
+                  1e-14, 3000, "jacobi"))
+    specs.append((P.laplacian_2d(16), P.rhs_uniform(256, 9) * 2.0 ** 300, ar, 1e-20, 500, None))
+    Ms = []
+    for A, b, a, tol, maxit, pc in specs:
+        M = mw.CSRMatrix.from_csr(A)
+        if pc:
+            M.preconditioner = pc
+        Ms.append(M)
+    bs = [torch.as_tensor(sp[1], device="cuda") for sp in specs]
+    res = mw.solve_batched(Ms, bs, [sp[2] for sp in specs], [sp[3] for sp in specs], [sp[4] for sp in specs])
+    C = mw.batched_cluster_size()
+    statuses = set()
+    for (A, b, a, tol, maxit, pc), M, r in zip(specs, Ms, res):
+        V = M.plan_for(a)[0]
+        xo, ito, rro, sto = orc.cg(a, A, b, tol=tol, maxit=maxit, plan=(V, 256, C), precond=pc)
+        assert (r.iters, r.status) == (ito, sto), (A.name, a, pc, r.iters, ito, r.status, sto)
+        assert same_bits(np.array([r.relres]), np.array([rro])), (A.name, a, pc)
+        assert same_bits(r.x.cpu().numpy(), xo), (A.name, a, pc)
+        statuses.add(sto)
+    assert {0, 1, 4} <= statuses and (2 in statuses) == (ar == "qqf")
+
+
+def test_unsupported_paths_rejected(mw, ar):
     from paper_2510_13536_gb300._capi import MWCGError
     A = P.laplacian_2d(20)
     M = mw.CSRMatrix.from_csr(A)
     b = dev(P.rhs_uniform(A.n, 80))
     with pytest.raises(MWCGError):
         mw.solve_bicgstab(M, b, ar, 1e-10, 10)
-    with pytest.raises(MWCGError):
-        mw.solve_batched([M], [b], ar, 1e-10, 10)
     assert mw.solve(M, b, ar, 1e-10, 200).status == 0
