@@ -85,8 +85,7 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr int kNArith = 12;   // MWCG_FP64 .. MWCG_QF
-// The FP32-word arithmetics: scaled CG, packed vectors; no BiCGStab, and a
-// single small system runs the graph, not the one-cluster launch.
+// The FP32-word arithmetics: scaled CG, packed vectors, no BiCGStab.
 bool fp32_words(int arith) { return arith == MWCG_QQF || arith == MWCG_QF; }
 constexpr int kMaxG = 1024;
 
@@ -702,7 +701,7 @@ int run_solve(mwcg_csr* A, const double* b, double* x, int arith, double tol, in
   }
   const int64_t tiles = (A->n + mwk::TPB - 1) / mwk::TPB;
   const int small = mwb_host::small_cluster_size();
-  if (!eager_mode() && A->plan.G == small && tiles <= small && !fp32_words(arith))
+  if (!eager_mode() && A->plan.G == small && tiles <= small)
     return run_cluster(A, b, x, arith, tol, maxit, hist, s, iters_out, relres_out);
   const bool eager = eager_mode();
   if (!eager && (rc = ensure_graph(A, arith)) != MWCG_OK) return rc;

@@ -175,12 +175,16 @@ def test_eager_launches(mw, orc, ar, monkeypatch):
     _check(mw, orc, M, A, b, 1e-20, 400, "eager", ar=ar)
 
 
-def test_small_systems_run_the_graph(mw, orc, ar):
-    """Systems small enough for the one-cluster launch of the other arithmetics."""
+def test_small_systems_one_cluster(mw, orc, ar):
+    """Systems small enough for the one-cluster launch (plan G = the cluster
+    size): the cluster solve of the scaled iteration, CG and Jacobi PCG, equals
+    the oracle in that plan, history included."""
     for A in (P.laplacian_2d(40), P.laplacian_2d(5), P.random_spd_small(9, seed=3)):
         b = P.rhs_uniform(A.n, 75)
         M = mw.CSRMatrix.from_csr(A)
         _check(mw, orc, M, A, b, 1e-22, 400, A.name, ar=ar)
+        M.preconditioner = "jacobi"
+        _check_pcg(mw, orc, M, A, b, 1e-22, 400, A.name + " pcg", ar)
 
 
 def test_scaling_far_outside_fp32_range(mw, orc, ar):
