@@ -59,8 +59,9 @@ extern "C" {
  * mwcg_solve, mwcg_solve_history, mwcg_solve_host, mwcg_spmv, mwcg_dot,
  * mwcg_word_op (op 5 collapses its words to FP64) and mwcg_profile_kernels;
  * the normalisation policy does not apply to it (r is normalised every
- * iteration).  It has CG, Jacobi PCG (mwcg_set_preconditioner), the batched
- * solve, the adjoint and mwcg_dot_noalloc; BiCGStab returns MWCG_ERR_ARG.
+ * iteration).  It has CG, Jacobi PCG (mwcg_set_preconditioner), BiCGStab,
+ * the batched solve, the adjoint and mwcg_dot_noalloc, each with the scaled
+ * iteration.
  * A solve whose x leaves FP32's range returns MWCG_OUT_OF_RANGE.
  * QF is QQF with every addition and product (FP64 x QF included) followed
  * by VecSum4, the non-quasi counterpart of QQF as DW is of QDW: on strongly
@@ -245,7 +246,12 @@ int mwcg_get_preconditioner(const mwcg_csr* A, int* kind);
  * mwcg_solve_history.  Returns MWCG_OK, MWCG_NOT_CONVERGED, MWCG_BREAKDOWN
  * (collapse of rho, rh^T v or t^T t zero or not finite, omega's collapse zero,
  * or a non-finite residual) or an error.  The handle's preconditioner and
- * normalisation policy apply to CG only; BiCGStab has no batched form. */
+ * normalisation policy apply to CG only; BiCGStab has no batched form.
+ * MWCG_QQF / MWCG_QF run it scaled: r, p, v, s, t at 2^E and the shadow
+ * residual at 2^E0, alpha and omega unscaled, x += (alpha 2^E) p~ +
+ * (omega 2^E) s~, r~ shifted by 2^-sh after its AXPY (sh from the FP64 sum of
+ * the r~ it replaces), beta~ = (rho~'/rho~)(alpha/omega); x in the packed FP32
+ * layout, MWCG_OUT_OF_RANGE as in mwcg_solve. */
 int mwcg_solve_bicgstab(mwcg_csr* A, const double* b, double* x, int arith, double tol, int32_t maxit, double* hist,
                         void* stream, int32_t* iters_out, double* relres_out);
 

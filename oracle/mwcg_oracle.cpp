@@ -1431,6 +1431,137 @@ CGResult bicgstab(int64_t n, const int64_t* rp, const int32_t* col, const double
   }
 }
 
+// ---------------------------------------------------------------------------
+// BiCGStab in QQF / QF: bicgstab()'s recurrence with the scaling of cg_qqf().
+// r, p, v, s and t are held at 2^E (r = 2^E r~, ...), the shadow residual at
+// 2^E0 (rh~ = r~0).  rho = rh^T r and rh^T v carry the same factor 2^(E0+E),
+// so alpha = rho~ / rh~^T v~ and omega = t~^T s~ / t~^T t~ are the unscaled
+// values; s~ = normalise(r~ + (-alpha) v~);
+// x = (x + (alpha 2^E) p~) + (omega 2^E) s~;
+// r~' = 2^-sh normalise(s~ + (-omega) t~), E' = E + sh; beta = 2^sh beta~ with
+// beta~ = (rho~' / rho~)(alpha / omega), and p~' = r~' + beta~ (p~ + (-omega) v~)
+// is at 2^E' without rescaling.  Readings (this project's):
+//  * the FP64 stopping residuals are 2^E sqrt(sum_i collapse(.)^2) / ||b||;
+//  * the shift sh is taken, as in pcg_qqf(), from the FP64 sum of the r~ it
+//    replaces, clamped as in cg_qqf();
+//  * the range of x as in cg_qqf(), tested after each x update (the early
+//    exit's included); everything else as bicgstab().
+// ---------------------------------------------------------------------------
+template <class A>
+double fp64_sumsq(const std::vector<double>& v, int64_t n, int64_t Rv, int G, bool plain) {
+  std::vector<double> c(n);
+  for (int64_t i = 0; i < n; ++i) c[i] = A::collapse(load<A>(v.data(), n, i));
+  return dot<FP64>(c.data(), c.data(), n, Rv, G, plain).w[0];
+}
+
+template <class A>
+CGResult bicgstab_qqf(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                      const double* b, double* x, double tol, int maxit, Plan plan, double* hist) {
+  using T = typename A::T;
+  const int W = A::W;
+  const bool plain = plan.V <= 0;
+  const int V = plain ? 1 : plan.V;
+  const int64_t Rs = plain ? 1 : std::max(1, plan.T / V);
+  const int64_t Rv = plain ? 1 : plan.T;
+  const int G = plain ? 1 : plan.G;
+  CGResult res{ST_CONVERGED, 0, 0.0};
+  const double bb = bnorm2(b, n, Rv, G, plain);
+  const double bn = fsqrt(bb);
+  if (bn == 0.0) {
+    for (int64_t i = 0; i < W * n; ++i) x[i] = 0.0;
+    return res;
+  }
+  int E = scale_exp(bb, n);
+  std::vector<double> r(W * n), rh(W * n), p(W * n), v(W * n), s(W * n), t(W * n);
+  spmv<A>(rp, col, val, x, v.data(), n, V);                   // A x0, unscaled
+  for (int64_t i = 0; i < n; ++i)
+    store<A>(r.data(), n, i,
+             A::add(A::from(std::ldexp(b[i], -E)), scale_words(neg<A>(load<A>(v.data(), n, i)), -E)));
+  rh = r;
+  T rho = dot<A>(rh.data(), r.data(), n, Rv, G, plain);
+  bool rzero = true;
+  for (int k = 0; k < W; ++k) rzero = rzero && (rho.w[k] == 0.0f);
+  if (rzero) return res;
+  double rr = fp64_sumsq<A>(r, n, Rv, G, plain);
+  res.relres = fdiv(std::ldexp(fsqrt(rr), E), bn);
+  if (maxit <= 0) { res.status = ST_MAXIT; return res; }
+  int sh = clamp_shift(scale_exp(rr, n), E);
+  T rho_prev = A::zero(), alpha = A::zero(), omega = A::zero();
+  for (;;) {
+    if (bad_scalar<A>(rho)) { res.status = ST_BREAKDOWN; return res; }
+    if (res.iters == 0) {
+      p = r;
+    } else {
+      T beta = A::mul(A::div(rho, rho_prev), A::div(alpha, omega));
+      T momega = neg<A>(omega);
+      for (int64_t i = 0; i < n; ++i) {
+        T tmp = A::muladd(load<A>(p.data(), n, i), momega, load<A>(v.data(), n, i));
+        store<A>(p.data(), n, i, A::muladd(load<A>(r.data(), n, i), beta, tmp));
+      }
+    }
+    spmv<A>(rp, col, val, p.data(), v.data(), n, V);
+    T rv = dot<A>(rh.data(), v.data(), n, Rs, G, plain);
+    res.iters += 1;
+    if (bad_scalar<A>(rv)) { res.status = ST_BREAKDOWN; return res; }
+    alpha = A::div(rho, rv);
+    T malpha = neg<A>(alpha);
+    for (int64_t i = 0; i < n; ++i) {
+      T si = A::muladd(load<A>(r.data(), n, i), malpha, load<A>(v.data(), n, i));
+      A::normalize(si);
+      store<A>(s.data(), n, i, si);
+    }
+    const T ca = scale_words(alpha, E);
+    double xmax = 0.0;
+    bool xfinite = true;
+    auto track = [&](const T& xi) {
+      if (!std::isfinite(xi.w[0])) xfinite = false;
+      else xmax = std::max(xmax, (double)std::fabs(xi.w[0]));
+    };
+    const double rs_ = fdiv(std::ldexp(fsqrt(fp64_sumsq<A>(s, n, Rv, G, plain)), E), bn);
+    if (rs_ < tol) {
+      for (int64_t i = 0; i < n; ++i) {
+        T xi = A::muladd(load<A>(x, n, i), ca, load<A>(p.data(), n, i));
+        store<A>(x, n, i, xi);
+        track(xi);
+      }
+      res.relres = rs_;
+      if (hist) hist[res.iters - 1] = rs_;
+      const bool x_under = xmax < std::ldexp(1.0, -126);
+      res.status = (!xfinite || x_under) ? (int)ST_RANGE : (int)ST_CONVERGED;
+      return res;
+    }
+    spmv<A>(rp, col, val, s.data(), t.data(), n, V);
+    T ts = dot<A>(t.data(), s.data(), n, Rs, G, plain);
+    T tt = dot<A>(t.data(), t.data(), n, Rs, G, plain);
+    if (bad_scalar<A>(tt)) { res.status = ST_BREAKDOWN; return res; }
+    omega = A::div(ts, tt);
+    T momega = neg<A>(omega);
+    const T co = scale_words(omega, E);
+    for (int64_t i = 0; i < n; ++i) {
+      T xi = A::muladd(A::muladd(load<A>(x, n, i), ca, load<A>(p.data(), n, i)), co, load<A>(s.data(), n, i));
+      store<A>(x, n, i, xi);
+      track(xi);
+      T ri = A::muladd(load<A>(s.data(), n, i), momega, load<A>(t.data(), n, i));
+      A::normalize(ri);
+      store<A>(r.data(), n, i, scale_words(ri, -sh));
+    }
+    E += sh;
+    T rho1 = dot<A>(rh.data(), r.data(), n, Rv, G, plain);
+    rr = fp64_sumsq<A>(r, n, Rv, G, plain);
+    const double relres = fdiv(std::ldexp(fsqrt(rr), E), bn);
+    res.relres = relres;
+    if (hist) hist[res.iters - 1] = relres;
+    const bool x_under = xmax < std::ldexp(1.0, -126);
+    if (!xfinite) { res.status = ST_RANGE; return res; }
+    if (relres < tol) { res.status = x_under ? (int)ST_RANGE : (int)ST_CONVERGED; return res; }
+    if (!std::isfinite(relres) || A::collapse(omega) == 0.0) { res.status = ST_BREAKDOWN; return res; }
+    if (res.iters >= maxit) { res.status = x_under ? (int)ST_RANGE : (int)ST_MAXIT; return res; }
+    rho_prev = rho;
+    rho = rho1;
+    sh = clamp_shift(scale_exp(rr, n), E);
+  }
+}
+
 // Gradient of L = w^T x through A x = b (values only, sparsity kept):
 // dL/dval_k = -lambda_row(k) * x_col(k), lambda the adjoint solution, formed
 // as the arithmetic's product lambda_i * x_j and collapsed to FP64.
@@ -1569,9 +1700,9 @@ template <class A> struct OpGrad {
   }
 };
 
-// QQF and QF run Algorithm 1 with the scaling of cg_qqf() and the Jacobi PCG
-// with that of pcg_qqf(); the policy and BiCGStab are not defined for them
-// (status -2).
+// QQF and QF run Algorithm 1 with the scaling of cg_qqf(), the Jacobi PCG
+// with that of pcg_qqf() and BiCGStab with that of bicgstab_qqf(); the
+// normalisation policy is not defined for them (status -2).
 // The adjoint's gradient is grad_values above: lambda and x are the unscaled
 // solutions cg_qqf() returns, multiplied in the arithmetic and collapsed.
 template <class A> struct OpCGScaled {
@@ -1602,10 +1733,20 @@ template <class A> struct OpPCGScaled {
   }
 };
 template <> struct OpPCG<QQF> : OpPCGScaled<QQF> {};
-template <> struct OpBiCG<QQF> : Unsupported {};
+template <class A> struct OpBiCGScaled {
+  static int run(int64_t n, const int64_t* rp, const int32_t* col, const double* val,
+                 const double* b, double* x, double tol, int maxit, int V, int T, int G,
+                 int* iters, double* relres, double* hist) {
+    CGResult r = bicgstab_qqf<A>(n, rp, col, val, b, x, tol, maxit, Plan{V, T, G}, hist);
+    *iters = r.iters;
+    *relres = r.relres;
+    return r.status;
+  }
+};
+template <> struct OpBiCG<QQF> : OpBiCGScaled<QQF> {};
 template <> struct OpCGNorm<QF> : Unsupported {};
 template <> struct OpPCG<QF> : OpPCGScaled<QF> {};
-template <> struct OpBiCG<QF> : Unsupported {};
+template <> struct OpBiCG<QF> : OpBiCGScaled<QF> {};
 
 }  // namespace
 

@@ -25,7 +25,7 @@ SOURCES = ["capi.cu", "batched.cu", "batched_k00.cu", "batched_k01.cu", "batched
            "precond.cu", "inst_fp64.cu", "inst_dw.cu", "inst_qdw.cu", "inst_tw.cu", "inst_qtw.cu", "inst_qw.cu",
            "inst_qqw.cu", "inst_qqf.cu", "inst_qf.cu", "inst_bicg_a.cu", "inst_bicg_b.cu", "inst_bicg_c.cu"]
 HEADERS = ["mw_device.cuh", "mw_device4.cuh", "mw_float.cuh", "mw_int.cuh", "cg_kernels.cuh", "cg_float.cuh",
-           "bicg_kernels.cuh", "batched.cuh", "batched_float.cuh"]
+           "bicg_kernels.cuh", "bicg_float.cuh", "batched.cuh", "batched_float.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", INCLUDE, "-I", CSRC]

@@ -60,6 +60,8 @@ BiTable bitable_qtw_nn();
 BiTable bitable_qw();
 BiTable bitable_qqw();
 BiTable bitable_qqw_nn();
+BiTable bitable_qqf();
+BiTable bitable_qf();
 }  // namespace mwk
 
 namespace {
@@ -85,7 +87,7 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr int kNArith = 12;   // MWCG_FP64 .. MWCG_QF
-// The FP32-word arithmetics: scaled CG, packed vectors, no BiCGStab.
+// The FP32-word arithmetics: scaled CG and BiCGStab, packed vectors.
 bool fp32_words(int arith) { return arith == MWCG_QQF || arith == MWCG_QF; }
 constexpr int kMaxG = 1024;
 
@@ -155,12 +157,14 @@ const mwk::BiTable* bitable(int arith) {
     t[7] = mwk::bitable_qw();
     t[8] = mwk::bitable_qqw();
     t[9] = mwk::bitable_qqw_nn();
+    t[10] = mwk::bitable_qqf();
+    t[11] = mwk::bitable_qf();
     for (auto& k : t)
       for (const void* f : {k.init, k.spmv_v, k.s, k.spmv_t, k.xr})
         if (f) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem(kMaxG, 4));
     cudaGetLastError();
   });
-  if (arith < 0 || arith >= kNArith || !t[arith].init) return nullptr;   // none for QQF and QF
+  if (arith < 0 || arith >= kNArith || !t[arith].init) return nullptr;
   return &t[arith];
 }
 
@@ -766,10 +770,13 @@ int ensure_bigraph(mwcg_csr* A, int arith) {
   const mwk::Work W = work_view(A, (unsigned long long)h, 1);
   const mwk::BiWork B = biwork_view(A, (unsigned long long)h, 1);
   cudaGraphNode_t n0, n1, n2, nw, b[5];
+  cudaGraphNode_t npre = nullptr;
   int rc;
   const int mode0 = 0;
+  const void* pre = init_pre(arith);          // QQF / QF: ||b|| and the first scale
   if ((rc = add_kernel(&n0, g, nullptr, 0, kt->spmv, G, smem, M, W, mode0)) ||
-      (rc = add_kernel(&n1, g, &n0, 1, bt->init, G, smem, M, B)) ||
+      (pre && (rc = add_kernel(&npre, g, &n0, 1, pre, G, smem, M, W))) ||
+      (rc = add_kernel(&n1, g, npre ? &npre : &n0, 1, bt->init, G, smem, M, B)) ||
       (rc = add_kernel(&n2, g, &n1, 1, kt->zero_x, G, 0, M, W))) {
     cudaGraphDestroy(g);
     return rc;
@@ -834,6 +841,7 @@ int run_bicg(mwcg_csr* A, const double* b, double* x, int arith, double tol, int
     void* a_w[] = {(void*)&M, (void*)&W};
     void* a_b[] = {(void*)&M, (void*)&B};
     CK(cudaLaunchKernel(kt->spmv, dim3(G), dim3(mwk::TPB), a_spmv0, smem, s));
+    if (const void* pre = init_pre(arith)) CK(cudaLaunchKernel(pre, dim3(G), dim3(mwk::TPB), a_w, smem, s));
     CK(cudaLaunchKernel(bt->init, dim3(G), dim3(mwk::TPB), a_b, smem, s));
     CK(cudaLaunchKernel(kt->zero_x, dim3(G), dim3(mwk::TPB), a_w, 0, s));
     const void* fns[5] = {bt->p, bt->spmv_v, bt->s, bt->spmv_t, bt->xr};

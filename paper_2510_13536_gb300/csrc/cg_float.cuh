@@ -19,10 +19,9 @@
 // correctly rounded multiplication by a power of two.
 //
 // The kernels keep the plan's summation order (the vector kernels' tiles of
-// TPB rows over G blocks) and the stop tests of cg_kernels.cuh.  QQF runs no
-// BiCGStab, so E, the shift applied by this iteration's update and the shift
-// the next update applies are kept in the DevState's BiCGStab slot omega[0..2]
-// (small integers, exact as doubles).
+// TPB rows over G blocks) and the stop tests of cg_kernels.cuh.  E, the shift
+// applied by this iteration's update and the shift the next update applies
+// are kept in the DevState (q_e, q_s, q_s_next).
 #pragma once
 #include "cg_kernels.cuh"
 #include "mw_float.cuh"
@@ -54,13 +53,13 @@ __device__ __forceinline__ void st<mw::QF>(double* __restrict__ v, int64_t n, in
 }
 constexpr int kQqfSlots = 2;          // 8-byte slots per element
 
-__device__ __forceinline__ int qqf_E(const DevState* S) { return (int)S->omega[0]; }
-__device__ __forceinline__ int qqf_shift(const DevState* S) { return (int)S->omega[1]; }
-__device__ __forceinline__ int qqf_next_shift(const DevState* S) { return (int)S->omega[2]; }
+__device__ __forceinline__ int qqf_E(const DevState* S) { return S->q_e; }
+__device__ __forceinline__ int qqf_shift(const DevState* S) { return S->q_s; }
+__device__ __forceinline__ int qqf_next_shift(const DevState* S) { return S->q_s_next; }
 __device__ __forceinline__ void qqf_set_scale(DevState* S, int E, int s, int s_next) {
-  S->omega[0] = (double)E;
-  S->omega[1] = (double)s;
-  S->omega[2] = (double)s_next;
+  S->q_e = E;
+  S->q_s = s;
+  S->q_s_next = s_next;
 }
 
 // ilogb of a positive finite FP64 value, from the bits.

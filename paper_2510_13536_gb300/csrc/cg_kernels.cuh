@@ -72,6 +72,10 @@ struct DevState {
   double omega[4];          // BiCGStab: omega
   int32_t early;            // BiCGStab: ||s|| met the tolerance (x += alpha p ends the solve)
   uint32_t xmax_bits;       // QQF: largest |leading word of x| of this iteration, as FP32 bits
+  int32_t q_e;              // QQF: the scaling exponent E (r = 2^E r~)
+  int32_t q_s;              // QQF: the shift applied by this iteration's update
+  int32_t q_s_next;         // QQF: the shift the next update applies
+  int32_t pad1;
 };
 
 // Normalisation places (an extension of Sec. IV-D, which normalises r after

@@ -230,9 +230,8 @@ def solve_bicgstab(A: CSRMatrix, b: torch.Tensor, arith="qtw", tol: float = 1e-1
                    x0: torch.Tensor | None = None, history: bool = False) -> SolveResult:
     """BiCGStab on A x = b (A may be nonsymmetric) in the given arithmetic (device tensors)."""
     a = arith_id(arith)
-    w = WORDS[a]
-    x = torch.zeros((w, A.n), dtype=torch.float64, device=b.device) if x0 is None else \
-        x0.to(torch.float64).reshape(w, A.n).clone().contiguous()
+    x = torch.zeros((SLOTS[a], A.n), dtype=torch.float64, device=b.device) if x0 is None else \
+        _to_abi(a, x0, A.n).clone()
     it, rr = ctypes.c_int32(0), ctypes.c_double(0.0)
     hist = None
     if history:
@@ -242,7 +241,7 @@ def solve_bicgstab(A: CSRMatrix, b: torch.Tensor, arith="qtw", tol: float = 1e-1
                                                 ctypes.byref(rr)))
     if history:
         hist = hist[: it.value]
-    return SolveResult(x, it.value, rr.value, st, hist)
+    return SolveResult(_from_abi(a, x, A.n), it.value, rr.value, st, hist)
 
 
 def solve_host(A: CSRMatrix, b: np.ndarray, arith="qtw", tol: float = 1e-14, maxit: int = 20000,

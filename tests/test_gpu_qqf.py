@@ -372,11 +372,40 @@ def test_batched_bit_exact(mw, orc, ar):
     assert {0, 1, 4} <= statuses and (2 in statuses) == (ar == "qqf")
 
 
-def test_unsupported_paths_rejected(mw, ar):
-    from paper_2510_13536_gb300._capi import MWCGError
-    A = P.laplacian_2d(20)
-    M = mw.CSRMatrix.from_csr(A)
-    b = dev(P.rhs_uniform(A.n, 80))
-    with pytest.raises(MWCGError):
-        mw.solve_bicgstab(M, b, ar, 1e-10, 10)
-    assert mw.solve(M, b, ar, 1e-10, 200).status == 0
+def test_bicgstab_bit_exact(mw, orc, ar, monkeypatch):
+    """BiCGStab in FP32 words (r, p, v, s, t at 2^E, the shadow residual at
+    2^E0; the generic p update and SpMV kernels, the scaled init, s and x / r
+    kernels) equals the oracle's scaled BiCGStab bit for bit: iterations,
+    status, residual history and x, on the graph and on host-launched kernels,
+    for nonsymmetric convection-diffusion systems, the early exit (A = 2I),
+    a breakdown (a rotation), b = 0, maxit = 0 and x leaving FP32's range."""
+    def check(M, A, b, tol, maxit, tag):
+        r = mw.solve_bicgstab(M, dev(b), ar, tol, maxit, history=True)
+        xo, ito, rro, sto, ho = orc.bicgstab(ar, A, b, tol=tol, maxit=maxit, plan=M.plan, history=True)
+        assert (r.iters, r.status) == (ito, sto), (tag, r.iters, ito, r.status, sto)
+        assert same_bits(np.array([r.relres]), np.array([rro])), tag
+        assert same_bits(r.x.cpu().numpy(), xo), tag
+        if r.iters:
+            assert same_bits(r.history.cpu().numpy(), ho), tag
+        return r
+    for A, seed, tol in ((P.convection_diffusion_2d(48, 2.0), 91, 1e-22),
+                         (P.convection_diffusion_2d(90, 8.0), 92, 1e-14)):
+        b = P.rhs_uniform(A.n, seed)
+        M = mw.CSRMatrix.from_csr(A)
+        assert check(M, A, b, tol, 3000, A.name).iters > 10
+    A = P.convection_diffusion_2d(48, 2.0)
+    b = P.rhs_uniform(A.n, 91)
+    monkeypatch.setenv("MWCG_EAGER", "1")
+    check(mw.CSRMatrix.from_csr(A), A, b, 1e-22, 3000, "eager")
+    monkeypatch.delenv("MWCG_EAGER")
+    n = 300
+    D = P.CSR(n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.full(n, 2.0))
+    r = check(mw.CSRMatrix.from_csr(D), D, P.rhs_uniform(n, 93), 1e-30, 5, "2I")
+    assert (r.status, r.iters) == (0, 1)
+    R = P.CSR(2, np.array([0, 1, 2], dtype=np.int64), np.array([1, 0], dtype=np.int32), np.array([1.0, -1.0]))
+    assert check(mw.CSRMatrix.from_csr(R), R, np.array([1.0, 0.0]), 1e-30, 5, "rotation").status == 2
+    C = P.convection_diffusion_2d(16, 1.0)
+    MC = mw.CSRMatrix.from_csr(C)
+    check(MC, C, np.zeros(C.n), 1e-12, 50, "b = 0")
+    check(MC, C, P.rhs_uniform(C.n, 94), 1e-12, 0, "maxit 0")
+    assert check(MC, C, P.rhs_uniform(C.n, 95) * 2.0 ** 300, 1e-22, 2000, "2^300").status == 4
