@@ -665,7 +665,7 @@ def _measured_hbm_gbs():
 
 def run_bicg(torch, mw, P, cpu):
     """BiCGStab on nonsymmetric upwind convection-diffusion systems (512^2,
-    mesh Peclet 1 and 8), every arithmetic from FP64 to QQW, to 1e-14."""
+    mesh Peclet 1 and 8), FP64 to QQW and the FP32-word QQF and QF, to 1e-14."""
     out = {}
     for beta in (1.0, 8.0):
         A = P.convection_diffusion_2d(512, beta)
@@ -674,7 +674,7 @@ def run_bicg(torch, mw, P, cpu):
         db = torch.as_tensor(b, device="cuda")
         res = {"workload": f"2-D upwind convection-diffusion 512^2 (n = {A.n}), mesh Peclet {beta:g}, b = 2U-1, "
                            "tol 1e-14, maxit 20000", "plan": list(M.plan), "runs": []}
-        for ar in ("fp64", "dw", "qdw", "qtw", "qqw"):
+        for ar in ("fp64", "dw", "qdw", "qtw", "qqw", "qqf", "qf"):
             mw.solve_bicgstab(M, db, ar, 1e-14, 2)
             r, ms = _timed(torch, lambda: mw.solve_bicgstab(M, db, ar, 1e-14, 20000))
             res["runs"].append({"arith": ar, "iters": r.iters, "status": r.status, "relres": r.relres,
